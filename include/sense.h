@@ -1,0 +1,154 @@
+/*
+ * sense.h -- C ABI of libsense.so, a CUDA (sm_103a) implementation of
+ * multi-coil Cartesian SENSE reconstruction.
+ *
+ * Method: arXiv 1807.11830 (OpenCLIPER), Sec. IV-A, Eq. 1,
+ *     M = sum_i S_i^* F^{-1}(Y_i),
+ * is the coil-combining adjoint E^H of the encoding operator
+ *     E x = { M_f F2 (S_c . x_f) }_{f,c}
+ * when every k-space line is sampled.  The library provides E, E^H, the
+ * normal operator E^H E and conjugate-gradient SENSE (CG on E^H E x = E^H y),
+ * plus root-sum-of-squares (Sec. IV-B).
+ *
+ * Conventions shared by every entry point:
+ *   - F is the unitary DFT, exp(-2 pi i jk/n)/sqrt(n) forward, its conjugate
+ *     inverse (Eq. 1 writes F^{-1} with no scale); DC at index 0 (no shift).
+ *   - Row index y (slow, "ny") is the phase-encode direction and is masked by
+ *     line; x (fast, "nx") is the fully sampled readout.
+ *   - Layouts, row-major, complex interleaved (re, im):
+ *       image x, out, x_out     [frames][ny][nx]        sense_c32
+ *       sensitivities S         [coils][ny][nx]         storage type
+ *       k-space y               [frames][coils][lines][nx]  storage type
+ *       lines                   [frames][lines] int32, each row strictly
+ *                               increasing inside [0, ny)
+ *     "storage type" is sense_c32 for SENSE_STORE_C64 and a pair of
+ *     bfloat16 (re, im; 4 bytes) for SENSE_STORE_BF16.  All frames of one
+ *     plan share the same S.
+ *   - Every array argument is a DEVICE pointer on the plan's device, owned by
+ *     the caller, 16-byte aligned; the library never frees caller memory.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream).  Argument errors are reported
+ *     synchronously by the return value.  Invalid line indices are detected
+ *     by the kernels, which skip the offending line and raise a device flag
+ *     that sense_plan_check() reports as SENSE_EDEVICE.
+ *   - A plan is not thread-safe: calls on one plan must be serialised by the
+ *     caller (they share the plan's workspace).
+ *   - On any non-OK return, sense_last_error() holds a message for the
+ *     calling thread.
+ */
+#ifndef SENSE_H
+#define SENSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { float re, im; } sense_c32;
+
+typedef enum {
+  SENSE_OK = 0,
+  SENSE_EINVAL = 1,             /* null/unaligned pointer, bad shape or argument */
+  SENSE_EUNSUPPORTED_SIZE = 2,  /* ny or nx has no compiled transform (see sense_size_supported) */
+  SENSE_ENOMEM = 3,             /* device allocation failed */
+  SENSE_ECUDA = 4,              /* a CUDA runtime call failed */
+  SENSE_ETIMEOUT = 5,           /* a bounded device-side wait gave up */
+  SENSE_ENUMERIC = 6,           /* CG breakdown: Re<p, E^H E p> not > 0 (or NaN) */
+  SENSE_EQUEUE_FULL = 7,        /* request queue cannot admit more work */
+  SENSE_ENOTFOUND = 8,          /* unknown request id */
+  SENSE_EDEVICE = 9             /* a kernel flagged invalid input (bad line index/order) */
+} sense_status;
+
+typedef enum { SENSE_STORE_C64 = 0, SENSE_STORE_BF16 = 1 } sense_storage;
+
+/* Problem shape of one plan: ny x nx images, `coils` maps, `frames` images
+ * sharing them, `lines` sampled phase-encode rows per frame. */
+typedef struct {
+  int ny, nx, coils, frames, lines;
+  int storage; /* sense_storage of S and y */
+} sense_shape;
+
+/* Per-frame CG outcome written by sense_cg_solve. */
+typedef enum {
+  SENSE_CG_CONVERGED = 1, /* relative residual reached rel_tol, or became exactly 0 */
+  SENSE_CG_MAXITER = 2,   /* max_iter iterations applied */
+  SENSE_CG_BREAKDOWN = 3  /* Re<p, E^H E p> was not > 0; x holds the last good iterate */
+} sense_cg_outcome;
+
+typedef struct sense_plan sense_plan;
+
+/* 1 if n is a supported transform length for ny or nx, else 0. */
+int sense_size_supported(int n);
+
+/* Create a plan for `shape` on CUDA device `device`: validates the shape,
+ * uploads FP64-derived twiddle tables and allocates the plan's workspace
+ * (compacted k-space intermediate, CG vectors, FP64 partial sums).  The plan
+ * owns all of it.  Returns SENSE_EUNSUPPORTED_SIZE for untransformable ny/nx,
+ * SENSE_ENOMEM if the workspace does not fit. */
+sense_status sense_plan_create(const sense_shape* shape, int device, sense_plan** out);
+
+/* Release everything the plan owns.  Waits for the plan's outstanding work. */
+sense_status sense_plan_destroy(sense_plan* plan);
+
+/* Device memory the plan holds, in bytes. */
+size_t sense_plan_workspace_bytes(const sense_plan* plan);
+
+/* Encoding operator E (Eq. 1's forward model):
+ *   y[f][c][l][:] = (F2 (S_c . x_f))[lines[f][l]][:]
+ * x: [frames][ny][nx] c32; S, y: storage type.  In BF16 storage the result is
+ * rounded to bfloat16 (round-to-nearest-even) when stored. */
+sense_status sense_forward(sense_plan* plan, const sense_c32* x, const void* S, const int32_t* lines, void* y,
+                           void* stream);
+
+/* Adjoint E^H (Eq. 1 with zero-filled missing lines):
+ *   x_f = sum_c conj(S_c) . F2^H (Z_f y_{f,c}),  Z_f scattering line l to row lines[f][l].
+ * With lines = all rows this is exactly Eq. 1 of the paper. */
+sense_status sense_adjoint(sense_plan* plan, const void* y, const void* S, const int32_t* lines, sense_c32* x,
+                           void* stream);
+
+/* Normal operator out = E^H E x, per frame.  Computed column-wise: because the
+ * mask acts on rows only and F_x is unitary, E^H E = sum_c S_c^H F_y^H M_f F_y S_c,
+ * so no x-direction transform is needed.  `out` must not alias `x`. */
+sense_status sense_normal(sense_plan* plan, const sense_c32* x, const void* S, const int32_t* lines,
+                          sense_c32* out, void* stream);
+
+/* CG-SENSE: Hestenes-Stiefel conjugate gradients on (E^H E) x = E^H y, run
+ * independently per frame from x0 = 0 with FP64 inner products:
+ *   r0 = p0 = E^H y;  per iteration  q = E^H E p,  alpha = <r,r>/Re<p,q>,
+ *   x += alpha p,  r -= alpha q,  beta = <r',r'>/<r,r>,  p = r' + beta p.
+ * A frame stops when <r,r> becomes 0, when rel_tol > 0 and
+ * sqrt(<r,r>/<r0,r0>) <= rel_tol, after max_iter iterations, or on breakdown
+ * (Re<p,q> not > 0).  Outputs (device arrays, any may be NULL except x_out):
+ *   x_out [frames][ny][nx];  iters_out [frames] iterations applied;
+ *   rel_resid_out [frames] sqrt(<r,r>/<r0,r0>) at exit (0 if y_f == 0);
+ *   outcome_out [frames] a sense_cg_outcome.
+ * The iteration loop runs on the device without host synchronisation; with
+ * rel_tol > 0 the host polls a device counter of live frames every few
+ * iterations to stop early.  x_out must not alias y or S. */
+sense_status sense_cg_solve(sense_plan* plan, const void* y, const void* S, const int32_t* lines, int max_iter,
+                            double rel_tol, sense_c32* x_out, int32_t* iters_out, double* rel_resid_out,
+                            int32_t* outcome_out, void* stream);
+
+/* Root sum of squares (Sec. IV-B): out[f][i] = sqrt(sum_c |F2^H(Z_f y_{f,c})[i]|^2),
+ * out: [frames][ny][nx] float. S is not used. */
+sense_status sense_rss(sense_plan* plan, const void* y, const int32_t* lines, float* out, void* stream);
+
+/* Convert `count` complex64 values to the bfloat16-pair storage format with
+ * round-to-nearest-even (for preparing S and y of a BF16 plan). */
+sense_status sense_c32_to_bf16(const sense_c32* in, void* out, size_t count, void* stream);
+
+/* Synchronise `stream` and report errors the kernels flagged since the last
+ * check (SENSE_EDEVICE for bad lines, SENSE_ETIMEOUT for a bounded wait that
+ * gave up).  Clears the flags. */
+sense_status sense_plan_check(sense_plan* plan, void* stream);
+
+/* Message describing the last non-OK status returned on this thread. */
+const char* sense_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SENSE_H */

@@ -1,0 +1,42 @@
+// Host-side launchers of the SENSE kernels, dispatched on the transform
+// length.  Each returns cudaErrorInvalidValue for a length without a
+// compiled configuration, else the launch status.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace sense {
+
+bool size_supported(int n);
+int col_width(int n);      // columns per block of the column kernels for length n
+int col_threads(int n);
+int row_width(int n);      // rows per block of the row kernels for length n
+
+template <class St>
+cudaError_t launch_fwd_col(int n, const FwdColArgs<St>& a, int tiles, int frames, cudaStream_t s);
+template <class St>
+cudaError_t launch_adj_col(int n, int mode, const AdjColArgs<St>& a, int tiles, int frames, cudaStream_t s);
+template <class St>
+cudaError_t launch_normal(int n, bool cg, const NormalArgs<St>& a, int tiles, int frames, cudaStream_t s);
+// forward row pass: FP32 in, storage St out
+template <class St>
+cudaError_t launch_rows_fwd(int n, const RowArgs<float2, typename St::T>& a, cudaStream_t s);
+// inverse row pass: storage St in, FP32 out
+template <class St>
+cudaError_t launch_rows_inv(int n, const RowArgs<typename St::T, float2>& a, cudaStream_t s);
+
+// Set the dynamic shared memory limit of `kern` once per device.
+template <class K>
+inline cudaError_t ensure_smem(K kern, size_t bytes, unsigned long long* done_mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (__atomic_load_n(done_mask, __ATOMIC_ACQUIRE) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) __atomic_fetch_or(done_mask, bit, __ATOMIC_ACQ_REL);
+  return e;
+}
+
+}  // namespace sense

@@ -1,0 +1,516 @@
+// Host runtime and C ABI of libsense.so: plans (twiddles + workspace), the
+// operator entry points and the CG-SENSE driver loop (captured once per
+// argument set into a CUDA graph and replayed).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "cg_kernels.cuh"
+#include "launch.h"
+#include "sense.h"
+
+using namespace sense;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sense_status fail(sense_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define SENSE_CUDA_TRY(expr)                                                                  \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) return fail(SENSE_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool aligned16(const void* p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool aligned4(const void* p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
+
+// exp(-2 pi i m / n), m = 0..n-1, in FP64 and rounded once to FP32.
+std::vector<float2> twiddles(int n) {
+  std::vector<float2> t((size_t)n);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int m = 0; m < n; ++m) {
+    const double a = -two_pi * (double)m / (double)n;
+    t[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  return t;
+}
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev_);
+    if (prev_ != dev) cudaSetDevice(dev);
+    dev_ = dev;
+  }
+  ~DeviceGuard() {
+    if (prev_ != dev_) cudaSetDevice(prev_);
+  }
+
+ private:
+  int prev_ = 0, dev_ = 0;
+};
+
+}  // namespace
+
+struct sense_plan {
+  sense_shape sh{};
+  int device = 0;
+  int tiles = 0;        // column tiles per frame
+  int upd_blocks = 0;   // CG-update blocks per frame
+  size_t img = 0;       // ny * nx
+  float2* tw_y = nullptr;
+  float2* tw_x = nullptr;
+  float2* tmp = nullptr;  // [F][C][L][nx] intermediate of E / E^H
+  float2* r = nullptr;
+  float2* p = nullptr;
+  float2* q = nullptr;
+  double* dbl = nullptr;  // rho, rho0, alpha, beta, resid  ([5][F])
+  int* ints = nullptr;    // iters, outcome, active ([3][F]), live, err
+  unsigned* counter = nullptr;
+  double* part = nullptr;
+  int part_stride = 0;
+  int* live_host = nullptr;  // pinned
+  size_t ws_bytes = 0;
+  std::vector<void*> allocs;
+  cudaStream_t capture_stream = nullptr;
+  // CUDA graphs of the CG iteration loop, keyed by the arguments they bake in
+  std::map<std::tuple<const void*, const void*, const void*, int, int, double>, cudaGraphExec_t> graphs;
+
+  CgState cg(double tol) const {
+    CgState g;
+    const int F = sh.frames;
+    g.rho = dbl;
+    g.rho0 = dbl + F;
+    g.alpha = dbl + 2 * F;
+    g.beta = dbl + 3 * F;
+    g.resid = dbl + 4 * F;
+    g.iters = ints;
+    g.outcome = ints + F;
+    g.active = ints + 2 * F;
+    g.live = ints + 3 * F;
+    g.counter = counter;
+    g.part = part;
+    g.part_stride = part_stride;
+    g.tol = tol;
+    return g;
+  }
+  int* err() const { return ints + 3 * sh.frames + 1; }
+};
+
+namespace {
+
+template <class T>
+sense_status dalloc(sense_plan* pl, T** out, size_t count) {
+  void* ptr = nullptr;
+  const size_t bytes = count * sizeof(T);
+  cudaError_t e = cudaMalloc(&ptr, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SENSE_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  pl->allocs.push_back(ptr);
+  pl->ws_bytes += bytes;
+  *out = static_cast<T*>(ptr);
+  return SENSE_OK;
+}
+
+void release(sense_plan* pl) {
+  for (auto& kv : pl->graphs) cudaGraphExecDestroy(kv.second);
+  pl->graphs.clear();
+  for (void* ptr : pl->allocs) cudaFree(ptr);
+  pl->allocs.clear();
+  if (pl->live_host) cudaFreeHost(pl->live_host);
+  pl->live_host = nullptr;
+  if (pl->capture_stream) cudaStreamDestroy(pl->capture_stream);
+  pl->capture_stream = nullptr;
+}
+
+sense_status check_shape(const sense_shape* sh) {
+  if (!sh) return fail(SENSE_EINVAL, "shape is NULL");
+  if (sh->frames < 1 || sh->coils < 1 || sh->ny < 1 || sh->nx < 1)
+    return fail(SENSE_EINVAL, "frames, coils, ny and nx must be >= 1");
+  if (sh->frames > 65535) return fail(SENSE_EINVAL, "at most 65535 frames per plan");
+  if (sh->lines < 1 || sh->lines > sh->ny) return fail(SENSE_EINVAL, "lines must be in [1, ny]");
+  if (sh->storage != SENSE_STORE_C64 && sh->storage != SENSE_STORE_BF16)
+    return fail(SENSE_EINVAL, "storage must be SENSE_STORE_C64 or SENSE_STORE_BF16");
+  if (!size_supported(sh->ny) || !size_supported(sh->nx))
+    return fail(SENSE_EUNSUPPORTED_SIZE, "no compiled transform for ny=" + std::to_string(sh->ny) +
+                                             " / nx=" + std::to_string(sh->nx));
+  return SENSE_OK;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+sense_status launch_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return SENSE_OK;
+  return fail(SENSE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---- operator launch sequences (shared by the entry points and graph capture) ----
+
+template <class St>
+sense_status run_forward(sense_plan* pl, const float2* x, const void* S, const int* lines, void* y,
+                         cudaStream_t st) {
+  const sense_shape& sh = pl->sh;
+  FwdColArgs<St> a{};
+  a.x = x;
+  a.S = static_cast<const typename St::T*>(S);
+  a.lines = lines;
+  a.tmp = pl->tmp;
+  a.tw = pl->tw_y;
+  a.nx = sh.nx;
+  a.coils = sh.coils;
+  a.L = sh.lines;
+  a.err = pl->err();
+  sense_status rc = launch_status(launch_fwd_col<St>(sh.ny, a, pl->tiles, sh.frames, st), "forward column pass");
+  if (rc != SENSE_OK) return rc;
+  RowArgs<float2, typename St::T> ra{};
+  ra.in = pl->tmp;
+  ra.out = static_cast<typename St::T*>(y);
+  ra.tw = pl->tw_x;
+  ra.rows = (long)sh.frames * sh.coils * sh.lines;
+  return launch_status(launch_rows_fwd<St>(sh.nx, ra, st), "forward row pass");
+}
+
+template <class St>
+sense_status run_rows_inv(sense_plan* pl, const void* y, cudaStream_t st) {
+  const sense_shape& sh = pl->sh;
+  RowArgs<typename St::T, float2> ra{};
+  ra.in = static_cast<const typename St::T*>(y);
+  ra.out = pl->tmp;
+  ra.tw = pl->tw_x;
+  ra.rows = (long)sh.frames * sh.coils * sh.lines;
+  return launch_status(launch_rows_inv<St>(sh.nx, ra, st), "adjoint row pass");
+}
+
+template <class St>
+sense_status run_adjoint(sense_plan* pl, int mode, const void* y, const void* S, const int* lines, float2* x,
+                         float* rss, double tol, cudaStream_t st) {
+  const sense_shape& sh = pl->sh;
+  sense_status rc = run_rows_inv<St>(pl, y, st);
+  if (rc != SENSE_OK) return rc;
+  if (mode == 2) {
+    AdjColArgs<StC64> a{};
+    a.tmp = pl->tmp;
+    a.lines = lines;
+    a.tw = pl->tw_y;
+    a.rss = rss;
+    a.nx = sh.nx;
+    a.coils = sh.coils;
+    a.L = sh.lines;
+    a.tiles = pl->tiles;
+    a.err = pl->err();
+    return launch_status(launch_adj_col<StC64>(sh.ny, 2, a, pl->tiles, sh.frames, st), "rss column pass");
+  }
+  AdjColArgs<St> a{};
+  a.tmp = pl->tmp;
+  a.S = static_cast<const typename St::T*>(S);
+  a.lines = lines;
+  a.tw = pl->tw_y;
+  a.x = x;
+  a.r = pl->r;
+  a.p = pl->p;
+  a.nx = sh.nx;
+  a.coils = sh.coils;
+  a.L = sh.lines;
+  a.tiles = pl->tiles;
+  a.err = pl->err();
+  a.cg = pl->cg(tol);
+  return launch_status(launch_adj_col<St>(sh.ny, mode, a, pl->tiles, sh.frames, st), "adjoint column pass");
+}
+
+template <class St>
+sense_status run_normal(sense_plan* pl, const float2* x, const void* S, const int* lines, float2* out,
+                        cudaStream_t st) {
+  const sense_shape& sh = pl->sh;
+  NormalArgs<St> a{};
+  a.x = x;
+  a.out = out;
+  a.S = static_cast<const typename St::T*>(S);
+  a.lines = lines;
+  a.tw = pl->tw_y;
+  a.nx = sh.nx;
+  a.coils = sh.coils;
+  a.L = sh.lines;
+  a.tiles = pl->tiles;
+  a.err = pl->err();
+  return launch_status(launch_normal<St>(sh.ny, false, a, pl->tiles, sh.frames, st), "normal operator");
+}
+
+// One CG iteration: q = E^H E p (with p = r + beta p first when p_update),
+// alpha; then x += alpha p, r -= alpha q, beta / stopping test.
+template <class St>
+sense_status run_cg_iteration(sense_plan* pl, const void* S, const int* lines, float2* x, int p_update,
+                              double tol, cudaStream_t st) {
+  const sense_shape& sh = pl->sh;
+  NormalArgs<St> a{};
+  a.p = pl->p;
+  a.r = pl->r;
+  a.q = pl->q;
+  a.S = static_cast<const typename St::T*>(S);
+  a.lines = lines;
+  a.tw = pl->tw_y;
+  a.nx = sh.nx;
+  a.coils = sh.coils;
+  a.L = sh.lines;
+  a.tiles = pl->tiles;
+  a.p_update = p_update;
+  a.err = pl->err();
+  a.cg = pl->cg(tol);
+  sense_status rc = launch_status(launch_normal<St>(sh.ny, true, a, pl->tiles, sh.frames, st), "CG normal pass");
+  if (rc != SENSE_OK) return rc;
+  UpdateArgs u{};
+  u.x = reinterpret_cast<float4*>(x);
+  u.p = reinterpret_cast<const float4*>(pl->p);
+  u.q = reinterpret_cast<const float4*>(pl->q);
+  u.r = reinterpret_cast<float4*>(pl->r);
+  u.img4 = (long)(pl->img / 2);
+  u.blocks_per_frame = pl->upd_blocks;
+  u.cg = pl->cg(tol);
+  k_cg_update<<<dim3(pl->upd_blocks, sh.frames), UPD_THREADS, 0, st>>>(u);
+  return launch_status(cudaGetLastError(), "CG update");
+}
+
+template <class St>
+sense_status run_cg_chunk(sense_plan* pl, const void* S, const int* lines, float2* x, int first, int count,
+                          double tol, cudaStream_t st) {
+  for (int i = 0; i < count; ++i) {
+    sense_status rc = run_cg_iteration<St>(pl, S, lines, x, (first + i) > 0 ? 1 : 0, tol, st);
+    if (rc != SENSE_OK) return rc;
+  }
+  return SENSE_OK;
+}
+
+// Replay (capturing on first use) the graph of `count` iterations starting at
+// iteration `first` for these arguments.
+template <class St>
+sense_status cg_chunk_graph(sense_plan* pl, const void* S, const int* lines, float2* x, int first, int count,
+                            double tol, cudaStream_t st) {
+  const int first_key = first > 0 ? 1 : 0;
+  auto key = std::make_tuple(S, (const void*)lines, (const void*)x, first_key, count, tol);
+  auto it = pl->graphs.find(key);
+  if (it == pl->graphs.end()) {
+    cudaStream_t cs = pl->capture_stream;
+    SENSE_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    sense_status rc = run_cg_chunk<St>(pl, S, lines, x, first, count, tol, cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    if (rc != SENSE_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ee != cudaSuccess) return fail(SENSE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
+    cudaGraphExec_t exec = nullptr;
+    ee = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ee != cudaSuccess) return fail(SENSE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ee));
+    if (pl->graphs.size() > 64) {  // bound the cache
+      for (auto& kv : pl->graphs) cudaGraphExecDestroy(kv.second);
+      pl->graphs.clear();
+    }
+    it = pl->graphs.emplace(key, exec).first;
+  }
+  SENSE_CUDA_TRY(cudaGraphLaunch(it->second, st));
+  return SENSE_OK;
+}
+
+constexpr int kPollEvery = 5;
+
+template <class St>
+sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const int* lines, int max_iter, double tol,
+                          float2* x, int* iters_out, double* resid_out, int* outcome_out, cudaStream_t st) {
+  const sense_shape& sh = pl->sh;
+  SENSE_CUDA_TRY(cudaMemsetAsync(pl->counter, 0, sizeof(unsigned) * sh.frames, st));
+  SENSE_CUDA_TRY(cudaMemsetAsync(pl->cg(tol).live, 0, sizeof(int), st));
+  sense_status rc = run_adjoint<St>(pl, 1, y, S, lines, x, nullptr, tol, st);
+  if (rc != SENSE_OK) return rc;
+  {  // kernel attributes are set outside stream capture
+    NormalArgs<St> none{};
+    rc = launch_status(launch_normal<St>(sh.ny, true, none, 0, 0, st), "CG normal set-up");
+    if (rc != SENSE_OK) return rc;
+  }
+  if (tol <= 0.0) {
+    if (max_iter > 0) rc = cg_chunk_graph<St>(pl, S, lines, x, 0, max_iter, tol, st);
+    if (rc != SENSE_OK) return rc;
+  } else {
+    int done = 0;
+    while (done < max_iter) {
+      const int count = (max_iter - done) < kPollEvery ? (max_iter - done) : kPollEvery;
+      rc = cg_chunk_graph<St>(pl, S, lines, x, done, count, tol, st);
+      if (rc != SENSE_OK) return rc;
+      done += count;
+      if (done >= max_iter) break;
+      SENSE_CUDA_TRY(cudaMemcpyAsync(pl->live_host, pl->cg(tol).live, sizeof(int), cudaMemcpyDeviceToHost, st));
+      SENSE_CUDA_TRY(cudaStreamSynchronize(st));
+      if (*pl->live_host <= 0) break;
+    }
+  }
+  k_cg_finish<<<(sh.frames + 127) / 128, 128, 0, st>>>(pl->cg(tol), sh.frames, iters_out, resid_out, outcome_out);
+  return launch_status(cudaGetLastError(), "CG finish");
+}
+
+}  // namespace
+
+extern "C" {
+
+int sense_size_supported(int n) { return size_supported(n) ? 1 : 0; }
+
+const char* sense_last_error(void) { return g_last_error.c_str(); }
+
+sense_status sense_plan_create(const sense_shape* shape, int device, sense_plan** out) {
+  if (!out) return fail(SENSE_EINVAL, "out is NULL");
+  *out = nullptr;
+  sense_status rc = check_shape(shape);
+  if (rc != SENSE_OK) return rc;
+  int ndev = 0;
+  SENSE_CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(SENSE_EINVAL, "device index out of range");
+  DeviceGuard guard(device);
+  sense_plan* pl = new sense_plan();
+  pl->sh = *shape;
+  pl->device = device;
+  const sense_shape& sh = pl->sh;
+  const int W = col_width(sh.ny);
+  pl->tiles = (sh.nx + W - 1) / W;
+  pl->img = (size_t)sh.ny * sh.nx;
+  pl->upd_blocks = (int)((pl->img + UPD_PER_BLOCK - 1) / UPD_PER_BLOCK);
+  pl->part_stride = pl->tiles > pl->upd_blocks ? pl->tiles : pl->upd_blocks;
+  const size_t F = (size_t)sh.frames;
+  if ((rc = dalloc(pl, &pl->tw_y, (size_t)sh.ny)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->tw_x, (size_t)sh.nx)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->tmp, F * sh.coils * sh.lines * sh.nx)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->r, F * pl->img)) != SENSE_OK || (rc = dalloc(pl, &pl->p, F * pl->img)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->q, F * pl->img)) != SENSE_OK || (rc = dalloc(pl, &pl->dbl, 5 * F)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->ints, 3 * F + 2)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->counter, F)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->part, F * pl->part_stride)) != SENSE_OK) {
+    release(pl);
+    delete pl;
+    return rc;
+  }
+  cudaError_t e = cudaMallocHost(&pl->live_host, sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->capture_stream, cudaStreamNonBlocking);
+  std::vector<float2> ty = twiddles(sh.ny), tx = twiddles(sh.nx);
+  if (e == cudaSuccess) e = cudaMemcpy(pl->tw_y, ty.data(), sizeof(float2) * ty.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(pl->tw_x, tx.data(), sizeof(float2) * tx.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(pl->counter, 0, sizeof(unsigned) * F);
+  if (e == cudaSuccess) e = cudaMemset(pl->ints, 0, sizeof(int) * (3 * F + 2));
+  if (e == cudaSuccess) e = cudaMemset(pl->dbl, 0, sizeof(double) * 5 * F);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    release(pl);
+    delete pl;
+    return fail(SENSE_ECUDA, std::string("plan set-up: ") + cudaGetErrorString(e));
+  }
+  *out = pl;
+  return SENSE_OK;
+}
+
+sense_status sense_plan_destroy(sense_plan* plan) {
+  if (!plan) return SENSE_OK;
+  DeviceGuard guard(plan->device);
+  cudaDeviceSynchronize();
+  release(plan);
+  delete plan;
+  return SENSE_OK;
+}
+
+size_t sense_plan_workspace_bytes(const sense_plan* plan) { return plan ? plan->ws_bytes : 0; }
+
+sense_status sense_forward(sense_plan* pl, const sense_c32* x, const void* S, const int32_t* lines, void* y,
+                           void* stream) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (!aligned16(x) || !aligned16(S) || !aligned16(y) || !aligned4(lines))
+    return fail(SENSE_EINVAL, "x, S, y must be non-NULL and 16-byte aligned; lines 4-byte aligned");
+  DeviceGuard guard(pl->device);
+  const float2* xf = reinterpret_cast<const float2*>(x);
+  if (pl->sh.storage == SENSE_STORE_BF16) return run_forward<StBF16>(pl, xf, S, lines, y, as_stream(stream));
+  return run_forward<StC64>(pl, xf, S, lines, y, as_stream(stream));
+}
+
+sense_status sense_adjoint(sense_plan* pl, const void* y, const void* S, const int32_t* lines, sense_c32* x,
+                           void* stream) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (!aligned16(x) || !aligned16(S) || !aligned16(y) || !aligned4(lines))
+    return fail(SENSE_EINVAL, "x, S, y must be non-NULL and 16-byte aligned; lines 4-byte aligned");
+  DeviceGuard guard(pl->device);
+  float2* xf = reinterpret_cast<float2*>(x);
+  if (pl->sh.storage == SENSE_STORE_BF16)
+    return run_adjoint<StBF16>(pl, 0, y, S, lines, xf, nullptr, 0.0, as_stream(stream));
+  return run_adjoint<StC64>(pl, 0, y, S, lines, xf, nullptr, 0.0, as_stream(stream));
+}
+
+sense_status sense_normal(sense_plan* pl, const sense_c32* x, const void* S, const int32_t* lines, sense_c32* out,
+                          void* stream) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (!aligned16(x) || !aligned16(S) || !aligned16(out) || !aligned4(lines))
+    return fail(SENSE_EINVAL, "x, S, out must be non-NULL and 16-byte aligned; lines 4-byte aligned");
+  if ((const void*)x == (const void*)out) return fail(SENSE_EINVAL, "out must not alias x");
+  DeviceGuard guard(pl->device);
+  const float2* xf = reinterpret_cast<const float2*>(x);
+  float2* of = reinterpret_cast<float2*>(out);
+  if (pl->sh.storage == SENSE_STORE_BF16) return run_normal<StBF16>(pl, xf, S, lines, of, as_stream(stream));
+  return run_normal<StC64>(pl, xf, S, lines, of, as_stream(stream));
+}
+
+sense_status sense_cg_solve(sense_plan* pl, const void* y, const void* S, const int32_t* lines, int max_iter,
+                            double rel_tol, sense_c32* x_out, int32_t* iters_out, double* rel_resid_out,
+                            int32_t* outcome_out, void* stream) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (!aligned16(x_out) || !aligned16(S) || !aligned16(y) || !aligned4(lines))
+    return fail(SENSE_EINVAL, "x_out, S, y must be non-NULL and 16-byte aligned; lines 4-byte aligned");
+  if (max_iter < 0 || !(rel_tol >= 0.0)) return fail(SENSE_EINVAL, "max_iter must be >= 0 and rel_tol >= 0");
+  if ((const void*)x_out == y || (const void*)x_out == S) return fail(SENSE_EINVAL, "x_out aliases an input");
+  DeviceGuard guard(pl->device);
+  float2* xf = reinterpret_cast<float2*>(x_out);
+  if (pl->sh.storage == SENSE_STORE_BF16)
+    return run_cg_solve<StBF16>(pl, y, S, lines, max_iter, rel_tol, xf, iters_out, rel_resid_out, outcome_out,
+                                as_stream(stream));
+  return run_cg_solve<StC64>(pl, y, S, lines, max_iter, rel_tol, xf, iters_out, rel_resid_out, outcome_out,
+                             as_stream(stream));
+}
+
+sense_status sense_rss(sense_plan* pl, const void* y, const int32_t* lines, float* out, void* stream) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (!aligned16(y) || !aligned16(out) || !aligned4(lines))
+    return fail(SENSE_EINVAL, "y, out must be non-NULL and 16-byte aligned; lines 4-byte aligned");
+  DeviceGuard guard(pl->device);
+  if (pl->sh.storage == SENSE_STORE_BF16)
+    return run_adjoint<StBF16>(pl, 2, y, nullptr, lines, nullptr, out, 0.0, as_stream(stream));
+  return run_adjoint<StC64>(pl, 2, y, nullptr, lines, nullptr, out, 0.0, as_stream(stream));
+}
+
+sense_status sense_c32_to_bf16(const sense_c32* in, void* out, size_t count, void* stream) {
+  if (count == 0) return SENSE_OK;
+  if (!aligned4(in) || !aligned4(out)) return fail(SENSE_EINVAL, "in/out must be non-NULL and aligned");
+  const unsigned blocks = (unsigned)((count + 255) / 256 < 4096 ? (count + 255) / 256 : 4096);
+  k_to_bf16<<<blocks, 256, 0, as_stream(stream)>>>(reinterpret_cast<const float2*>(in),
+                                                    static_cast<__nv_bfloat162*>(out), count);
+  return launch_status(cudaGetLastError(), "bf16 conversion");
+}
+
+sense_status sense_plan_check(sense_plan* pl, void* stream) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  DeviceGuard guard(pl->device);
+  SENSE_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+  int flags = 0;
+  SENSE_CUDA_TRY(cudaMemcpy(&flags, pl->err(), sizeof(int), cudaMemcpyDeviceToHost));
+  SENSE_CUDA_TRY(cudaMemset(pl->err(), 0, sizeof(int)));
+  if (flags & ERR_LINES)
+    return fail(SENSE_EDEVICE, "a line index was outside [0, ny) or lines were not strictly increasing");
+  if (flags & ERR_TIMEOUT) return fail(SENSE_ETIMEOUT, "a bounded device-side wait gave up");
+  return SENSE_OK;
+}
+
+}  // extern "C"

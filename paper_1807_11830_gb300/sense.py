@@ -1,0 +1,187 @@
+"""Thin Python binding of libsense.so (ctypes; argument marshalling only).
+
+The functions keep the C names of ``include/sense.h`` and take PyTorch CUDA
+tensors, which serve only as device memory; every step of the computation
+runs in the library's kernels.  A missing library raises -- there is no
+fallback path.
+
+Tensor conventions (all contiguous, on the plan's device):
+  images x, out          complex64  [frames, ny, nx]
+  S (C64 storage)        complex64  [coils, ny, nx]
+  y (C64 storage)        complex64  [frames, coils, lines, nx]
+  S, y (BF16 storage)    bfloat16   [..., 2]  (re, im pairs)
+  lines                  int32      [frames, lines]
+"""
+import ctypes
+import os
+
+import torch
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsense.so")
+
+STORE_C64 = 0
+STORE_BF16 = 1
+
+SENSE_OK = 0
+STATUS_NAMES = {
+    0: "SENSE_OK", 1: "SENSE_EINVAL", 2: "SENSE_EUNSUPPORTED_SIZE", 3: "SENSE_ENOMEM", 4: "SENSE_ECUDA",
+    5: "SENSE_ETIMEOUT", 6: "SENSE_ENUMERIC", 7: "SENSE_EQUEUE_FULL", 8: "SENSE_ENOTFOUND", 9: "SENSE_EDEVICE",
+}
+CG_CONVERGED, CG_MAXITER, CG_BREAKDOWN = 1, 2, 3
+
+EXPORTED = (
+    "sense_size_supported", "sense_plan_create", "sense_plan_destroy", "sense_plan_workspace_bytes",
+    "sense_forward", "sense_adjoint", "sense_normal", "sense_cg_solve", "sense_rss", "sense_c32_to_bf16",
+    "sense_plan_check", "sense_last_error",
+)
+
+
+class SenseError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+
+
+class _Shape(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int), ("nx", ctypes.c_int), ("coils", ctypes.c_int),
+                ("frames", ctypes.c_int), ("lines", ctypes.c_int), ("storage", ctypes.c_int)]
+
+
+_LIB = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libsense.so and declare its entry points (raises if not built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libsense.so is not built (%s); run paper_1807_11830_gb300/build.py" % path)
+    lib = ctypes.CDLL(path)
+    vp, i, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+    lib.sense_size_supported.argtypes = [i]
+    lib.sense_size_supported.restype = i
+    lib.sense_plan_create.argtypes = [ctypes.POINTER(_Shape), i, ctypes.POINTER(vp)]
+    lib.sense_plan_create.restype = st
+    lib.sense_plan_destroy.argtypes = [vp]
+    lib.sense_plan_destroy.restype = st
+    lib.sense_plan_workspace_bytes.argtypes = [vp]
+    lib.sense_plan_workspace_bytes.restype = ctypes.c_size_t
+    for name in ("sense_forward", "sense_adjoint", "sense_normal"):
+        getattr(lib, name).argtypes = [vp, vp, vp, vp, vp, vp]
+        getattr(lib, name).restype = st
+    lib.sense_cg_solve.argtypes = [vp, vp, vp, vp, i, ctypes.c_double, vp, vp, vp, vp, vp]
+    lib.sense_cg_solve.restype = st
+    lib.sense_rss.argtypes = [vp, vp, vp, vp, vp]
+    lib.sense_rss.restype = st
+    lib.sense_c32_to_bf16.argtypes = [vp, vp, ctypes.c_size_t, vp]
+    lib.sense_c32_to_bf16.restype = st
+    lib.sense_plan_check.argtypes = [vp, vp]
+    lib.sense_plan_check.restype = st
+    lib.sense_last_error.argtypes = []
+    lib.sense_last_error.restype = ctypes.c_char_p
+    _LIB = lib
+    return lib
+
+
+def _check(rc):
+    if rc != SENSE_OK:
+        msg = load_library().sense_last_error()
+        raise SenseError(rc, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def sense_size_supported(n):
+    return bool(load_library().sense_size_supported(int(n)))
+
+
+class Plan:
+    """Owns a ``sense_plan*`` (twiddles + workspace) for one problem shape."""
+
+    def __init__(self, ny, nx, coils, frames, lines, storage=STORE_C64, device=0):
+        lib = load_library()
+        self.shape = dict(ny=ny, nx=nx, coils=coils, frames=frames, lines=lines, storage=storage)
+        self.device = device
+        h = ctypes.c_void_p()
+        sh = _Shape(ny, nx, coils, frames, lines, storage)
+        _check(lib.sense_plan_create(ctypes.byref(sh), device, ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load_library().sense_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self):
+        return load_library().sense_plan_workspace_bytes(self.handle)
+
+
+def sense_plan_create(ny, nx, coils, frames, lines, storage=STORE_C64, device=0):
+    return Plan(ny, nx, coils, frames, lines, storage, device)
+
+
+def sense_plan_destroy(plan):
+    plan.close()
+
+
+def sense_forward(plan, x, S, lines, y, stream=None):
+    _check(load_library().sense_forward(plan.handle, _ptr(x), _ptr(S), _ptr(lines), _ptr(y), _stream(stream)))
+    return y
+
+
+def sense_adjoint(plan, y, S, lines, x, stream=None):
+    _check(load_library().sense_adjoint(plan.handle, _ptr(y), _ptr(S), _ptr(lines), _ptr(x), _stream(stream)))
+    return x
+
+
+def sense_normal(plan, x, S, lines, out, stream=None):
+    _check(load_library().sense_normal(plan.handle, _ptr(x), _ptr(S), _ptr(lines), _ptr(out), _stream(stream)))
+    return out
+
+
+def sense_cg_solve(plan, y, S, lines, max_iter, rel_tol, x_out, iters_out=None, rel_resid_out=None,
+                   outcome_out=None, stream=None):
+    _check(load_library().sense_cg_solve(plan.handle, _ptr(y), _ptr(S), _ptr(lines), int(max_iter),
+                                         float(rel_tol), _ptr(x_out), _ptr(iters_out), _ptr(rel_resid_out),
+                                         _ptr(outcome_out), _stream(stream)))
+    return x_out
+
+
+def sense_rss(plan, y, lines, out, stream=None):
+    _check(load_library().sense_rss(plan.handle, _ptr(y), _ptr(lines), _ptr(out), _stream(stream)))
+    return out
+
+
+def sense_c32_to_bf16(inp, out, stream=None):
+    count = inp.numel()
+    _check(load_library().sense_c32_to_bf16(_ptr(inp), _ptr(out), count, _stream(stream)))
+    return out
+
+
+def sense_plan_check(plan, stream=None):
+    _check(load_library().sense_plan_check(plan.handle, _stream(stream)))
+
+
+def to_bf16_pairs(t, stream=None):
+    """complex64 CUDA tensor -> bfloat16 [..., 2] tensor (RNE, in the library's kernel)."""
+    out = torch.empty(tuple(t.shape) + (2,), dtype=torch.bfloat16, device=t.device)
+    return sense_c32_to_bf16(t.contiguous(), out, stream)

@@ -1,0 +1,73 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, and
+exports every entry point include/sense.h declares; host-only calls behave."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1807_11830_gb300 import build as sense_build
+from paper_1807_11830_gb300 import sense
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(sense_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = sense_build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_operator_calls():
+    names = declared_entry_points()
+    for required in ("sense_forward", "sense_adjoint", "sense_normal", "sense_cg_solve", "sense_plan_create",
+                     "sense_plan_destroy", "sense_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in sorted(declared_entry_points()):
+        assert hasattr(lib, name), "libsense.so does not export %s" % name
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(sense.EXPORTED) <= declared_entry_points() | {"sense_plan_workspace_bytes"}
+    for name in declared_entry_points():
+        assert name in sense.EXPORTED or name.startswith("sense_queue") or name.startswith("sense_sched"), name
+
+
+def test_size_table_is_host_only(lib):
+    lib.sense_size_supported.restype = ctypes.c_int
+    for n in (8, 12, 16, 20, 32, 64, 96, 128, 160, 192, 256, 320, 384):
+        assert lib.sense_size_supported(n) == 1
+    for n in (0, 7, 100, 512, 1000):
+        assert lib.sense_size_supported(n) == 0
+
+
+def test_null_arguments_rejected_without_device(lib):
+    lib.sense_plan_create.restype = ctypes.c_int
+    lib.sense_plan_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    lib.sense_last_error.restype = ctypes.c_char_p
+    out = ctypes.c_void_p()
+    assert lib.sense_plan_create(None, 0, ctypes.byref(out)) == 1  # SENSE_EINVAL
+    assert b"NULL" in lib.sense_last_error()
+    bad = sense._Shape(100, 100, 4, 1, 10, 0)
+    assert lib.sense_plan_create(ctypes.byref(bad), 0, ctypes.byref(out)) == 2  # unsupported size
+    lib.sense_forward.restype = ctypes.c_int
+    lib.sense_forward.argtypes = [ctypes.c_void_p] * 6
+    assert lib.sense_forward(None, None, None, None, None, None) == 1
+
+
+def test_built_for_sm_103a(lib):
+    log = open(os.path.join(ROOT, "_build", "ptxas.log")).read()
+    assert "sm_103a" in log

@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path against the FP64 oracle, element by element.
+
+Tolerances (relative L2 over the whole output): 1e-5 per operator
+application in FP32 arithmetic, 1e-4 on the CG image after a fixed number of
+iterations.  Shapes span several column tiles, ragged tails (nx smaller than
+or not a multiple of the tile width), one line, all lines, non-square
+images and every compiled transform length.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1807_11830_gb300 import sense, synth
+from tests.gpu_util import (CG_TOL, OP_TOL, ensure_built, gpu_adjoint, gpu_cg, gpu_forward, gpu_normal, gpu_rss,
+                            i32, c64, make_plan, rel)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+# (ny, nx, coils, lines, frames)
+OP_SHAPES = [
+    (8, 8, 2, 3, 2),
+    (12, 20, 3, 5, 1),
+    (16, 12, 2, 16, 2),
+    (20, 16, 3, 1, 1),
+    (32, 96, 3, 11, 2),
+    (64, 64, 4, 21, 1),
+    (96, 160, 2, 30, 1),
+    (128, 192, 3, 40, 2),
+    (160, 160, 8, 160, 1),
+    (192, 128, 5, 48, 2),
+    (256, 256, 12, 64, 2),
+    (320, 320, 4, 107, 1),
+    (384, 384, 3, 64, 1),
+    (256, 320, 3, 50, 1),
+    (384, 8, 2, 96, 1),
+]
+
+
+def _problem(shape, seed):
+    ny, nx, C, L, F = shape
+    rng = synth.rng_for(seed)
+    S = synth.sensitivities(C, ny, nx)
+    lines = synth.mask_lines(ny, L, min(4, L), F, rng)
+    x = synth.random_complex((F, ny, nx), rng)
+    y = synth.random_complex((F, C, L, nx), rng)
+    return x, S, lines, y
+
+
+@pytest.mark.parametrize("shape", OP_SHAPES, ids=lambda s: "%dx%d_c%d_l%d_f%d" % s)
+def test_forward(shape):
+    x, S, lines, _ = _problem(shape, 1000 + sum(shape))
+    S32 = S.astype(np.complex64).astype(np.complex128)
+    x32 = x.astype(np.complex64).astype(np.complex128)
+    assert rel(gpu_forward(x, S, lines), oracle.forward(x32, S32, lines)) <= OP_TOL
+
+
+@pytest.mark.parametrize("shape", OP_SHAPES, ids=lambda s: "%dx%d_c%d_l%d_f%d" % s)
+def test_adjoint(shape):
+    _, S, lines, y = _problem(shape, 2000 + sum(shape))
+    S32 = S.astype(np.complex64).astype(np.complex128)
+    y32 = y.astype(np.complex64).astype(np.complex128)
+    assert rel(gpu_adjoint(y, S, lines), oracle.adjoint(y32, S32, lines)) <= OP_TOL
+
+
+@pytest.mark.parametrize("shape", OP_SHAPES, ids=lambda s: "%dx%d_c%d_l%d_f%d" % s)
+def test_normal(shape):
+    x, S, lines, _ = _problem(shape, 3000 + sum(shape))
+    S32 = S.astype(np.complex64).astype(np.complex128)
+    x32 = x.astype(np.complex64).astype(np.complex128)
+    assert rel(gpu_normal(x, S, lines), oracle.normal(x32, S32, lines)) <= OP_TOL
+
+
+def _as32(a):
+    return a.astype(np.complex64).astype(np.complex128)
+
+
+def test_eq1_fully_sampled_coil_combine():
+    """Eq. 1 of the paper: with every line sampled the adjoint is
+    M = sum_i S_i^* F^-1(Y_i); with sum|S|^2 = 1 and Y = E x it returns x."""
+    p = synth.single_slice_64()
+    n = 64
+    lines = synth.full_lines(n, 1)
+    y = oracle.forward(p.x_true, p.S, lines)
+    m = gpu_adjoint(y, p.S, lines)
+    assert rel(m, oracle.adjoint(_as32(y), _as32(p.S), lines)) <= OP_TOL
+    assert rel(m, p.x_true) <= 1e-5
+
+
+def test_cg_single_slice_64():
+    p = synth.single_slice_64()
+    y = oracle.forward(p.x_true, p.S, p.lines) + p.noise
+    xo, io, ro, so = oracle.cg(_as32(y), _as32(p.S), p.lines, p.iters)
+    xg, ig, rg, sg = gpu_cg(y, p.S, p.lines, p.iters)
+    assert rel(xg, xo) <= CG_TOL
+    np.testing.assert_array_equal(ig, io)
+    np.testing.assert_array_equal(sg, so)
+    np.testing.assert_allclose(rg, ro, rtol=1e-3)
+
+
+def test_cg_cine_two_frames():
+    p = synth.cine_256(frames=20)
+    sel = [0, 13]
+    x_true = p.x_true[sel]
+    lines = p.lines[sel]
+    y = oracle.forward(x_true, p.S, lines) + p.noise[sel]
+    xo, io, ro, so = oracle.cg(_as32(y), _as32(p.S), lines, p.iters)
+    xg, ig, rg, sg = gpu_cg(y, p.S, lines, p.iters)
+    assert rel(xg, xo) <= CG_TOL
+    np.testing.assert_array_equal(ig, io)
+    np.testing.assert_array_equal(sg, so)
+
+
+def test_cg_stops_at_tolerance():
+    p = synth.single_slice_64()
+    y = oracle.forward(p.x_true, p.S, p.lines) + p.noise
+    tol = 3e-3
+    xo, io, ro, so = oracle.cg(_as32(y), _as32(p.S), p.lines, 100, tol)
+    xg, ig, rg, sg = gpu_cg(y, p.S, p.lines, 100, tol)
+    assert so[0] == sg[0] == sense.CG_CONVERGED
+    assert rg[0] <= tol and ro[0] <= tol
+    assert abs(int(ig[0]) - int(io[0])) <= 1
+    if ig[0] == io[0]:
+        assert rel(xg, xo) <= CG_TOL
+
+
+def test_cg_one_step_exact_recovery():
+    """Full sampling and sum|S|^2 = 1 make E^H E = I: one CG step returns x."""
+    rng = synth.rng_for(5)
+    n, C = 64, 4
+    S = synth.sensitivities(C, n, n)
+    lines = synth.full_lines(n, 2)
+    x = synth.phantom(n, n, 10, rng, frames=2)
+    y = oracle.forward(x, S, lines)
+    x1, it, rr, oc = gpu_cg(y, S, lines, 1)
+    assert rel(x1, x) <= 1e-5 and list(it) == [1, 1]
+    xs, it, rr, oc = gpu_cg(y, S, lines, 10, tol=1e-4)
+    assert list(it) == [1, 1] and list(oc) == [sense.CG_CONVERGED] * 2 and np.all(rr <= 1e-4)
+    assert rel(xs, x) <= 1e-5
+
+
+def test_cg_zero_frame_and_independence():
+    p = synth.cine_256(frames=3)
+    y = oracle.forward(p.x_true, p.S, p.lines) + p.noise
+    y[1] = 0.0
+    xg, ig, rg, sg = gpu_cg(y, p.S, p.lines, 6)
+    assert ig[1] == 0 and sg[1] == sense.CG_CONVERGED and rg[1] == 0.0
+    assert np.all(xg[1] == 0)
+    # frame 2 alone gives the same bits as frame 2 inside the batch
+    xa, ia, ra, sa = gpu_cg(y[2:3], p.S, p.lines[2:3], 6)
+    np.testing.assert_array_equal(xa[0], xg[2])
+    assert ia[0] == ig[2] == 6 and sa[0] == sense.CG_MAXITER
+
+
+def test_cg_reuses_captured_graph():
+    p = synth.single_slice_64()
+    y = oracle.forward(p.x_true, p.S, p.lines) + p.noise
+    plan = make_plan(p.S, p.lines)
+    a = gpu_cg(y, p.S, p.lines, 10, plan=plan)
+    b = gpu_cg(y, p.S, p.lines, 10, plan=plan)
+    np.testing.assert_array_equal(a[0], b[0])
+
+
+def test_bad_lines_are_flagged():
+    x, S, lines, y = _problem((32, 32, 2, 8, 1), 7)
+    plan = make_plan(S, lines)
+    bad = lines.copy()
+    bad[0, 3] = 40  # outside [0, ny)
+    out = torch.empty((1, 32, 32), dtype=torch.complex64, device="cuda:0")
+    sense.sense_normal(plan, c64(x), c64(S), i32(bad), out)
+    with pytest.raises(sense.SenseError) as ei:
+        sense.sense_plan_check(plan)
+    assert ei.value.status == 9
+    unsorted = lines.copy()
+    unsorted[0, [2, 3]] = unsorted[0, [3, 2]]
+    sense.sense_adjoint(plan, c64(y), c64(S), i32(unsorted), out)
+    with pytest.raises(sense.SenseError):
+        sense.sense_plan_check(plan)
+    sense.sense_plan_check(plan)  # flags were cleared
+
+
+def test_argument_errors():
+    x, S, lines, y = _problem((32, 32, 2, 8, 1), 8)
+    plan = make_plan(S, lines)
+    xt = c64(x)
+    with pytest.raises(sense.SenseError) as ei:
+        sense.sense_normal(plan, xt, c64(S), i32(lines), xt)  # out aliases x
+    assert ei.value.status == 1
+    with pytest.raises(sense.SenseError) as ei:
+        sense.Plan(100, 100, 2, 1, 10)
+    assert ei.value.status == 2
+
+
+@pytest.mark.parametrize("shape", [(160, 160, 8, 160, 2), (64, 96, 3, 21, 2)])
+def test_rss(shape):
+    _, S, lines, y = _problem(shape, 4000 + sum(shape))
+    ny = shape[0]
+    assert rel(gpu_rss(y, lines, ny), oracle.rss(_as32(y), lines, ny)) <= OP_TOL
