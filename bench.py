@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Benchmark of CG-SENSE on the cine workload (one JSON line on rank 0).
+
+Workload (one "step"): a CG-SENSE reconstruction of a 256x256 cine series,
+20 frames, 12 coils, acceleration 4 (64 of 256 phase-encode lines per frame,
+16 of them centre lines, a fresh line pattern per frame), 30 CG iterations
+per frame from x0 = 0: the adjoint E^H y, then 30 x (E^H E p, CG scalars,
+fused x/r update), all in libsense.so.  Inputs are seeded synthetic
+phantoms, coil maps and masks; k-space is E x plus complex Gaussian noise.
+
+Metric: E^H E applications per second (one application = one normal-operator
+product for one frame).  `value` times the steps with inputs resident in
+HBM; `e2e` times the same call with the inputs copied from pinned host
+memory and the image copied back inside the timed region.  L2 is flushed
+(a 512 MiB write) before every timed step.
+
+With --gpus N under torchrun, each rank runs an independent replica of the
+workload on its own GPU (the problems do not exchange data; weak scaling);
+the step time is the maximum over ranks.  ``--impl reference`` times the
+FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FRAMES, COILS, N, ACCEL, CENTRE, ITERS = 20, 12, 256, 4, 16, 30
+WORKLOAD = "cine 256x256, 20 frames, 12 coils, R=4 (64 lines, 16 centre), 30 CG-SENSE iterations"
+METRIC = "E^H·E applications/s"
+UNIT = "applications/s"
+FLUSH_BYTES = 512 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-iters", type=int, default=6)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def base_config(world):
+    return {
+        "workload": WORKLOAD, "ny": N, "nx": N, "frames": FRAMES, "coils": COILS, "lines": N // ACCEL,
+        "centre_lines": CENTRE, "cg_iterations": ITERS, "storage": "complex64",
+        "l2": "flushed before every timed step (512 MiB device write)",
+        "parallelism": "replicas x%d (independent problems, no collective)" % world,
+    }
+
+
+# ---------------------------------------------------------------------------
+# CPU side: the FP64 oracle on a bounded sample (reference arm / cpu_baseline)
+# ---------------------------------------------------------------------------
+_ORACLE_INPUTS = {}
+
+
+def oracle_inputs():
+    """k-space of the whole workload made once by the oracle's E (untimed)."""
+    if not _ORACLE_INPUTS:
+        import oracle
+        from paper_1807_11830_gb300 import synth
+
+        p = synth.cine_256(frames=FRAMES)
+        S = p.S.astype(np.complex64).astype(np.complex128)
+        y = oracle.forward(p.x_true.astype(np.complex64), S, p.lines) + p.noise
+        _ORACLE_INPUTS.update(y=y, S=S, lines=p.lines)
+    return _ORACLE_INPUTS
+
+
+def oracle_sample(frames, iters, seed_offset=0):
+    """Time oracle CG-SENSE on `frames` frames of the workload for `iters`
+    iterations.  Returns (applications/s, wall seconds, threads)."""
+    import oracle
+
+    d = oracle_inputs()
+    sel = [(i + seed_offset) % FRAMES for i in range(frames)]
+    y, S, lines = d["y"][sel], d["S"], d["lines"][sel]
+    t0 = time.perf_counter()
+    oracle.cg(y, S, lines, iters)
+    wall = time.perf_counter() - t0
+    return frames * iters / wall, wall, min(oracle.threads(), frames)
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    threads = oracle.threads()
+    frames = max(1, min(FRAMES, threads))
+    iters = 2
+    for _ in range(args.warmup):
+        oracle_sample(frames, 1)
+    walls = []
+    apps = 0
+    for k in range(args.steps):
+        _, wall, _ = oracle_sample(frames, iters, seed_offset=k)
+        walls.append(wall)
+        apps += frames * iters
+    total = sum(walls)
+    value = apps / total
+    sample = "%d of %d frames x %d CG iterations per step (full 256x256, 12 coils, R=4)" % (frames, FRAMES, iters)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": base_config(1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(threads, frames), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [v.strip() for v in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [s for t, s in self.samples if t0 <= t <= t1]
+        window = "timed region"
+        if len(rows) < 2:  # short timed region: widen to the loaded period around it
+            rows = [s for t, s in self.samples if t0 - 2.0 <= t <= t1 + 0.5]
+            window = "timed region +- load around it"
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        sm, smax, pw = [], [], []
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+                pw.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(rows),
+                "window": window}
+
+
+# ---------------------------------------------------------------------------
+# GPU side
+# ---------------------------------------------------------------------------
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1807_11830_gb300 import build as sense_build
+    from paper_1807_11830_gb300 import sense, synth
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if not os.path.exists(sense.LIB_PATH):
+        sense_build.build()
+    sense.load_library()
+
+    # ---- inputs (seeded; k-space made on the device by the library's E) ----
+    p = synth.cine_256(frames=FRAMES)
+    L = p.lines.shape[1]
+    x_true = torch.from_numpy(p.x_true.astype(np.complex64)).to(dev)
+    S = torch.from_numpy(p.S.astype(np.complex64)).to(dev)
+    lines = torch.from_numpy(p.lines).to(dev)
+    plan = sense.Plan(N, N, COILS, FRAMES, L, device=local_rank)
+    y = torch.empty((FRAMES, COILS, L, N), dtype=torch.complex64, device=dev)
+    sense.sense_forward(plan, x_true, S, lines, y)
+    y += torch.from_numpy(p.noise.astype(np.complex64)).to(dev)
+    x = torch.empty((FRAMES, N, N), dtype=torch.complex64, device=dev)
+    iters = torch.zeros(FRAMES, dtype=torch.int32, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        sense.sense_cg_solve(plan, y, S, lines, ITERS, 0.0, x, iters, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    sense.sense_plan_check(plan)
+    if int(iters.min()) != ITERS:
+        raise RuntimeError("CG did not run %d iterations per frame" % ITERS)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+
+    # ---- device-resident timed region ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    t_wall0 = time.time()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    barrier()
+    t_wall1 = time.time()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+
+    # ---- end to end: pinned host inputs in, image out, inside the timed region ----
+    y_h = y.cpu().pin_memory()
+    S_h = S.cpu().pin_memory()
+    lines_h = lines.cpu().pin_memory()
+    x_h = torch.empty(x.shape, dtype=x.dtype).pin_memory()
+    y_d = torch.empty_like(y)
+    S_d = torch.empty_like(S)
+    lines_d = torch.empty_like(lines)
+
+    def e2e_step():
+        y_d.copy_(y_h, non_blocking=True)
+        S_d.copy_(S_h, non_blocking=True)
+        lines_d.copy_(lines_h, non_blocking=True)
+        sense.sense_cg_solve(plan, y_d, S_d, lines_d, ITERS, 0.0, x, iters, stream=stream)
+        x_h.copy_(x, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        e_starts[k].record(stream)
+        e2e_step()
+        e_ends[k].record(stream)
+    barrier()
+    clocks.stop()
+    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends))
+    h2d = y.numel() * 8 + S.numel() * 8 + lines.numel() * 4
+    d2h = x.numel() * 8
+
+    # ---- kernel roofline: the same step with the plan's event timers on ----
+    sense.sense_plan_set_timing(plan, True)
+    for _ in range(5):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize(dev)
+    phase = {}
+    for name in sense.PHASES:
+        ms, n = sense.sense_plan_phase_time(plan, name)
+        if n:
+            phase[name] = {"ms_per_launch": ms / n, "launches": n, "ms_total": ms}
+    sense.sense_plan_set_timing(plan, False)
+
+    # max over ranks
+    tot = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
+    total_ms, e2e_ms = float(tot[0]), float(tot[1])
+
+    apps_per_step = FRAMES * ITERS
+    value = apps_per_step * world * args.steps / (total_ms / 1e3)
+    e2e_value = apps_per_step * world * args.steps / (e2e_ms / 1e3)
+
+    if rank == 0:
+        hbm_gbs, sm_max_mhz, peak_src = peaks()
+        img = N * N
+        # dominant kernel: E^H E inside CG.  Algorithmic work per launch (all 20 frames):
+        #   flops = C * F * (2 * Nx * 5 Ny log2 Ny + 14 Ny Nx)   (5 n log2 n per length-n transform)
+        #   bytes = 8 * img * (C + 4 F)   (S once; r, p read; p, q written per frame)
+        cgn = phase.get("cg_normal", {})
+        dur_s = cgn.get("ms_per_launch", float("nan")) / 1e3
+        flops = COILS * FRAMES * (2 * N * 5 * N * np.log2(N) + 14 * img)
+        bytes_ = 8 * img * (COILS + 4 * FRAMES)
+        alu_peak_tflops = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+        achieved_tflops = flops / dur_s / 1e12
+        roofline = {
+            "kernel": "k_normal (CG mode)", "bound": "alu", "achieved": achieved_tflops, "peak": alu_peak_tflops,
+            "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak_tflops, "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max)" % (sm_max_mhz, peak_src),
+            "algorithmic_gflop_per_launch": flops / 1e9, "algorithmic_mb_per_launch": bytes_ / 1e6,
+            "hbm_achieved_gbs": bytes_ / dur_s / 1e9, "hbm_peak_gbs": hbm_gbs,
+            "hbm_frac": bytes_ / dur_s / 1e9 / hbm_gbs, "duration_us": dur_s * 1e6,
+        }
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            frames = max(1, min(FRAMES, oracle.threads()))
+            v, wall, cores = oracle_sample(frames, args.cpu_sample_iters)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "%d of %d frames x %d CG iterations (full 256x256, 12 coils, R=4), %.1f s"
+                             % (frames, FRAMES, args.cpu_sample_iters, wall)}
+        launches_per_step = 2 + 2 * ITERS + 1
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": base_config(world),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": e2e_ms / args.steps},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary(t_wall0, t_wall1),
+            "kernels_us": {k: round(v["ms_per_launch"] * 1e3, 2) for k, v in phase.items()},
+            "step_ms_p50": statistics.median(step_ms), "step_ms_min": min(step_ms),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    plan.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -144,6 +144,30 @@ sense_status sense_c32_to_bf16(const sense_c32* in, void* out, size_t count, voi
  * gave up).  Clears the flags. */
 sense_status sense_plan_check(sense_plan* plan, void* stream);
 
+/* Kernel phases timed by the plan's event timers. */
+typedef enum {
+  SENSE_PHASE_ROWS_FWD = 0, /* E, x-direction pass */
+  SENSE_PHASE_ROWS_INV = 1, /* E^H, x-direction pass */
+  SENSE_PHASE_FWD_COL = 2,  /* E, y-direction pass with S and the line mask */
+  SENSE_PHASE_ADJ_COL = 3,  /* E^H, y-direction pass with conj(S) and the coil sum (also CG start, RSS) */
+  SENSE_PHASE_NORMAL = 4,   /* E^H E (sense_normal) */
+  SENSE_PHASE_CG_NORMAL = 5,/* E^H E inside CG, with the p update and Re<p,q> */
+  SENSE_PHASE_CG_UPDATE = 6,/* CG x/r update with <r,r> */
+  SENSE_PHASE_COUNT = 7
+} sense_phase;
+
+/* Turn the plan's kernel timers on (1) or off (0); either way the totals
+ * are reset.  While on, every launch of the plan is bracketed by a pair of
+ * CUDA events recorded on the launching stream, and sense_cg_solve launches
+ * its iterations directly instead of replaying a CUDA graph.  Timing is a
+ * diagnostic mode: it adds event records between kernels. */
+sense_status sense_plan_set_timing(sense_plan* plan, int on);
+
+/* Wait for the timed launches and return, for `phase`, the summed kernel
+ * time in milliseconds and the number of launches since timing was turned
+ * on.  Either output may be NULL. */
+sense_status sense_plan_phase_time(sense_plan* plan, int phase, double* ms_total, long* launches);
+
 /* Message describing the last non-OK status returned on this thread. */
 const char* sense_last_error(void);
 

@@ -84,6 +84,12 @@ struct sense_plan {
   size_t ws_bytes = 0;
   std::vector<void*> allocs;
   cudaStream_t capture_stream = nullptr;
+  // kernel timers (diagnostic mode): event pairs per launch, summed per phase
+  int timing = 0;
+  double phase_ms[SENSE_PHASE_COUNT] = {};
+  long phase_launches[SENSE_PHASE_COUNT] = {};
+  struct Span { int phase; cudaEvent_t a, b; };
+  std::vector<Span> pending;
   // CUDA graphs of the CG iteration loop, keyed by the arguments they bake in
   std::map<std::tuple<const void*, const void*, const void*, int, int, double>, cudaGraphExec_t> graphs;
 
@@ -110,6 +116,43 @@ struct sense_plan {
 
 namespace {
 
+// Brackets one launch with a pair of events on `st` when the plan's timers
+// are on.
+class PhaseScope {
+ public:
+  PhaseScope(sense_plan* pl, int phase, cudaStream_t st) : pl_(pl), st_(st) {
+    if (!pl->timing) return;
+    span_.phase = phase;
+    if (cudaEventCreate(&span_.a) != cudaSuccess || cudaEventCreate(&span_.b) != cudaSuccess) return;
+    cudaEventRecord(span_.a, st_);
+    on_ = true;
+  }
+  ~PhaseScope() {
+    if (!on_) return;
+    cudaEventRecord(span_.b, st_);
+    pl_->pending.push_back(span_);
+  }
+
+ private:
+  sense_plan* pl_;
+  cudaStream_t st_;
+  sense_plan::Span span_{};
+  bool on_ = false;
+};
+
+void collect_spans(sense_plan* pl) {
+  for (auto& sp : pl->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(sp.b) == cudaSuccess && cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
+      pl->phase_ms[sp.phase] += ms;
+      pl->phase_launches[sp.phase] += 1;
+    }
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
+  pl->pending.clear();
+}
+
 template <class T>
 sense_status dalloc(sense_plan* pl, T** out, size_t count) {
   void* ptr = nullptr;
@@ -126,6 +169,7 @@ sense_status dalloc(sense_plan* pl, T** out, size_t count) {
 }
 
 void release(sense_plan* pl) {
+  collect_spans(pl);
   for (auto& kv : pl->graphs) cudaGraphExecDestroy(kv.second);
   pl->graphs.clear();
   for (void* ptr : pl->allocs) cudaFree(ptr);
@@ -173,13 +217,18 @@ sense_status run_forward(sense_plan* pl, const float2* x, const void* S, const i
   a.coils = sh.coils;
   a.L = sh.lines;
   a.err = pl->err();
-  sense_status rc = launch_status(launch_fwd_col<St>(sh.ny, a, pl->tiles, sh.frames, st), "forward column pass");
+  sense_status rc;
+  {
+    PhaseScope ps(pl, SENSE_PHASE_FWD_COL, st);
+    rc = launch_status(launch_fwd_col<St>(sh.ny, a, pl->tiles, sh.frames, st), "forward column pass");
+  }
   if (rc != SENSE_OK) return rc;
   RowArgs<float2, typename St::T> ra{};
   ra.in = pl->tmp;
   ra.out = static_cast<typename St::T*>(y);
   ra.tw = pl->tw_x;
   ra.rows = (long)sh.frames * sh.coils * sh.lines;
+  PhaseScope ps(pl, SENSE_PHASE_ROWS_FWD, st);
   return launch_status(launch_rows_fwd<St>(sh.nx, ra, st), "forward row pass");
 }
 
@@ -191,6 +240,7 @@ sense_status run_rows_inv(sense_plan* pl, const void* y, cudaStream_t st) {
   ra.out = pl->tmp;
   ra.tw = pl->tw_x;
   ra.rows = (long)sh.frames * sh.coils * sh.lines;
+  PhaseScope ps(pl, SENSE_PHASE_ROWS_INV, st);
   return launch_status(launch_rows_inv<St>(sh.nx, ra, st), "adjoint row pass");
 }
 
@@ -211,6 +261,7 @@ sense_status run_adjoint(sense_plan* pl, int mode, const void* y, const void* S,
     a.L = sh.lines;
     a.tiles = pl->tiles;
     a.err = pl->err();
+    PhaseScope ps(pl, SENSE_PHASE_ADJ_COL, st);
     return launch_status(launch_adj_col<StC64>(sh.ny, 2, a, pl->tiles, sh.frames, st), "rss column pass");
   }
   AdjColArgs<St> a{};
@@ -227,6 +278,7 @@ sense_status run_adjoint(sense_plan* pl, int mode, const void* y, const void* S,
   a.tiles = pl->tiles;
   a.err = pl->err();
   a.cg = pl->cg(tol);
+  PhaseScope ps(pl, SENSE_PHASE_ADJ_COL, st);
   return launch_status(launch_adj_col<St>(sh.ny, mode, a, pl->tiles, sh.frames, st), "adjoint column pass");
 }
 
@@ -245,6 +297,7 @@ sense_status run_normal(sense_plan* pl, const float2* x, const void* S, const in
   a.L = sh.lines;
   a.tiles = pl->tiles;
   a.err = pl->err();
+  PhaseScope ps(pl, SENSE_PHASE_NORMAL, st);
   return launch_status(launch_normal<St>(sh.ny, false, a, pl->tiles, sh.frames, st), "normal operator");
 }
 
@@ -268,7 +321,11 @@ sense_status run_cg_iteration(sense_plan* pl, const void* S, const int* lines, f
   a.p_update = p_update;
   a.err = pl->err();
   a.cg = pl->cg(tol);
-  sense_status rc = launch_status(launch_normal<St>(sh.ny, true, a, pl->tiles, sh.frames, st), "CG normal pass");
+  sense_status rc;
+  {
+    PhaseScope ps(pl, SENSE_PHASE_CG_NORMAL, st);
+    rc = launch_status(launch_normal<St>(sh.ny, true, a, pl->tiles, sh.frames, st), "CG normal pass");
+  }
   if (rc != SENSE_OK) return rc;
   UpdateArgs u{};
   u.x = reinterpret_cast<float4*>(x);
@@ -278,6 +335,7 @@ sense_status run_cg_iteration(sense_plan* pl, const void* S, const int* lines, f
   u.img4 = (long)(pl->img / 2);
   u.blocks_per_frame = pl->upd_blocks;
   u.cg = pl->cg(tol);
+  PhaseScope ps(pl, SENSE_PHASE_CG_UPDATE, st);
   k_cg_update<<<dim3(pl->upd_blocks, sh.frames), UPD_THREADS, 0, st>>>(u);
   return launch_status(cudaGetLastError(), "CG update");
 }
@@ -297,6 +355,7 @@ sense_status run_cg_chunk(sense_plan* pl, const void* S, const int* lines, float
 template <class St>
 sense_status cg_chunk_graph(sense_plan* pl, const void* S, const int* lines, float2* x, int first, int count,
                             double tol, cudaStream_t st) {
+  if (pl->timing) return run_cg_chunk<St>(pl, S, lines, x, first, count, tol, st);
   const int first_key = first > 0 ? 1 : 0;
   auto key = std::make_tuple(S, (const void*)lines, (const void*)x, first_key, count, tol);
   auto it = pl->graphs.find(key);
@@ -498,6 +557,28 @@ sense_status sense_c32_to_bf16(const sense_c32* in, void* out, size_t count, voi
   k_to_bf16<<<blocks, 256, 0, as_stream(stream)>>>(reinterpret_cast<const float2*>(in),
                                                     static_cast<__nv_bfloat162*>(out), count);
   return launch_status(cudaGetLastError(), "bf16 conversion");
+}
+
+sense_status sense_plan_set_timing(sense_plan* pl, int on) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  DeviceGuard guard(pl->device);
+  collect_spans(pl);
+  pl->timing = on ? 1 : 0;
+  for (int i = 0; i < SENSE_PHASE_COUNT; ++i) {
+    pl->phase_ms[i] = 0.0;
+    pl->phase_launches[i] = 0;
+  }
+  return SENSE_OK;
+}
+
+sense_status sense_plan_phase_time(sense_plan* pl, int phase, double* ms_total, long* launches) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (phase < 0 || phase >= SENSE_PHASE_COUNT) return fail(SENSE_EINVAL, "phase out of range");
+  DeviceGuard guard(pl->device);
+  collect_spans(pl);
+  if (ms_total) *ms_total = pl->phase_ms[phase];
+  if (launches) *launches = pl->phase_launches[phase];
+  return SENSE_OK;
 }
 
 sense_status sense_plan_check(sense_plan* pl, void* stream) {

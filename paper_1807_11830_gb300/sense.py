@@ -32,8 +32,10 @@ CG_CONVERGED, CG_MAXITER, CG_BREAKDOWN = 1, 2, 3
 EXPORTED = (
     "sense_size_supported", "sense_plan_create", "sense_plan_destroy", "sense_plan_workspace_bytes",
     "sense_forward", "sense_adjoint", "sense_normal", "sense_cg_solve", "sense_rss", "sense_c32_to_bf16",
-    "sense_plan_check", "sense_last_error",
+    "sense_plan_check", "sense_last_error", "sense_plan_set_timing", "sense_plan_phase_time",
 )
+
+PHASES = ("rows_fwd", "rows_inv", "fwd_col", "adj_col", "normal", "cg_normal", "cg_update")
 
 
 class SenseError(RuntimeError):
@@ -78,6 +80,10 @@ def load_library(path=LIB_PATH):
     lib.sense_c32_to_bf16.restype = st
     lib.sense_plan_check.argtypes = [vp, vp]
     lib.sense_plan_check.restype = st
+    lib.sense_plan_set_timing.argtypes = [vp, i]
+    lib.sense_plan_set_timing.restype = st
+    lib.sense_plan_phase_time.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)]
+    lib.sense_plan_phase_time.restype = st
     lib.sense_last_error.argtypes = []
     lib.sense_last_error.restype = ctypes.c_char_p
     _LIB = lib
@@ -179,6 +185,19 @@ def sense_c32_to_bf16(inp, out, stream=None):
 
 def sense_plan_check(plan, stream=None):
     _check(load_library().sense_plan_check(plan.handle, _stream(stream)))
+
+
+def sense_plan_set_timing(plan, on):
+    _check(load_library().sense_plan_set_timing(plan.handle, 1 if on else 0))
+
+
+def sense_plan_phase_time(plan, phase):
+    """(summed kernel milliseconds, launches) of a phase name or index."""
+    idx = PHASES.index(phase) if isinstance(phase, str) else int(phase)
+    ms = ctypes.c_double()
+    n = ctypes.c_long()
+    _check(load_library().sense_plan_phase_time(plan.handle, idx, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def to_bf16_pairs(t, stream=None):
