@@ -108,6 +108,31 @@ sense_status sense_forward(sense_plan* plan, const sense_c32* x, const void* S, 
 sense_status sense_adjoint(sense_plan* plan, const void* y, const void* S, const int32_t* lines, sense_c32* x,
                            void* stream);
 
+/* Allocation-free adjoint (the paper has no counterpart; this is a deployment
+ * variant of sense_adjoint).  Some callers cannot allocate device memory --
+ * plugins inside a host application that owns all device memory through its
+ * own pool, processes whose device memory budget is fixed up front, and
+ * latency-critical loops that must stay out of the CUDA allocator (cudaMalloc
+ * and cudaFree can synchronise the device) -- so they cannot create a plan.
+ * This call computes the same x = E^H y as sense_adjoint for `shape` without a
+ * plan and without allocating: the row-pass intermediate lives in a fixed
+ * file-scope device array of 2^21 complex values (16 MiB) that every GPU
+ * which loads the library holds until the process exits, next to twiddle
+ * tables for every supported length.  The caller still passes y, S, lines and
+ * x (device pointers, layouts as above).
+ *   - frames*coils*lines*nx must not exceed 2^21; larger shapes return
+ *     SENSE_EINVAL with a message (use sense_adjoint with a plan instead).
+ *   - The first call on each device does a one-time set-up with that device
+ *     current (symbol addresses and a synchronous upload of the twiddle
+ *     tables); make that first call before any stream capture.
+ *   - Every call shares the one array and leaves its contents behind: calls
+ *     that overlap on the GPU (different streams, or different host threads)
+ *     race on it and must be serialised by the caller.
+ *   - Line-index errors are skipped by the kernels but not reported (there is
+ *     no plan to hold the flag); pass valid lines. */
+sense_status sense_adjoint_noalloc(const sense_shape* shape, const void* y, const void* S, const int32_t* lines,
+                                   sense_c32* x, void* stream);
+
 /* Normal operator out = E^H E x, per frame.  Computed column-wise: because the
  * mask acts on rows only and F_x is unitary, E^H E = sum_c S_c^H F_y^H M_f F_y S_c,
  * so no x-direction transform is needed.  `out` must not alias `x`. */

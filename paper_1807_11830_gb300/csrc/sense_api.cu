@@ -21,6 +21,15 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
+namespace sense {
+// Lets other units of the library report through sense_last_error().
+void record_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace sense
+
+namespace {
+
 sense_status fail(sense_status st, const std::string& msg) {
   g_last_error = msg;
   return st;

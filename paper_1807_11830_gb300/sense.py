@@ -33,6 +33,7 @@ EXPORTED = (
     "sense_size_supported", "sense_plan_create", "sense_plan_destroy", "sense_plan_workspace_bytes",
     "sense_forward", "sense_adjoint", "sense_normal", "sense_cg_solve", "sense_rss", "sense_c32_to_bf16",
     "sense_plan_check", "sense_last_error", "sense_plan_set_timing", "sense_plan_phase_time",
+    "sense_adjoint_noalloc",
 )
 
 PHASES = ("rows_fwd", "rows_inv", "fwd_col", "adj_col", "normal", "cg_normal", "cg_update")
@@ -84,6 +85,8 @@ def load_library(path=LIB_PATH):
     lib.sense_plan_set_timing.restype = st
     lib.sense_plan_phase_time.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)]
     lib.sense_plan_phase_time.restype = st
+    lib.sense_adjoint_noalloc.argtypes = [ctypes.POINTER(_Shape), vp, vp, vp, vp, vp]
+    lib.sense_adjoint_noalloc.restype = st
     lib.sense_last_error.argtypes = []
     lib.sense_last_error.restype = ctypes.c_char_p
     _LIB = lib
@@ -156,6 +159,17 @@ def sense_forward(plan, x, S, lines, y, stream=None):
 
 def sense_adjoint(plan, y, S, lines, x, stream=None):
     _check(load_library().sense_adjoint(plan.handle, _ptr(y), _ptr(S), _ptr(lines), _ptr(x), _stream(stream)))
+    return x
+
+
+def sense_adjoint_noalloc(shape, y, S, lines, x, stream=None):
+    """Adjoint without a plan and without device allocation (fixed-size
+    library scratch; see include/sense.h).  `shape` is a dict with ny, nx,
+    coils, frames, lines and optionally storage."""
+    sh = _Shape(shape["ny"], shape["nx"], shape["coils"], shape["frames"], shape["lines"],
+                shape.get("storage", STORE_C64))
+    _check(load_library().sense_adjoint_noalloc(ctypes.byref(sh), _ptr(y), _ptr(S), _ptr(lines), _ptr(x),
+                                                _stream(stream)))
     return x
 
 

@@ -71,3 +71,19 @@ def test_null_arguments_rejected_without_device(lib):
 def test_built_for_sm_103a(lib):
     log = open(os.path.join(ROOT, "_build", "ptxas.log")).read()
     assert "sm_103a" in log
+
+
+def test_noalloc_size_limit_checked_before_any_device_work(lib):
+    """sense_adjoint_noalloc rejects shapes beyond its fixed scratch (2^21
+    complex values) on the host, before any CUDA call, so no device is needed."""
+    lib.sense_adjoint_noalloc.restype = ctypes.c_int
+    lib.sense_adjoint_noalloc.argtypes = [ctypes.c_void_p] * 6
+    lib.sense_last_error.restype = ctypes.c_char_p
+    over = sense._Shape(256, 256, 32, 3, 128, 0)   # 3*32*128*256 = 3*2^20 > 2^21
+    assert lib.sense_adjoint_noalloc(ctypes.byref(over), None, None, None, None, None) == 1
+    assert b"exceeds" in lib.sense_last_error()
+    at_limit = sense._Shape(256, 256, 32, 2, 128, 0)  # exactly 2^21: size accepted, NULL pointers rejected
+    assert lib.sense_adjoint_noalloc(ctypes.byref(at_limit), None, None, None, None, None) == 1
+    assert b"aligned" in lib.sense_last_error()
+    bad_size = sense._Shape(100, 100, 2, 1, 10, 0)
+    assert lib.sense_adjoint_noalloc(ctypes.byref(bad_size), None, None, None, None, None) == 2
