@@ -164,6 +164,38 @@ sense_status sense_rss(sense_plan* plan, const void* y, const int32_t* lines, fl
  * round-to-nearest-even (for preparing S and y of a BF16 plan). */
 sense_status sense_c32_to_bf16(const sense_c32* in, void* out, size_t count, void* stream);
 
+/* How sense_cg_solve runs its iterations.
+ *   1 (default): one persistent launch runs every iteration of every frame.
+ *     Blocks take work items (a normal-operator column tile or an update
+ *     chunk of one frame and iteration) from a global ticket counter in a
+ *     fixed order; an item waits only for the previous phase of its own
+ *     frame, so frames pipeline and no kernel boundary separates phases.
+ *   0: two kernels per iteration (normal operator, update), captured once
+ *     per argument set into a CUDA graph and replayed.
+ * Both give the same iterates up to rounding of the inner products' partial
+ * sums (the per-tile and per-chunk partitions differ). */
+sense_status sense_plan_set_cg_mode(sense_plan* plan, int mode);
+
+/* Kernel variants.  Each transform length has one or more compiled variants
+ * of the normal-operator kernel (threads per column, columns per block,
+ * radix schedule, register cap).  A plan starts with variant 0.
+ * sense_plan_set_variant selects one (SENSE_EINVAL if it does not exist for
+ * the plan's ny); sense_plan_variant reports the current one. */
+sense_status sense_plan_set_variant(sense_plan* plan, int variant);
+int sense_plan_variant(const sense_plan* plan);
+
+/* Autotuner: time every variant of the normal-operator kernel on this plan's
+ * shape with the caller's S and lines (device pointers; the plan's own CG
+ * vectors serve as scratch input and output), keep the fastest and return it
+ * in *variant_out.  ms_out (may be NULL) receives the mean milliseconds per
+ * launch of each variant (kernel variants that do not exist get -1); it must
+ * hold 4 values.  Results are cached per (device, shape, storage) for the
+ * process, and appended to the file named by the environment variable
+ * SENSE_AUTOTUNE_CACHE when set (read back on first use).  A cached shape is
+ * not re-timed.  Synchronises `stream`. */
+sense_status sense_plan_autotune(sense_plan* plan, const void* S, const int32_t* lines, int* variant_out,
+                                 double* ms_out, void* stream);
+
 /* Synchronise `stream` and report errors the kernels flagged since the last
  * check (SENSE_EDEVICE for bad lines, SENSE_ETIMEOUT for a bounded wait that
  * gave up).  Clears the flags. */
@@ -178,7 +210,8 @@ typedef enum {
   SENSE_PHASE_NORMAL = 4,   /* E^H E (sense_normal) */
   SENSE_PHASE_CG_NORMAL = 5,/* E^H E inside CG, with the p update and Re<p,q> */
   SENSE_PHASE_CG_UPDATE = 6,/* CG x/r update with <r,r> */
-  SENSE_PHASE_COUNT = 7
+  SENSE_PHASE_CG_PERSISTENT = 7, /* all CG iterations in one persistent launch */
+  SENSE_PHASE_COUNT = 8
 } sense_phase;
 
 /* Turn the plan's kernel timers on (1) or off (0); either way the totals
@@ -192,6 +225,13 @@ sense_status sense_plan_set_timing(sense_plan* plan, int on);
  * time in milliseconds and the number of launches since timing was turned
  * on.  Either output may be NULL. */
 sense_status sense_plan_phase_time(sense_plan* plan, int phase, double* ms_total, long* launches);
+
+/* Self-test of the device-side bounded wait used by the persistent CG
+ * kernel: one thread polls a device flag that nothing sets, at most
+ * max_spins times (>= 64 ns apart; max_spins in [1, 2^20]), then gives up.
+ * Returns SENSE_ETIMEOUT when the wait gave up as designed (the expected
+ * outcome), anything else on failure.  The device stays usable. */
+sense_status sense_selftest_wait(int device, long max_spins);
 
 /* Message describing the last non-OK status returned on this thread. */
 const char* sense_last_error(void);

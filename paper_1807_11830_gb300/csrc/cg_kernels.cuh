@@ -1,7 +1,7 @@
 // CG vector update, CG finish and bf16 conversion kernels (host-launched by
 // the API unit only).
 #pragma once
-#include "common.cuh"
+#include "persistent.cuh"
 
 namespace sense {
 
@@ -29,22 +29,35 @@ __global__ void __launch_bounds__(UPD_THREADS) k_cg_update(UpdateArgs a) {
   __shared__ double red[32];
   const float al = (float)__ldg(a.cg.alpha + f);
   const size_t base = (size_t)f * a.img4;
+  float4* __restrict__ xp = a.x + base;
+  float4* __restrict__ rp = a.r + base;
+  const float4* __restrict__ pp = a.p + base;
+  const float4* __restrict__ qp = a.q + base;
+  // issue every load before any store so they are all in flight together
+  float4 xv[UPD_VEC], pv[UPD_VEC], qv[UPD_VEC], rv[UPD_VEC];
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < UPD_VEC; ++j) {
+    const long i = (long)blockIdx.x * (UPD_THREADS * UPD_VEC) + j * UPD_THREADS + threadIdx.x;
+    const bool ok = i < a.img4;
+    xv[j] = ok ? xp[i] : z;
+    pv[j] = ok ? __ldg(pp + i) : z;
+    qv[j] = ok ? __ldg(qp + i) : z;
+    rv[j] = ok ? rp[i] : z;
+  }
   float acc = 0.f;
 #pragma unroll
   for (int j = 0; j < UPD_VEC; ++j) {
     const long i = (long)blockIdx.x * (UPD_THREADS * UPD_VEC) + j * UPD_THREADS + threadIdx.x;
+    float4 xn = xv[j], rn = rv[j];
+    xn.x = fmaf(al, pv[j].x, xn.x); xn.y = fmaf(al, pv[j].y, xn.y);
+    xn.z = fmaf(al, pv[j].z, xn.z); xn.w = fmaf(al, pv[j].w, xn.w);
+    rn.x = fmaf(-al, qv[j].x, rn.x); rn.y = fmaf(-al, qv[j].y, rn.y);
+    rn.z = fmaf(-al, qv[j].z, rn.z); rn.w = fmaf(-al, qv[j].w, rn.w);
     if (i < a.img4) {
-      float4 xv = a.x[base + i];
-      const float4 pv = __ldg(a.p + base + i);
-      const float4 qv = __ldg(a.q + base + i);
-      float4 rv = a.r[base + i];
-      xv.x = fmaf(al, pv.x, xv.x); xv.y = fmaf(al, pv.y, xv.y);
-      xv.z = fmaf(al, pv.z, xv.z); xv.w = fmaf(al, pv.w, xv.w);
-      rv.x = fmaf(-al, qv.x, rv.x); rv.y = fmaf(-al, qv.y, rv.y);
-      rv.z = fmaf(-al, qv.z, rv.z); rv.w = fmaf(-al, qv.w, rv.w);
-      a.x[base + i] = xv;
-      a.r[base + i] = rv;
-      acc = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, acc))));
+      xp[i] = xn;
+      rp[i] = rn;
+      acc = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, acc))));
     }
   }
   const double tot = block_sum<UPD_THREADS>((double)acc, red);
@@ -78,6 +91,12 @@ __global__ void k_cg_finish(CgState g, int frames, int* iters_out, double* resid
   if (iters_out) iters_out[f] = g.iters[f];
   if (resid_out) resid_out[f] = g.resid[f];
   if (outcome_out) outcome_out[f] = oc;
+}
+
+// Self-test of the bounded wait: waits for a flag that nothing sets and
+// records whether the wait gave up (1) or saw the flag (0).
+__global__ void k_wait_selftest(const int* flag, long max_spins, int* timed_out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *timed_out = wait_at_least(flag, 1, max_spins) ? 0 : 1;
 }
 
 __global__ void k_to_bf16(const float2* in, __nv_bfloat162* out, size_t n) {

@@ -37,24 +37,55 @@ struct StBF16 {
 };
 
 // ---------------------------------------------------------------------------
-// transform configuration per length: Col<N1, N2, T, W>
-// (threads per block always a multiple of 32)
+// transform configuration per length: Col<T, W, Radices<...>>, each thread
+// holding about 8 values per stage (threads per block a multiple of 32)
 // ---------------------------------------------------------------------------
 template <int N>
 struct Cfg;
-template <> struct Cfg<8> { using C = Col<4, 2, 2, 16>; };
-template <> struct Cfg<12> { using C = Col<4, 3, 4, 16>; };
-template <> struct Cfg<16> { using C = Col<4, 4, 4, 16>; };
-template <> struct Cfg<20> { using C = Col<5, 4, 4, 16>; };
-template <> struct Cfg<32> { using C = Col<8, 4, 4, 32>; };
-template <> struct Cfg<64> { using C = Col<8, 8, 8, 32>; };
-template <> struct Cfg<96> { using C = Col<12, 8, 8, 32>; };
-template <> struct Cfg<128> { using C = Col<16, 8, 8, 32>; };
-template <> struct Cfg<160> { using C = Col<10, 16, 16, 16>; };
-template <> struct Cfg<192> { using C = Col<12, 16, 16, 16>; };
-template <> struct Cfg<256> { using C = Col<16, 16, 16, 16>; };
-template <> struct Cfg<320> { using C = Col<16, 20, 20, 16>; };
-template <> struct Cfg<384> { using C = Col<16, 24, 24, 16>; };
+template <> struct Cfg<8> { using C = Col<2, 16, Radices<4, 2>>; };
+template <> struct Cfg<12> { using C = Col<4, 16, Radices<4, 3>>; };
+template <> struct Cfg<16> { using C = Col<4, 16, Radices<4, 4>>; };
+template <> struct Cfg<20> { using C = Col<4, 16, Radices<5, 4>>; };
+template <> struct Cfg<32> { using C = Col<4, 32, Radices<8, 4>>; };
+template <> struct Cfg<64> { using C = Col<8, 32, Radices<8, 8>>; };
+template <> struct Cfg<96> { using C = Col<24, 16, Radices<4, 4, 6>>; };
+template <> struct Cfg<128> { using C = Col<16, 16, Radices<8, 4, 4>>; };
+template <> struct Cfg<160> { using C = Col<20, 16, Radices<8, 4, 5>>; };
+template <> struct Cfg<192> { using C = Col<24, 16, Radices<8, 3, 8>>; };
+template <> struct Cfg<256> { using C = Col<32, 16, Radices<8, 4, 8>>; };
+template <> struct Cfg<320> { using C = Col<40, 16, Radices<8, 4, 10>>; };
+template <> struct Cfg<384> { using C = Col<48, 16, Radices<8, 4, 12>>; };
+
+// Variants of the normal-operator kernel per length: V = 0 is Cfg<N>; the
+// others trade threads per column, tile width and a minimum number of
+// resident blocks (which caps registers).  The autotuner times the variants
+// that exist for a plan's length and keeps the fastest.
+template <int N, int V>
+struct NormCfg {
+  static constexpr bool exists = (V == 0);
+  using C = typename Cfg<N>::C;
+  static constexpr int MINB = 1;
+};
+#define SENSE_NORM_VARIANT(N_, V_, MINB_, ...)   \
+  template <>                                    \
+  struct NormCfg<N_, V_> {                       \
+    static constexpr bool exists = true;         \
+    using C = __VA_ARGS__;                       \
+    static constexpr int MINB = MINB_;           \
+  };
+SENSE_NORM_VARIANT(128, 1, 1, Col<8, 32, Radices<16, 8>>)
+SENSE_NORM_VARIANT(128, 2, 4, Col<16, 16, Radices<8, 4, 4>>)
+SENSE_NORM_VARIANT(192, 1, 1, Col<16, 16, Radices<12, 16>>)
+SENSE_NORM_VARIANT(192, 2, 2, Col<24, 16, Radices<8, 3, 8>>)
+SENSE_NORM_VARIANT(256, 1, 2, Col<32, 16, Radices<8, 4, 8>>)
+SENSE_NORM_VARIANT(256, 2, 1, Col<16, 16, Radices<16, 16>>)
+SENSE_NORM_VARIANT(256, 3, 4, Col<32, 8, Radices<8, 4, 8>>)
+SENSE_NORM_VARIANT(320, 1, 1, Col<20, 16, Radices<16, 20>>)
+SENSE_NORM_VARIANT(320, 2, 2, Col<40, 8, Radices<8, 4, 10>>)
+SENSE_NORM_VARIANT(384, 1, 1, Col<24, 16, Radices<16, 24>>)
+SENSE_NORM_VARIANT(384, 2, 2, Col<48, 8, Radices<8, 4, 12>>)
+#undef SENSE_NORM_VARIANT
+constexpr int kNormVariants = 4;
 
 #define SENSE_FOR_EACH_SIZE(X) \
   X(8) X(12) X(16) X(20) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(320) X(384)

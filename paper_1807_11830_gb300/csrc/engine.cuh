@@ -1,107 +1,244 @@
-// Two-level mixed-radix transform of W independent length-N sequences held
-// by one thread block ("columns" of a tile), N = N1 * N2.
+// Multi-stage mixed-radix transform of W independent length-N sequences
+// ("columns" of a tile) held by one thread block, N = R_0 R_1 ... R_{S-1}.
 //
-// Thread layout: THREADS = T * W.  Thread (t, c) with c = tid % W the
-// sequence (column) and t = tid / W its phase.  For W = 32 a warp is one t
-// across 32 adjacent columns, so every global access of a warp is one
-// contiguous 256-byte row segment and every shared access is one row.
+// Thread layout: THREADS = T * W.  Thread (t, c) with c = tid % W the column
+// and t = tid / W its phase.  With W = 16 a half-warp is one t across 16
+// adjacent columns, so every shared-memory access of a half-warp is one
+// 128-byte row (conflict-free) and every global access is a contiguous
+// row segment.
 //
-// Index split (Cooley-Tukey, N = N1 N2):
-//   sample n = N2*n1 + n2,   frequency k = k1 + N1*k2
-//   X[k1 + N1 k2] = sum_n2 w_N2^{n2 k2} w_N^{n2 k1} sum_n1 x[N2 n1 + n2] w_N1^{n1 k1}
-// Sample-side registers  xr[b][n1]: n2 = t + T*b  (B1 = ceil(N2/T) groups)
-// Frequency-side registers kr[b][k2]: k1 = t + T*b (B2 = ceil(N1/T) groups)
-// One shared-memory exchange moves data between the two layouts.  The
-// exchange buffer holds element (k1, n2) of column c at
-//   ((k1*N2 + n2) * W + c'),  c' = c, or c ^ 4 on odd (k1 + n2) when W = 8
-// (the swizzle keeps half-warps conflict-free for 8-column tiles).
+// Index digits (decimation in time):
+//   sample    n = n_0 P_0 + n_1 P_1 + ... + n_{S-1} P_{S-1},  P_s = prod_{j>s} R_j
+//   frequency k = k_0 Q_0 + k_1 Q_1 + ... + k_{S-1} Q_{S-1},  Q_s = prod_{j<s} R_j
+// Stage s runs N/R_s butterflies b = kk * P_s + r (kk < Q_s, r < P_s): an
+// R_s-point DFT over n_s of the stage input, then the twiddle
+// exp(-2 pi i r k_s Q_s / N) on output k_s.  Between stages the data goes
+// through shared memory, laid out as row (kk + Q_s k_s) P_s + r; stage s+1
+// reads row kk P_s + n_{s+1} P_{s+1} + r'.  The first stage reads registers
+// (sample layout), the last writes registers (frequency layout), so an
+// S-stage transform costs S-1 exchanges.  The inverse runs the stages in
+// reverse with the same butterflies and rows, conjugate twiddles applied
+// before each DFT.  Thread t runs butterflies b = t + T j of every stage.
 #pragma once
 #include "codelets.cuh"
 
 namespace sense {
 
-template <int N1_, int N2_, int T_, int W_>
+template <int... Rs>
+struct Radices {
+  static constexpr int S = sizeof...(Rs);
+  static constexpr int r[S] = {Rs...};
+  static constexpr int N = (Rs * ...);
+  static constexpr int radix(int s) { return r[s]; }
+  static constexpr int P(int s) {  // product of radices after s
+    int p = 1;
+    for (int j = s + 1; j < S; ++j) p *= r[j];
+    return p;
+  }
+  static constexpr int Q(int s) {  // product of radices before s
+    int q = 1;
+    for (int j = 0; j < s; ++j) q *= r[j];
+    return q;
+  }
+};
+
+template <int T_, int W_, class Rad>
 struct Col {
-  static constexpr int N1 = N1_, N2 = N2_, T = T_, W = W_;
-  static constexpr int N = N1 * N2;
-  static constexpr int B1 = (N2 + T - 1) / T;
-  static constexpr int B2 = (N1 + T - 1) / T;
+  static constexpr int N = Rad::N;
+  static constexpr int S = Rad::S;
+  static constexpr int T = T_, W = W_;
   static constexpr int THREADS = T * W;
-  static constexpr bool FULL1 = (B1 * T == N2);
-  static constexpr bool FULL2 = (B2 * T == N1);
+  static_assert(S >= 1, "at least one stage");
   static_assert(W == 8 || W == 16 || W == 32, "tile width");
+  static_assert(THREADS % 32 == 0, "block size must be a multiple of 32");
+
+  template <int s>
+  struct St {
+    static constexpr int R = Rad::radix(s);
+    static constexpr int P = Rad::P(s);
+    static constexpr int Q = Rad::Q(s);
+    static constexpr int NB = N / R;            // butterflies of this stage
+    static constexpr int J = (NB + T - 1) / T;  // butterflies per thread
+    static constexpr bool FULL = (J * T == NB);
+  };
+  // sample-side registers (input of stage 0) and frequency-side registers
+  // (output of stage S-1)
+  static constexpr int J0 = St<0>::J, R0 = St<0>::R;
+  static constexpr int JL = St<S - 1>::J, RL = St<S - 1>::R;
+  static constexpr int P0 = St<0>::P, QL = St<S - 1>::Q;
 
   int t, c;
   __device__ __forceinline__ Col() : t((int)threadIdx.x / W), c((int)threadIdx.x % W) {}
 
-  __device__ __forceinline__ int n2_of(int b) const { return t + T * b; }
-  __device__ __forceinline__ int k1_of(int b) const { return t + T * b; }
-  __device__ __forceinline__ bool ok1(int b) const { return FULL1 || (t + T * b) < N2; }
-  __device__ __forceinline__ bool ok2(int b) const { return FULL2 || (t + T * b) < N1; }
-  // row of the sample held in xr[b][n1] / of the frequency held in kr[b][k2]
-  __device__ __forceinline__ int xrow(int b, int n1) const { return N2 * n1 + (t + T * b); }
-  __device__ __forceinline__ int krow(int b, int k2) const { return (t + T * b) + N1 * k2; }
-
-  __device__ __forceinline__ int xidx(int k1, int n2) const {
-    int cc = c;
-    if (W == 8) cc ^= ((k1 + n2) & 1) << 2;
-    return (k1 * N2 + n2) * W + cc;
+  template <int s>
+  __device__ __forceinline__ bool ok(int j) const {
+    return St<s>::FULL || (t + T * j) < St<s>::NB;
   }
+  __device__ __forceinline__ bool ok0(int j) const { return ok<0>(j); }
+  __device__ __forceinline__ bool okL(int j) const { return ok<S - 1>(j); }
+  // row (sample index) held in x[j][n]: n * P_0 + b
+  __device__ __forceinline__ int xrow(int j, int n) const { return n * P0 + (t + T * j); }
+  // frequency index held in k[j][m]: b + Q_{S-1} m
+  __device__ __forceinline__ int krow(int j, int m) const { return (t + T * j) + QL * m; }
+  __device__ __forceinline__ int sidx(int row) const { return row * W + c; }
 
-  // forward (exp(-...)) transform, sample layout -> frequency layout, unnormalised.
-  // tw[m] = exp(-2 pi i m / N).  One __syncthreads inside.
-  __device__ __forceinline__ void fwd(float2 (&xr)[B1][N1], float2 (&kr)[B2][N2], float2* buf,
-                                      const float2* tw) const {
+  // ---- forward stages ----
+  // stage 0: registers in, (S > 1) shared out
+  __device__ __forceinline__ void fwd_first(float2 (&x)[J0][R0], float2* out, const float2* tw) const {
 #pragma unroll
-    for (int b = 0; b < B1; ++b) {
-      if (ok1(b)) {
-        const int n2 = n2_of(b);
-        Dft<N1, -1>::run(xr[b]);
+    for (int j = 0; j < J0; ++j) {
+      if (!ok<0>(j)) continue;
+      const int b = t + T * j;  // = r, kk = 0
+      Dft<R0, -1>::run(x[j]);
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          float2 v = xr[b][k1];
-          if (k1 > 0) v = cmul(v, tw[n2 * k1]);
-          buf[xidx(k1, n2)] = v;
-        }
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int b = 0; b < B2; ++b) {
-      if (ok2(b)) {
-        const int k1 = k1_of(b);
-#pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) kr[b][n2] = buf[xidx(k1, n2)];
-        Dft<N2, -1>::run(kr[b]);
+      for (int k = 0; k < R0; ++k) {
+        float2 v = x[j][k];
+        if (k > 0) v = cmul(v, tw[b * k]);
+        out[sidx(k * P0 + b)] = v;
       }
     }
   }
 
-  // inverse (exp(+...)) transform, frequency layout -> sample layout, unnormalised.
-  __device__ __forceinline__ void inv(float2 (&kr)[B2][N2], float2 (&xr)[B1][N1], float2* buf,
-                                      const float2* tw) const {
+  template <int s>
+  __device__ __forceinline__ void fwd_mid(const float2* in, float2* out, const float2* tw) const {
+    using G = St<s>;
+    constexpr int Pp = G::P * G::R;  // P_{s-1}
 #pragma unroll
-    for (int b = 0; b < B2; ++b) {
-      if (ok2(b)) {
-        const int k1 = k1_of(b);
-        Dft<N2, 1>::run(kr[b]);
+    for (int j = 0; j < G::J; ++j) {
+      if (!ok<s>(j)) continue;
+      const int b = t + T * j;
+      const int kk = b / G::P, r = b - kk * G::P;
+      float2 v[G::R];
 #pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) {
-          float2 v = kr[b][n2];
-          if (n2 > 0) v = cmulc(v, tw[n2 * k1]);
-          buf[xidx(k1, n2)] = v;
-        }
+      for (int n = 0; n < G::R; ++n) v[n] = in[sidx(kk * Pp + n * G::P + r)];
+      Dft<G::R, -1>::run(v);
+#pragma unroll
+      for (int k = 0; k < G::R; ++k) {
+        float2 w = v[k];
+        if (k > 0) w = cmul(w, tw[r * k * G::Q]);
+        out[sidx((kk + G::Q * k) * G::P + r)] = w;
       }
     }
-    __syncthreads();
+  }
+
+  // last stage: shared in (S > 1), registers out
+  __device__ __forceinline__ void fwd_last(const float2* in, float2 (&kr)[JL][RL]) const {
+    using G = St<S - 1>;
 #pragma unroll
-    for (int b = 0; b < B1; ++b) {
-      if (ok1(b)) {
-        const int n2 = n2_of(b);
+    for (int j = 0; j < JL; ++j) {
+      if (!ok<S - 1>(j)) continue;
+      const int kk = t + T * j;
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) xr[b][k1] = buf[xidx(k1, n2)];
-        Dft<N1, 1>::run(xr[b]);
+      for (int n = 0; n < RL; ++n) kr[j][n] = in[sidx(kk * RL + n)];
+      Dft<RL, -1>::run(kr[j]);
+    }
+  }
+
+  template <int s>
+  __device__ __forceinline__ void fwd_mids(float2* const* buf, const float2* tw) const {
+    if constexpr (s < S - 1) {
+      __syncthreads();
+      fwd_mid<s>(buf[(s - 1) & 1], buf[s & 1], tw);
+      fwd_mids<s + 1>(buf, tw);
+    }
+  }
+
+  // Forward transform x (sample layout) -> k (frequency layout), unnormalised.
+  // Uses buf[0], buf[1] alternately; S-1 barriers.
+  __device__ __forceinline__ void fwd(float2 (&x)[J0][R0], float2 (&kr)[JL][RL], float2* const* buf,
+                                      const float2* tw) const {
+    if constexpr (S == 1) {
+#pragma unroll
+      for (int j = 0; j < J0; ++j) {
+#pragma unroll
+        for (int n = 0; n < R0; ++n) kr[j][n] = x[j][n];
+        Dft<R0, -1>::run(kr[j]);
       }
+    } else {
+      fwd_first(x, buf[0], tw);
+      fwd_mids<1>(buf, tw);
+      __syncthreads();
+      fwd_last(buf[(S - 2) & 1], kr);
+    }
+  }
+
+  // ---- inverse stages (conjugate twiddles before each DFT) ----
+  __device__ __forceinline__ void inv_first(float2 (&kr)[JL][RL], float2* out) const {
+#pragma unroll
+    for (int j = 0; j < JL; ++j) {
+      if (!ok<S - 1>(j)) continue;
+      const int kk = t + T * j;
+      Dft<RL, 1>::run(kr[j]);
+#pragma unroll
+      for (int n = 0; n < RL; ++n) out[sidx(kk * RL + n)] = kr[j][n];
+    }
+  }
+
+  template <int s>
+  __device__ __forceinline__ void inv_mid(const float2* in, float2* out, const float2* tw) const {
+    using G = St<s>;
+    constexpr int Pp = G::P * G::R;
+#pragma unroll
+    for (int j = 0; j < G::J; ++j) {
+      if (!ok<s>(j)) continue;
+      const int b = t + T * j;
+      const int kk = b / G::P, r = b - kk * G::P;
+      float2 v[G::R];
+#pragma unroll
+      for (int k = 0; k < G::R; ++k) {
+        float2 w = in[sidx((kk + G::Q * k) * G::P + r)];
+        if (k > 0) w = cmulc(w, tw[r * k * G::Q]);
+        v[k] = w;
+      }
+      Dft<G::R, 1>::run(v);
+#pragma unroll
+      for (int n = 0; n < G::R; ++n) out[sidx(kk * Pp + n * G::P + r)] = v[n];
+    }
+  }
+
+  __device__ __forceinline__ void inv_last(const float2* in, float2 (&x)[J0][R0], const float2* tw) const {
+#pragma unroll
+    for (int j = 0; j < J0; ++j) {
+      if (!ok<0>(j)) continue;
+      const int b = t + T * j;
+#pragma unroll
+      for (int k = 0; k < R0; ++k) {
+        float2 w = in[sidx(k * P0 + b)];
+        if (k > 0) w = cmulc(w, tw[b * k]);
+        x[j][k] = w;
+      }
+      Dft<R0, 1>::run(x[j]);
+    }
+  }
+
+  // exchange index e = S-1 .. 2S-3 continues the alternation of the forward
+  template <int s>
+  __device__ __forceinline__ void inv_mids(float2* const* buf, const float2* tw) const {
+    if constexpr (s >= 1) {
+      __syncthreads();
+      constexpr int e_in = (S - 1) + (S - 2 - s);  // exchange written by the previous inverse stage
+      inv_mid<s>(buf[e_in & 1], buf[(e_in + 1) & 1], tw);
+      inv_mids<s - 1>(buf, tw);
+    }
+  }
+
+  // Inverse transform k (frequency layout) -> x (sample layout), unnormalised.
+  // Continues the buffer alternation of fwd() so fwd followed by inv needs
+  // exactly one barrier per exchange.
+  __device__ __forceinline__ void inv(float2 (&kr)[JL][RL], float2 (&x)[J0][R0], float2* const* buf,
+                                      const float2* tw) const {
+    if constexpr (S == 1) {
+#pragma unroll
+      for (int j = 0; j < J0; ++j) {
+#pragma unroll
+        for (int n = 0; n < R0; ++n) x[j][n] = kr[j][n];
+        Dft<R0, 1>::run(x[j]);
+      }
+    } else {
+      inv_first(kr, buf[(S - 1) & 1]);
+      inv_mids<S - 2>(buf, tw);
+      __syncthreads();
+      inv_last(buf[(2 * S - 3) & 1], x, tw);
     }
   }
 };

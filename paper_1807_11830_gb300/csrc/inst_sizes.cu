@@ -1,5 +1,5 @@
 // Size table queries (host).
-#include "launch.h"
+#include "launch_col.cuh"
 
 namespace sense {
 
@@ -35,5 +35,25 @@ int col_threads(int n) {
 }
 
 int row_width(int n) { return col_width(n); }
+
+int normal_variant_threads(int n, int variant) {
+  switch (n) {
+#define SENSE_CASE(N) case N: return norm_variant_threads<N>(variant);
+    SENSE_FOR_EACH_SIZE(SENSE_CASE)
+#undef SENSE_CASE
+    default:
+      return 0;
+  }
+}
+
+int normal_variant_width(int n, int variant) {
+  switch (n) {
+#define SENSE_CASE(N) case N: return norm_variant_width<N>(variant);
+    SENSE_FOR_EACH_SIZE(SENSE_CASE)
+#undef SENSE_CASE
+    default:
+      return 0;
+  }
+}
 
 }  // namespace sense

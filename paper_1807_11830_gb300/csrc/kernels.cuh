@@ -15,10 +15,10 @@
 
 namespace sense {
 
-// shared-memory bytes of the column kernels for length N
-template <int N>
-constexpr size_t col_smem_bytes() {
-  using C = typename Cfg<N>::C;
+// shared-memory bytes of the column kernels for configuration C
+template <class C>
+constexpr size_t col_smem_bytes_c() {
+  constexpr int N = C::N;
   return sizeof(float2) * (size_t)N            // twiddles
          + 2 * sizeof(float2) * (size_t)N * C::W  // two exchange buffers
          + 32 * sizeof(double)                 // block-sum scratch
@@ -26,9 +26,14 @@ constexpr size_t col_smem_bytes() {
 }
 
 template <int N>
+constexpr size_t col_smem_bytes() {
+  return col_smem_bytes_c<typename Cfg<N>::C>();
+}
+
+template <int N>
 constexpr size_t row_smem_bytes() {
   using C = typename Cfg<N>::C;
-  return sizeof(float2) * (size_t)N + sizeof(float2) * (size_t)C::W * (N + 1);
+  return sizeof(float2) * (size_t)N + sizeof(float2) * (size_t)C::W * (N + 1) + sizeof(float2) * (size_t)C::W * N;
 }
 
 struct ColSmem {
@@ -39,9 +44,23 @@ struct ColSmem {
   short* map;
 };
 
-template <int N>
-__device__ __forceinline__ ColSmem col_smem(unsigned char* base) {
-  using C = typename Cfg<N>::C;
+// Exchange buffers for the c-th transform of a loop that runs one direction
+// per iteration: with an odd number of exchanges per transform (S even) the
+// pair is swapped every iteration, so no buffer is written while another
+// thread may still read it.
+template <class C>
+struct BufPair {
+  float2* b[2];
+  __device__ __forceinline__ BufPair(float2* b0, float2* b1, int iter) {
+    const bool swap = ((C::S % 2) == 0) && (iter & 1);
+    b[0] = swap ? b1 : b0;
+    b[1] = swap ? b0 : b1;
+  }
+};
+
+template <class C>
+__device__ __forceinline__ ColSmem col_smem_c(unsigned char* base) {
+  constexpr int N = C::N;
   ColSmem s;
   s.tw = reinterpret_cast<float2*>(base);
   s.buf0 = s.tw + N;
@@ -49,6 +68,11 @@ __device__ __forceinline__ ColSmem col_smem(unsigned char* base) {
   s.red = reinterpret_cast<double*>(s.buf1 + N * C::W);
   s.map = reinterpret_cast<short*>(s.red + 32);
   return s;
+}
+
+template <int N>
+__device__ __forceinline__ ColSmem col_smem(unsigned char* base) {
+  return col_smem_c<typename Cfg<N>::C>(base);
 }
 
 // Copy the twiddles and build map[row] = index of `row` in this frame's line
@@ -100,35 +124,36 @@ __global__ void __launch_bounds__(TH) k_fwd_col(FwdColArgs<St> a) {
   const size_t img = (size_t)N * a.nx;
   const float scale = rsqrtf((float)N);
 
-  float2 xv[C::B1][C::N1];
+  float2 xv[C::J0][C::R0];
 #pragma unroll
-  for (int b = 0; b < C::B1; ++b)
+  for (int j = 0; j < C::J0; ++j)
 #pragma unroll
-    for (int n1 = 0; n1 < C::N1; ++n1)
-      xv[b][n1] = (col.ok1(b) && xin) ? __ldg(a.x + f * img + (size_t)col.xrow(b, n1) * a.nx + x)
+    for (int n = 0; n < C::R0; ++n)
+      xv[j][n] = (col.ok0(j) && xin) ? __ldg(a.x + f * img + (size_t)col.xrow(j, n) * a.nx + x)
                                       : make_float2(0.f, 0.f);
 
 #pragma unroll 1
   for (int c = 0; c < a.coils; ++c) {
-    float2 xr[C::B1][C::N1];
-    float2 kr[C::B2][C::N2];
+    float2 xr[C::J0][C::R0];
+    float2 kr[C::JL][C::RL];
 #pragma unroll
-    for (int b = 0; b < C::B1; ++b)
+    for (int j = 0; j < C::J0; ++j)
 #pragma unroll
-      for (int n1 = 0; n1 < C::N1; ++n1) {
+      for (int n = 0; n < C::R0; ++n) {
         float2 sv = make_float2(0.f, 0.f);
-        if (col.ok1(b) && xin) sv = St::ld(a.S, c * img + (size_t)col.xrow(b, n1) * a.nx + x);
-        xr[b][n1] = cmul(sv, xv[b][n1]);
+        if (col.ok0(j) && xin) sv = St::ld(a.S, c * img + (size_t)col.xrow(j, n) * a.nx + x);
+        xr[j][n] = cmul(sv, xv[j][n]);
       }
-    col.fwd(xr, kr, (c & 1) ? s.buf1 : s.buf0, s.tw);
+    const BufPair<C> bp(s.buf0, s.buf1, c);
+    col.fwd(xr, kr, bp.b, s.tw);
     float2* dst = a.tmp + ((size_t)f * a.coils + c) * a.L * a.nx;
 #pragma unroll
-    for (int b = 0; b < C::B2; ++b)
+    for (int j = 0; j < C::JL; ++j)
 #pragma unroll
-      for (int k2 = 0; k2 < C::N2; ++k2) {
-        if (col.ok2(b) && xin) {
-          const int l = s.map[col.krow(b, k2)];
-          if (l >= 0) dst[(size_t)l * a.nx + x] = cscale(kr[b][k2], scale);
+      for (int m = 0; m < C::RL; ++m) {
+        if (col.okL(j) && xin) {
+          const int l = s.map[col.krow(j, m)];
+          if (l >= 0) dst[(size_t)l * a.nx + x] = cscale(kr[j][m], scale);
         }
       }
   }
@@ -155,6 +180,7 @@ __global__ void __launch_bounds__(TH)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* tile = tw + N;
+  float2* bufs[2] = {tile, tile + C::W * P};  // the tile doubles as the first exchange buffer
   const C col;
   const long r0 = (long)blockIdx.x * C::W;
   for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = a.tw[i];
@@ -164,35 +190,35 @@ __global__ void __launch_bounds__(TH)
   }
   __syncthreads();
   const float scale = rsqrtf((float)N);
-  float2 xr[C::B1][C::N1];
-  float2 kr[C::B2][C::N2];
+  float2 xr[C::J0][C::R0];
+  float2 kr[C::JL][C::RL];
   float2* row = tile + col.c * P;
   if (DIR < 0) {
 #pragma unroll
-    for (int b = 0; b < C::B1; ++b)
+    for (int j = 0; j < C::J0; ++j)
 #pragma unroll
-      for (int n1 = 0; n1 < C::N1; ++n1) xr[b][n1] = col.ok1(b) ? row[col.xrow(b, n1)] : make_float2(0.f, 0.f);
+      for (int n = 0; n < C::R0; ++n) xr[j][n] = col.ok0(j) ? row[col.xrow(j, n)] : make_float2(0.f, 0.f);
     __syncthreads();  // the tile becomes the exchange buffer
-    col.fwd(xr, kr, tile, tw);
+    col.fwd(xr, kr, bufs, tw);
     __syncthreads();
 #pragma unroll
-    for (int b = 0; b < C::B2; ++b)
+    for (int j = 0; j < C::JL; ++j)
 #pragma unroll
-      for (int k2 = 0; k2 < C::N2; ++k2)
-        if (col.ok2(b)) row[col.krow(b, k2)] = cscale(kr[b][k2], scale);
+      for (int m = 0; m < C::RL; ++m)
+        if (col.okL(j)) row[col.krow(j, m)] = cscale(kr[j][m], scale);
   } else {
 #pragma unroll
-    for (int b = 0; b < C::B2; ++b)
+    for (int j = 0; j < C::JL; ++j)
 #pragma unroll
-      for (int k2 = 0; k2 < C::N2; ++k2) kr[b][k2] = col.ok2(b) ? row[col.krow(b, k2)] : make_float2(0.f, 0.f);
+      for (int m = 0; m < C::RL; ++m) kr[j][m] = col.okL(j) ? row[col.krow(j, m)] : make_float2(0.f, 0.f);
     __syncthreads();
-    col.inv(kr, xr, tile, tw);
+    col.inv(kr, xr, bufs, tw);
     __syncthreads();
 #pragma unroll
-    for (int b = 0; b < C::B1; ++b)
+    for (int j = 0; j < C::J0; ++j)
 #pragma unroll
-      for (int n1 = 0; n1 < C::N1; ++n1)
-        if (col.ok1(b)) row[col.xrow(b, n1)] = cscale(xr[b][n1], scale);
+      for (int n = 0; n < C::R0; ++n)
+        if (col.ok0(j)) row[col.xrow(j, n)] = cscale(xr[j][n], scale);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < C::W * N; i += C::THREADS) {
@@ -233,43 +259,44 @@ __global__ void __launch_bounds__(TH) k_adj_col(AdjColArgs<St> a) {
   load_tw_and_linemap<N, C::THREADS>(s, a.tw, a.lines + (size_t)f * a.L, a.L, a.err);
   const size_t img = (size_t)N * a.nx;
 
-  float2 acc[C::B1][C::N1];
-  float accr[C::B1][C::N1];
+  float2 acc[C::J0][C::R0];
+  float accr[C::J0][C::R0];
 #pragma unroll
-  for (int b = 0; b < C::B1; ++b)
+  for (int j = 0; j < C::J0; ++j)
 #pragma unroll
-    for (int n1 = 0; n1 < C::N1; ++n1) {
-      acc[b][n1] = make_float2(0.f, 0.f);
-      accr[b][n1] = 0.f;
+    for (int n = 0; n < C::R0; ++n) {
+      acc[j][n] = make_float2(0.f, 0.f);
+      accr[j][n] = 0.f;
     }
 
 #pragma unroll 1
   for (int c = 0; c < a.coils; ++c) {
-    float2 xr[C::B1][C::N1];
-    float2 kr[C::B2][C::N2];
+    float2 xr[C::J0][C::R0];
+    float2 kr[C::JL][C::RL];
     const float2* src = a.tmp + ((size_t)f * a.coils + c) * a.L * a.nx;
 #pragma unroll
-    for (int b = 0; b < C::B2; ++b)
+    for (int j = 0; j < C::JL; ++j)
 #pragma unroll
-      for (int k2 = 0; k2 < C::N2; ++k2) {
+      for (int m = 0; m < C::RL; ++m) {
         float2 v = make_float2(0.f, 0.f);
-        if (col.ok2(b) && xin) {
-          const int l = s.map[col.krow(b, k2)];
+        if (col.okL(j) && xin) {
+          const int l = s.map[col.krow(j, m)];
           if (l >= 0) v = __ldg(src + (size_t)l * a.nx + x);
         }
-        kr[b][k2] = v;
+        kr[j][m] = v;
       }
-    col.inv(kr, xr, (c & 1) ? s.buf1 : s.buf0, s.tw);
+    const BufPair<C> bp(s.buf0, s.buf1, c);
+    col.inv(kr, xr, bp.b, s.tw);
 #pragma unroll
-    for (int b = 0; b < C::B1; ++b)
+    for (int j = 0; j < C::J0; ++j)
 #pragma unroll
-      for (int n1 = 0; n1 < C::N1; ++n1) {
+      for (int n = 0; n < C::R0; ++n) {
         if (MODE == 2) {
-          accr[b][n1] = fmaf(xr[b][n1].x, xr[b][n1].x, fmaf(xr[b][n1].y, xr[b][n1].y, accr[b][n1]));
+          accr[j][n] = fmaf(xr[j][n].x, xr[j][n].x, fmaf(xr[j][n].y, xr[j][n].y, accr[j][n]));
         } else {
           float2 sv = make_float2(0.f, 0.f);
-          if (col.ok1(b) && xin) sv = St::ld(a.S, c * img + (size_t)col.xrow(b, n1) * a.nx + x);
-          acc[b][n1] = cfma_conj(acc[b][n1], sv, xr[b][n1]);
+          if (col.ok0(j) && xin) sv = St::ld(a.S, c * img + (size_t)col.xrow(j, n) * a.nx + x);
+          acc[j][n] = cfma_conj(acc[j][n], sv, xr[j][n]);
         }
       }
   }
@@ -277,15 +304,15 @@ __global__ void __launch_bounds__(TH) k_adj_col(AdjColArgs<St> a) {
   const float scale = rsqrtf((float)N);
   float part = 0.f;
 #pragma unroll
-  for (int b = 0; b < C::B1; ++b)
+  for (int j = 0; j < C::J0; ++j)
 #pragma unroll
-    for (int n1 = 0; n1 < C::N1; ++n1) {
-      if (!(col.ok1(b) && xin)) continue;
-      const size_t idx = f * img + (size_t)col.xrow(b, n1) * a.nx + x;
+    for (int n = 0; n < C::R0; ++n) {
+      if (!(col.ok0(j) && xin)) continue;
+      const size_t idx = f * img + (size_t)col.xrow(j, n) * a.nx + x;
       if (MODE == 2) {
-        a.rss[idx] = sqrtf(accr[b][n1] * (1.0f / (float)N));
+        a.rss[idx] = sqrtf(accr[j][n] * (1.0f / (float)N));
       } else {
-        const float2 v = cscale(acc[b][n1], scale);
+        const float2 v = cscale(acc[j][n], scale);
         if (MODE == 0) {
           a.x[idx] = v;
         } else {
@@ -324,14 +351,127 @@ __global__ void __launch_bounds__(TH) k_adj_col(AdjColArgs<St> a) {
 }
 
 // ---------------------------------------------------------------------------
-// E^H E, column-wise.  CG=false: out = E^H E x.
-// CG=true: p = r + beta p (when p_update), q = E^H E p, Re<p,q> -> alpha.
+// E^H E, column-wise, for one (frame, column tile).  Used by k_normal (one
+// launch per operator application) and by the persistent CG kernel.
+//   CG=false: out = E^H E x.
+//   CG=true : p_k = r + beta p_{k-1} formed on the fly when p_update (read
+//             from p_src, written to p_dst), q = E^H E p_k; returns this
+//             thread's share of Re<p_k, q> (FP32 over its own elements).
+// Inputs that other blocks of the same launch may have written are read
+// through L2 (ld.global.cg), and outputs are written the same way.
 // ---------------------------------------------------------------------------
+struct NormalTile {
+  const float2* x;      // CG=false input, frame base
+  float2* out;          // CG=false output, frame base
+  const float2* p_src;  // CG=true, frame base
+  float2* p_dst;        // CG=true, frame base
+  const float2* r;      // CG=true, frame base
+  float2* q;            // CG=true, frame base
+  const void* S;        // maps [C][N][nx], storage type
+  int nx, coils, tile, p_update;
+  float beta;
+};
+
+template <class C, class St, bool CG>
+__device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem& s, unsigned keep) {
+  constexpr int N = C::N;
+  const C col;
+  const int x = a.tile * C::W + col.c;
+  const bool xin = x < a.nx;
+  const size_t img = (size_t)N * a.nx;
+  float2 p[C::J0][C::R0], q[C::J0][C::R0];
+#pragma unroll
+  for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+    for (int n = 0; n < C::R0; ++n) {
+      float2 v = make_float2(0.f, 0.f);
+      if (col.ok0(j) && xin) {
+        const size_t idx = (size_t)col.xrow(j, n) * a.nx + x;
+        if (CG) {
+          v = __ldcg(a.p_src + idx);
+          if (a.p_update) {
+            const float2 rv = __ldcg(a.r + idx);
+            v = make_float2(fmaf(a.beta, v.x, rv.x), fmaf(a.beta, v.y, rv.y));
+            __stcg(a.p_dst + idx, v);
+          }
+        } else {
+          v = __ldg(a.x + idx);
+        }
+      }
+      p[j][n] = v;
+      q[j][n] = make_float2(0.f, 0.f);
+    }
+
+  float2* bufs[2] = {s.buf0, s.buf1};
+  const typename St::T* Sc = static_cast<const typename St::T*>(a.S) + x;
+#pragma unroll 1
+  for (int c = 0; c < a.coils; ++c, Sc += img) {
+    float2 xr[C::J0][C::R0];
+    float2 kr[C::JL][C::RL];
+#pragma unroll
+    for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+      for (int n = 0; n < C::R0; ++n) {
+        float2 sv = make_float2(0.f, 0.f);
+        if (col.ok0(j) && xin) sv = St::ld(Sc, (size_t)col.xrow(j, n) * a.nx);
+        xr[j][n] = cmul(sv, p[j][n]);
+      }
+    col.fwd(xr, kr, bufs, s.tw);
+#pragma unroll
+    for (int j = 0; j < C::JL; ++j)
+#pragma unroll
+      for (int m = 0; m < C::RL; ++m)
+        if (!((keep >> (j * C::RL + m)) & 1u)) kr[j][m] = make_float2(0.f, 0.f);
+    col.inv(kr, xr, bufs, s.tw);
+#pragma unroll
+    for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+      for (int n = 0; n < C::R0; ++n) {
+        float2 sv = make_float2(0.f, 0.f);
+        if (col.ok0(j) && xin) sv = St::ld(Sc, (size_t)col.xrow(j, n) * a.nx);
+        q[j][n] = cfma_conj(q[j][n], sv, xr[j][n]);
+      }
+  }
+
+  const float invN = 1.0f / (float)N;  // the two unitary transforms' 1/sqrt(N) each
+  float part = 0.f;
+#pragma unroll
+  for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+    for (int n = 0; n < C::R0; ++n) {
+      if (!(col.ok0(j) && xin)) continue;
+      const size_t idx = (size_t)col.xrow(j, n) * a.nx + x;
+      const float2 qv = cscale(q[j][n], invN);
+      if (CG) {
+        __stcg(a.q + idx, qv);
+        part = fmaf(p[j][n].x, qv.x, fmaf(p[j][n].y, qv.y, part));
+      } else {
+        a.out[idx] = qv;
+      }
+    }
+  return part;
+}
+
+// One bit per frequency row this thread holds: set if the row is sampled.
+template <class C>
+__device__ __forceinline__ unsigned sampled_bits(const ColSmem& s) {
+  static_assert(C::JL * C::RL <= 32, "mask bits");
+  const C col;
+  unsigned keep = 0u;
+#pragma unroll
+  for (int j = 0; j < C::JL; ++j)
+#pragma unroll
+    for (int m = 0; m < C::RL; ++m)
+      if (col.okL(j) && s.map[col.krow(j, m)] >= 0) keep |= 1u << (j * C::RL + m);
+  return keep;
+}
+
 template <class St>
 struct NormalArgs {
   const float2* x;             // CG=false input
   float2* out;                 // CG=false output
-  float2* p;                   // CG=true: search direction (updated in place)
+  const float2* p_src;         // CG=true: previous search direction (or the current one if !p_update)
+  float2* p_dst;               // CG=true: new search direction (written when p_update)
   const float2* r;             // CG=true
   float2* q;                   // CG=true output
   const typename St::T* S;
@@ -342,91 +482,30 @@ struct NormalArgs {
   CgState cg;
 };
 
-template <int N, class St, bool CG, int TH = Cfg<N>::C::THREADS>
-__global__ void __launch_bounds__(TH) k_normal(NormalArgs<St> a) {
-  using C = typename Cfg<N>::C;
+template <int N, int V, class St, bool CG, int TH = NormCfg<N, V>::C::THREADS, int MINB = NormCfg<N, V>::MINB>
+__global__ void __launch_bounds__(TH, MINB) k_normal(NormalArgs<St> a) {
+  using C = typename NormCfg<N, V>::C;
   const int f = blockIdx.y;
   if (CG && a.cg.active[f] == 0) return;  // uniform per block
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const ColSmem s = col_smem<N>(smem_raw);
-  const C col;
-  const int x = blockIdx.x * C::W + col.c;
-  const bool xin = x < a.nx;
+  const ColSmem s = col_smem_c<C>(smem_raw);
   load_tw_and_linemap<N, C::THREADS>(s, a.tw, a.lines + (size_t)f * a.L, a.L, a.err);
+  const unsigned keep = sampled_bits<C>(s);
   const size_t img = (size_t)N * a.nx;
-  const float invN = 1.0f / (float)N;
-
-  float beta = 0.f;
-  if (CG && a.p_update) beta = (float)__ldg(a.cg.beta + f);
-  float2 p[C::B1][C::N1], q[C::B1][C::N1];
-#pragma unroll
-  for (int b = 0; b < C::B1; ++b)
-#pragma unroll
-    for (int n1 = 0; n1 < C::N1; ++n1) {
-      float2 v = make_float2(0.f, 0.f);
-      if (col.ok1(b) && xin) {
-        const size_t idx = f * img + (size_t)col.xrow(b, n1) * a.nx + x;
-        if (CG) {
-          v = a.p[idx];
-          if (a.p_update) {
-            const float2 rv = a.r[idx];
-            v = make_float2(fmaf(beta, v.x, rv.x), fmaf(beta, v.y, rv.y));
-            a.p[idx] = v;
-          }
-        } else {
-          v = __ldg(a.x + idx);
-        }
-      }
-      p[b][n1] = v;
-      q[b][n1] = make_float2(0.f, 0.f);
-    }
-
-#pragma unroll 1
-  for (int c = 0; c < a.coils; ++c) {
-    float2 xr[C::B1][C::N1];
-    float2 kr[C::B2][C::N2];
-#pragma unroll
-    for (int b = 0; b < C::B1; ++b)
-#pragma unroll
-      for (int n1 = 0; n1 < C::N1; ++n1) {
-        float2 sv = make_float2(0.f, 0.f);
-        if (col.ok1(b) && xin) sv = St::ld(a.S, c * img + (size_t)col.xrow(b, n1) * a.nx + x);
-        xr[b][n1] = cmul(sv, p[b][n1]);
-      }
-    col.fwd(xr, kr, s.buf0, s.tw);
-#pragma unroll
-    for (int b = 0; b < C::B2; ++b)
-#pragma unroll
-      for (int k2 = 0; k2 < C::N2; ++k2) {
-        const bool keep = col.ok2(b) && s.map[col.krow(b, k2)] >= 0;
-        kr[b][k2] = keep ? cscale(kr[b][k2], invN) : make_float2(0.f, 0.f);
-      }
-    col.inv(kr, xr, s.buf1, s.tw);
-#pragma unroll
-    for (int b = 0; b < C::B1; ++b)
-#pragma unroll
-      for (int n1 = 0; n1 < C::N1; ++n1) {
-        float2 sv = make_float2(0.f, 0.f);
-        if (col.ok1(b) && xin) sv = St::ld(a.S, c * img + (size_t)col.xrow(b, n1) * a.nx + x);
-        q[b][n1] = cfma_conj(q[b][n1], sv, xr[b][n1]);
-      }
-  }
-
-  float part = 0.f;
-#pragma unroll
-  for (int b = 0; b < C::B1; ++b)
-#pragma unroll
-    for (int n1 = 0; n1 < C::N1; ++n1) {
-      if (!(col.ok1(b) && xin)) continue;
-      const size_t idx = f * img + (size_t)col.xrow(b, n1) * a.nx + x;
-      if (CG) {
-        a.q[idx] = q[b][n1];
-        part = fmaf(p[b][n1].x, q[b][n1].x, fmaf(p[b][n1].y, q[b][n1].y, part));
-      } else {
-        a.out[idx] = q[b][n1];
-      }
-    }
-
+  NormalTile t;
+  t.x = a.x + f * img;
+  t.out = a.out + f * img;
+  t.p_src = a.p_src + f * img;
+  t.p_dst = a.p_dst + f * img;
+  t.r = a.r + f * img;
+  t.q = a.q + f * img;
+  t.S = a.S;
+  t.nx = a.nx;
+  t.coils = a.coils;
+  t.tile = blockIdx.x;
+  t.p_update = a.p_update;
+  t.beta = (CG && a.p_update) ? (float)__ldg(a.cg.beta + f) : 0.f;
+  const float part = normal_tile<C, St, CG>(t, s, keep);
   if (CG) {
     const double tot = block_sum<C::THREADS>((double)part, s.red);
     const CgState& g = a.cg;

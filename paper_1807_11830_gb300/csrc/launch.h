@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "persistent.cuh"
 
 namespace sense {
 
@@ -17,8 +18,17 @@ template <class St>
 cudaError_t launch_fwd_col(int n, const FwdColArgs<St>& a, int tiles, int frames, cudaStream_t s);
 template <class St>
 cudaError_t launch_adj_col(int n, int mode, const AdjColArgs<St>& a, int tiles, int frames, cudaStream_t s);
+// normal operator, kernel variant `variant` (0 .. kNormVariants-1; see NormCfg);
+// the grid's tile count follows the variant's tile width
 template <class St>
-cudaError_t launch_normal(int n, bool cg, const NormalArgs<St>& a, int tiles, int frames, cudaStream_t s);
+cudaError_t launch_normal(int n, int variant, bool cg, const NormalArgs<St>& a, int frames, cudaStream_t s);
+// tile width / threads per block of a normal-operator variant, 0 if it does not exist
+int normal_variant_width(int n, int variant);
+int normal_variant_threads(int n, int variant);
+// persistent CG kernel (all iterations of all frames of `a` in one launch,
+// `sms` x resident blocks per SM)
+template <class St>
+cudaError_t launch_cg_persistent(int n, int variant, const PArgs& a, int sms, cudaStream_t s);
 // forward row pass: FP32 in, storage St out
 template <class St>
 cudaError_t launch_rows_fwd(int n, const RowArgs<float2, typename St::T>& a, cudaStream_t s);

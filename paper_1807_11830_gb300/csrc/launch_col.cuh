@@ -2,6 +2,7 @@
 // per-family instantiation units so the families compile in parallel).
 #pragma once
 #include "launch.h"
+#include "persistent.cuh"
 
 namespace sense {
 
@@ -25,14 +26,78 @@ cudaError_t adj_col_n(const AdjColArgs<St>& a, int tiles, int frames, cudaStream
   return cudaGetLastError();
 }
 
+template <int N, int V, class St, bool CG>
+cudaError_t normal_nv(const NormalArgs<St>& a, int frames, cudaStream_t s) {
+  if constexpr (!NormCfg<N, V>::exists) {
+    return cudaErrorInvalidValue;
+  } else {
+    using C = typename NormCfg<N, V>::C;
+    static unsigned long long done = 0;
+    constexpr size_t sm = col_smem_bytes_c<C>();
+    cudaError_t e = ensure_smem(k_normal<N, V, St, CG>, sm, &done);
+    const int tiles = (a.nx + C::W - 1) / C::W;
+    if (e != cudaSuccess || frames == 0) return e;  // no frames: attribute set-up only
+    k_normal<N, V, St, CG><<<dim3(tiles, frames), C::THREADS, sm, s>>>(a);
+    return cudaGetLastError();
+  }
+}
+
 template <int N, class St, bool CG>
-cudaError_t normal_n(const NormalArgs<St>& a, int tiles, int frames, cudaStream_t s) {
-  static unsigned long long done = 0;
-  constexpr size_t sm = col_smem_bytes<N>();
-  cudaError_t e = ensure_smem(k_normal<N, St, CG>, sm, &done);
-  if (e != cudaSuccess || tiles == 0 || frames == 0) return e;  // empty grid: attribute set-up only
-  k_normal<N, St, CG><<<dim3(tiles, frames), Cfg<N>::C::THREADS, sm, s>>>(a);
-  return cudaGetLastError();
+cudaError_t normal_n(int variant, const NormalArgs<St>& a, int frames, cudaStream_t s) {
+  switch (variant) {
+    case 0: return normal_nv<N, 0, St, CG>(a, frames, s);
+    case 1: return normal_nv<N, 1, St, CG>(a, frames, s);
+    case 2: return normal_nv<N, 2, St, CG>(a, frames, s);
+    case 3: return normal_nv<N, 3, St, CG>(a, frames, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int N, int V, class St>
+cudaError_t persistent_nv(const PArgs& a, int sms, cudaStream_t s) {
+  if constexpr (!NormCfg<N, V>::exists) {
+    return cudaErrorInvalidValue;
+  } else {
+    using C = typename NormCfg<N, V>::C;
+    static unsigned long long done = 0;
+    constexpr size_t sm = col_smem_bytes_c<C>();
+    cudaError_t e = ensure_smem(k_cg_persistent<N, V, St>, sm, &done);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persistent<N, V, St>, C::THREADS, sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (a.nframes == 0 || a.iters == 0) return cudaSuccess;  // attribute set-up only
+    k_cg_persistent<N, V, St><<<sms * per_sm, C::THREADS, sm, s>>>(a);
+    return cudaGetLastError();
+  }
+}
+
+template <int N, class St>
+cudaError_t persistent_n(int variant, const PArgs& a, int sms, cudaStream_t s) {
+  switch (variant) {
+    case 0: return persistent_nv<N, 0, St>(a, sms, s);
+    case 1: return persistent_nv<N, 1, St>(a, sms, s);
+    case 2: return persistent_nv<N, 2, St>(a, sms, s);
+    case 3: return persistent_nv<N, 3, St>(a, sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int N>
+constexpr int norm_variant_threads(int v) {
+  return v == 0 ? NormCfg<N, 0>::C::THREADS
+       : v == 1 ? (NormCfg<N, 1>::exists ? NormCfg<N, 1>::C::THREADS : 0)
+       : v == 2 ? (NormCfg<N, 2>::exists ? NormCfg<N, 2>::C::THREADS : 0)
+       : v == 3 ? (NormCfg<N, 3>::exists ? NormCfg<N, 3>::C::THREADS : 0) : 0;
+}
+
+template <int N>
+constexpr int norm_variant_width(int v) {
+  return v == 0 ? NormCfg<N, 0>::C::W
+       : v == 1 ? (NormCfg<N, 1>::exists ? NormCfg<N, 1>::C::W : 0)
+       : v == 2 ? (NormCfg<N, 2>::exists ? NormCfg<N, 2>::C::W : 0)
+       : v == 3 ? (NormCfg<N, 3>::exists ? NormCfg<N, 3>::C::W : 0) : 0;
 }
 
 template <int N, int DIR, class InSt, class OutSt>

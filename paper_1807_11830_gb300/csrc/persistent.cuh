@@ -1,0 +1,243 @@
+// Persistent CG-SENSE iteration kernel: one launch runs every CG iteration of
+// every frame in a table.
+//
+// Work is cut into items, handed out in a fixed order by one global atomic
+// ticket counter:
+//   ticket -> (iteration k, phase, frame f, piece)
+//   phase 0 (normal): piece = column tile: p_k = r + beta p_{k-1},
+//                     q = E^H E p_k on the tile, Re<p_k, q> partial;
+//                     the last tile of frame f computes alpha (or freezes f).
+//   phase 1 (update): piece = chunk of the image: x += alpha p_k,
+//                     r -= alpha q, <r, r> partial; the last chunk computes
+//                     beta and the stopping test.
+// Tickets are ordered by iteration, then phase, then frame, then piece.  An
+// item waits (thread 0, bounded spin) only for the previous phase of its own
+// frame, i.e. for items with smaller tickets, which blocks already running
+// have taken.  So the wait always ends; frames pipeline freely: one frame's
+// memory-bound update runs while another frame's transform-bound normal
+// product fills the rest of the GPU, and no kernel boundary or launch tail
+// separates the phases.  A wait that exceeds its bound sets ERR_TIMEOUT,
+// skips the item's work and still counts the item, so the launch ends.
+//
+// Data written by other blocks of the launch (p, r, q, x, partials, scalars)
+// is read through L2 (ld.global.cg / acquire) and written through L2.
+#pragma once
+#include "kernels.cuh"
+
+namespace sense {
+
+// One frame of the table: its instance's maps and its own vectors.
+struct PFrame {
+  const void* S;       // maps [C][N][nx] of the frame's instance (storage type)
+  const int* lines;    // this frame's lines [L]
+  float2* x;           // [N][nx] image (output)
+  float2* r;           // residual
+  float2* p[2];        // search directions, ping-pong by iteration parity
+  float2* q;           // E^H E p
+  int coils, L;
+};
+
+struct PState {
+  double *rho, *rho0, *alpha, *beta, *resid;  // [frames]
+  int *iters, *outcome, *active;              // [frames]
+  unsigned *nrm_arrive, *upd_arrive;          // [frames] arrivals of the current phase
+  int *nrm_ready, *upd_ready;                 // [frames] iterations whose phase is complete
+  double *part_nrm, *part_upd;                // [frames][tiles] / [frames][chunks]
+  double tol;
+};
+
+struct PArgs {
+  const PFrame* frames;
+  int nframes, nx, tiles, chunks, iters;
+  unsigned* ticket;
+  const float2* tw;  // twiddles of the column transform
+  int* err;
+  PState st;
+};
+
+constexpr long kPersistentMaxSpins = 1L << 24;  // x >= 64 ns sleeps: a wait gives up after >= 1 s
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0: wait until *flag >= target.  Returns false after max_spins polls.
+__device__ __forceinline__ bool wait_at_least(const int* flag, int target, long max_spins = kPersistentMaxSpins) {
+  long spins = 0;
+  while (ld_acquire(flag) < target) {
+    if (++spins > max_spins) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+
+template <int N, int V, class St, int TH = NormCfg<N, V>::C::THREADS, int MINB = NormCfg<N, V>::MINB>
+__global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
+  using C = typename NormCfg<N, V>::C;
+  constexpr int T = C::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ColSmem s = col_smem_c<C>(smem_raw);
+  __shared__ int s_ticket, s_ok, s_active;
+  for (int i = threadIdx.x; i < N; i += T) s.tw[i] = a.tw[i];
+
+  const int per_iter = a.nframes * (a.tiles + a.chunks);
+  const long total = (long)per_iter * a.iters;
+  const size_t img = (size_t)N * a.nx;
+  const PState& g = a.st;
+
+  for (;;) {
+    __syncthreads();  // previous item fully done with shared memory and s_*
+    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    const long t = s_ticket;
+    if (t >= total) break;
+    const int k = (int)(t / per_iter);
+    int w = (int)(t - (long)k * per_iter);
+    const bool normal = w < a.nframes * a.tiles;
+    if (!normal) w -= a.nframes * a.tiles;
+    const int per = normal ? a.tiles : a.chunks;
+    const int f = w / per;
+    const int piece = w - f * per;
+    const PFrame fr = a.frames[f];
+
+    // ---- wait for the previous phase of this frame ----
+    if (threadIdx.x == 0) {
+      bool ok = true;
+      if (normal) {
+        if (k > 0) ok = wait_at_least(g.upd_ready + f, k);
+      } else {
+        ok = wait_at_least(g.nrm_ready + f, k + 1);
+      }
+      if (!ok) atomicOr(a.err, ERR_TIMEOUT);
+      s_ok = ok ? 1 : 0;
+      s_active = ok ? __ldcg(g.active + f) : 0;
+    }
+    __syncthreads();
+    const bool work = s_ok && s_active;
+
+    if (normal) {
+      if (work) {
+        // line map of this frame
+        for (int i = threadIdx.x; i < N; i += T) s.map[i] = -1;
+        __syncthreads();
+        for (int l = threadIdx.x; l < fr.L; l += T) {
+          const int v = __ldg(fr.lines + l);
+          const bool good = v >= 0 && v < N && (l == 0 || __ldg(fr.lines + l - 1) < v);
+          if (good)
+            s.map[v] = (short)l;
+          else
+            atomicOr(a.err, ERR_LINES);
+        }
+        __syncthreads();
+        const unsigned keep = sampled_bits<C>(s);
+        NormalTile nt;
+        nt.p_src = fr.p[k > 0 ? ((k - 1) & 1) : 0];
+        nt.p_dst = fr.p[k & 1];
+        nt.r = fr.r;
+        nt.q = fr.q;
+        nt.S = fr.S;
+        nt.nx = a.nx;
+        nt.coils = fr.coils;
+        nt.tile = piece;
+        nt.p_update = k > 0 ? 1 : 0;
+        nt.beta = k > 0 ? (float)__ldcg(g.beta + f) : 0.f;
+        const float part = normal_tile<C, St, true>(nt, s, keep);
+        const double tot = block_sum<T>((double)part, s.red);
+        if (threadIdx.x == 0) __stcg(g.part_nrm + (size_t)f * a.tiles + piece, tot);
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(g.nrm_arrive + f, 1u);
+        if (prev == (unsigned)a.tiles - 1u) {  // last tile of the frame: alpha
+          g.nrm_arrive[f] = 0u;
+          __threadfence();
+          if (s_active) {
+            double pq = 0.0;
+            for (int i = 0; i < a.tiles; ++i) pq += __ldcg(g.part_nrm + (size_t)f * a.tiles + i);
+            if (pq > 0.0) {
+              __stcg(g.alpha + f, __ldcg(g.rho + f) / pq);
+            } else {  // breakdown (zero, negative or NaN curvature): freeze the frame
+              __stcg(g.active + f, 0);
+              __stcg(g.outcome + f, CG_BREAKDOWN);
+            }
+          }
+          __threadfence();
+          st_release(g.nrm_ready + f, k + 1);
+        }
+      }
+    } else {
+      float acc = 0.f;
+      if (work) {
+        const float al = (float)__ldcg(g.alpha + f);
+        const float4* pp = reinterpret_cast<const float4*>(fr.p[k & 1]);
+        const float4* qp = reinterpret_cast<const float4*>(fr.q);
+        float4* xp = reinterpret_cast<float4*>(fr.x);
+        float4* rp = reinterpret_cast<float4*>(fr.r);
+        const long img4 = (long)(img / 2);
+        constexpr int VEC = 4;
+        float4 xv[VEC], pv[VEC], qv[VEC], rv[VEC];
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+          const long i = (long)piece * (T * VEC) + j * T + threadIdx.x;
+          const bool ok = i < img4;
+          xv[j] = ok ? __ldcg(xp + i) : z;
+          pv[j] = ok ? __ldcg(pp + i) : z;
+          qv[j] = ok ? __ldcg(qp + i) : z;
+          rv[j] = ok ? __ldcg(rp + i) : z;
+        }
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+          const long i = (long)piece * (T * VEC) + j * T + threadIdx.x;
+          float4 xn = xv[j], rn = rv[j];
+          xn.x = fmaf(al, pv[j].x, xn.x); xn.y = fmaf(al, pv[j].y, xn.y);
+          xn.z = fmaf(al, pv[j].z, xn.z); xn.w = fmaf(al, pv[j].w, xn.w);
+          rn.x = fmaf(-al, qv[j].x, rn.x); rn.y = fmaf(-al, qv[j].y, rn.y);
+          rn.z = fmaf(-al, qv[j].z, rn.z); rn.w = fmaf(-al, qv[j].w, rn.w);
+          if (i < img4) {
+            __stcg(xp + i, xn);
+            __stcg(rp + i, rn);
+            acc = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, acc))));
+          }
+        }
+        const double tot = block_sum<T>((double)acc, s.red);
+        if (threadIdx.x == 0) __stcg(g.part_upd + (size_t)f * a.chunks + piece, tot);
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(g.upd_arrive + f, 1u);
+        if (prev == (unsigned)a.chunks - 1u) {  // last chunk of the frame: beta, stopping test
+          g.upd_arrive[f] = 0u;
+          __threadfence();
+          if (s_active) {
+            double rho_new = 0.0;
+            for (int i = 0; i < a.chunks; ++i) rho_new += __ldcg(g.part_upd + (size_t)f * a.chunks + i);
+            const double rho0 = __ldcg(g.rho0 + f);
+            __stcg(g.iters + f, __ldcg(g.iters + f) + 1);
+            __stcg(g.resid + f, sqrt(rho_new / rho0));
+            const bool stop = (rho_new == 0.0) || (g.tol > 0.0 && sqrt(rho_new / rho0) <= g.tol);
+            if (stop) {
+              __stcg(g.active + f, 0);
+              __stcg(g.outcome + f, CG_CONVERGED);
+            } else {
+              __stcg(g.beta + f, rho_new / __ldcg(g.rho + f));
+            }
+            __stcg(g.rho + f, rho_new);
+          }
+          __threadfence();
+          st_release(g.upd_ready + f, k + 1);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace sense

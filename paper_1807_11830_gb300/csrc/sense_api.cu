@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -75,15 +77,27 @@ class DeviceGuard {
 struct sense_plan {
   sense_shape sh{};
   int device = 0;
-  int tiles = 0;        // column tiles per frame
+  int tiles = 0;        // column tiles per frame (adjoint / forward column passes)
+  int norm_variant = 0;  // kernel variant of the normal operator (autotuned)
+  int norm_tiles = 0;    // column tiles per frame of that variant
+  int cg_mode = 1;       // 0: per-phase kernels replayed as CUDA graphs; 1: one persistent launch
+  int sms = 0;           // multiprocessors of the plan's device
+  PFrame* ptable = nullptr;       // device frame table of the persistent kernel
+  PFrame* ptable_host = nullptr;  // pinned staging copy
+  const void* ptable_key[3] = {nullptr, nullptr, nullptr};  // S, lines, x the table was built for
+  int* pints = nullptr;           // nrm_arrive, upd_arrive, nrm_ready, upd_ready ([4][F]), ticket
+  double* part_nrm = nullptr;     // [F][max tiles]
+  double* part_upd = nullptr;     // [F][max chunks]
+  int max_chunks = 0;
   int upd_blocks = 0;   // CG-update blocks per frame
   size_t img = 0;       // ny * nx
   float2* tw_y = nullptr;
   float2* tw_x = nullptr;
   float2* tmp = nullptr;  // [F][C][L][nx] intermediate of E / E^H
   float2* r = nullptr;
-  float2* p = nullptr;
+  float2* pp[2] = {nullptr, nullptr};  // search directions, ping-pong between iterations
   float2* q = nullptr;
+
   double* dbl = nullptr;  // rho, rho0, alpha, beta, resid  ([5][F])
   int* ints = nullptr;    // iters, outcome, active ([3][F]), live, err
   unsigned* counter = nullptr;
@@ -185,6 +199,8 @@ void release(sense_plan* pl) {
   pl->allocs.clear();
   if (pl->live_host) cudaFreeHost(pl->live_host);
   pl->live_host = nullptr;
+  if (pl->ptable_host) cudaFreeHost(pl->ptable_host);
+  pl->ptable_host = nullptr;
   if (pl->capture_stream) cudaStreamDestroy(pl->capture_stream);
   pl->capture_stream = nullptr;
 }
@@ -280,7 +296,7 @@ sense_status run_adjoint(sense_plan* pl, int mode, const void* y, const void* S,
   a.tw = pl->tw_y;
   a.x = x;
   a.r = pl->r;
-  a.p = pl->p;
+  a.p = pl->pp[0];
   a.nx = sh.nx;
   a.coils = sh.coils;
   a.L = sh.lines;
@@ -304,20 +320,24 @@ sense_status run_normal(sense_plan* pl, const float2* x, const void* S, const in
   a.nx = sh.nx;
   a.coils = sh.coils;
   a.L = sh.lines;
-  a.tiles = pl->tiles;
+  a.tiles = pl->norm_tiles;
   a.err = pl->err();
   PhaseScope ps(pl, SENSE_PHASE_NORMAL, st);
-  return launch_status(launch_normal<St>(sh.ny, false, a, pl->tiles, sh.frames, st), "normal operator");
+  return launch_status(launch_normal<St>(sh.ny, pl->norm_variant, false, a, sh.frames, st), "normal operator");
 }
 
-// One CG iteration: q = E^H E p (with p = r + beta p first when p_update),
-// alpha; then x += alpha p, r -= alpha q, beta / stopping test.
+// Iteration k of CG: q = E^H E p_k (p_k = r + beta p_{k-1} formed on the fly
+// for k > 0), alpha; then x += alpha p_k, r -= alpha q, beta / stopping test.
+// p_k lives in pp[k & 1]; p_0 = r_0 is written by the CG start into pp[0].
 template <class St>
-sense_status run_cg_iteration(sense_plan* pl, const void* S, const int* lines, float2* x, int p_update,
-                              double tol, cudaStream_t st) {
+sense_status run_cg_iteration(sense_plan* pl, const void* S, const int* lines, float2* x, int k, double tol,
+                              cudaStream_t st) {
   const sense_shape& sh = pl->sh;
+  const int p_update = k > 0 ? 1 : 0;
+  float2* p_cur = pl->pp[k & 1];
   NormalArgs<St> a{};
-  a.p = pl->p;
+  a.p_src = p_update ? pl->pp[(k - 1) & 1] : p_cur;
+  a.p_dst = p_cur;
   a.r = pl->r;
   a.q = pl->q;
   a.S = static_cast<const typename St::T*>(S);
@@ -326,19 +346,19 @@ sense_status run_cg_iteration(sense_plan* pl, const void* S, const int* lines, f
   a.nx = sh.nx;
   a.coils = sh.coils;
   a.L = sh.lines;
-  a.tiles = pl->tiles;
+  a.tiles = pl->norm_tiles;
   a.p_update = p_update;
   a.err = pl->err();
   a.cg = pl->cg(tol);
   sense_status rc;
   {
     PhaseScope ps(pl, SENSE_PHASE_CG_NORMAL, st);
-    rc = launch_status(launch_normal<St>(sh.ny, true, a, pl->tiles, sh.frames, st), "CG normal pass");
+    rc = launch_status(launch_normal<St>(sh.ny, pl->norm_variant, true, a, sh.frames, st), "CG normal pass");
   }
   if (rc != SENSE_OK) return rc;
   UpdateArgs u{};
   u.x = reinterpret_cast<float4*>(x);
-  u.p = reinterpret_cast<const float4*>(pl->p);
+  u.p = reinterpret_cast<const float4*>(p_cur);
   u.q = reinterpret_cast<const float4*>(pl->q);
   u.r = reinterpret_cast<float4*>(pl->r);
   u.img4 = (long)(pl->img / 2);
@@ -353,7 +373,7 @@ template <class St>
 sense_status run_cg_chunk(sense_plan* pl, const void* S, const int* lines, float2* x, int first, int count,
                           double tol, cudaStream_t st) {
   for (int i = 0; i < count; ++i) {
-    sense_status rc = run_cg_iteration<St>(pl, S, lines, x, (first + i) > 0 ? 1 : 0, tol, st);
+    sense_status rc = run_cg_iteration<St>(pl, S, lines, x, first + i, tol, st);
     if (rc != SENSE_OK) return rc;
   }
   return SENSE_OK;
@@ -365,7 +385,7 @@ template <class St>
 sense_status cg_chunk_graph(sense_plan* pl, const void* S, const int* lines, float2* x, int first, int count,
                             double tol, cudaStream_t st) {
   if (pl->timing) return run_cg_chunk<St>(pl, S, lines, x, first, count, tol, st);
-  const int first_key = first > 0 ? 1 : 0;
+  const int first_key = first == 0 ? 0 : 1 + (first & 1);  // p_update and ping-pong parity
   auto key = std::make_tuple(S, (const void*)lines, (const void*)x, first_key, count, tol);
   auto it = pl->graphs.find(key);
   if (it == pl->graphs.end()) {
@@ -393,7 +413,112 @@ sense_status cg_chunk_graph(sense_plan* pl, const void* S, const int* lines, flo
   return SENSE_OK;
 }
 
+// ---- autotune cache: in-process map, optionally mirrored to a text file ----
+// (SENSE_AUTOTUNE_CACHE=path; one "device ny nx coils frames lines storage variant" per line)
+struct TuneKey {
+  int device, ny, nx, coils, frames, lines, storage;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(device, ny, nx, coils, frames, lines, storage) <
+           std::tie(o.device, o.ny, o.nx, o.coils, o.frames, o.lines, o.storage);
+  }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load_file_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("SENSE_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fh = std::fopen(path, "r");
+  if (!fh) return;
+  TuneKey k{};
+  int v = 0;
+  while (std::fscanf(fh, "%d %d %d %d %d %d %d %d", &k.device, &k.ny, &k.nx, &k.coils, &k.frames, &k.lines,
+                     &k.storage, &v) == 8)
+    if (v >= 0 && v < kNormVariants && normal_variant_width(k.ny, v) > 0) g_tune[k] = v;
+  std::fclose(fh);
+}
+
+int tune_cache_lookup(const TuneKey& k) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_load_file_locked();
+  auto it = g_tune.find(k);
+  return it == g_tune.end() ? -1 : it->second;
+}
+
+void tune_cache_store(const TuneKey& k, int v) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_load_file_locked();
+  g_tune[k] = v;
+  const char* path = std::getenv("SENSE_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fh = std::fopen(path, "a");
+  if (!fh) return;
+  std::fprintf(fh, "%d %d %d %d %d %d %d %d\n", k.device, k.ny, k.nx, k.coils, k.frames, k.lines, k.storage, v);
+  std::fclose(fh);
+}
+
 constexpr int kPollEvery = 5;
+
+// All CG iterations in one persistent launch (see persistent.cuh).
+template <class St>
+sense_status run_cg_persistent(sense_plan* pl, const void* S, const int* lines, float2* x, int max_iter, double tol,
+                               cudaStream_t st) {
+  const sense_shape& sh = pl->sh;
+  const int F = sh.frames;
+  if (pl->ptable_key[0] != S || pl->ptable_key[1] != (const void*)lines || pl->ptable_key[2] != (const void*)x) {
+    SENSE_CUDA_TRY(cudaStreamSynchronize(st));  // the staging copy may still be read by an earlier call
+    for (int f = 0; f < F; ++f) {
+      PFrame& fr = pl->ptable_host[f];
+      fr.S = S;
+      fr.lines = lines + (size_t)f * sh.lines;
+      fr.x = x + (size_t)f * pl->img;
+      fr.r = pl->r + (size_t)f * pl->img;
+      fr.p[0] = pl->pp[0] + (size_t)f * pl->img;
+      fr.p[1] = pl->pp[1] + (size_t)f * pl->img;
+      fr.q = pl->q + (size_t)f * pl->img;
+      fr.coils = sh.coils;
+      fr.L = sh.lines;
+    }
+    SENSE_CUDA_TRY(cudaMemcpyAsync(pl->ptable, pl->ptable_host, sizeof(PFrame) * F, cudaMemcpyHostToDevice, st));
+    pl->ptable_key[0] = S;
+    pl->ptable_key[1] = lines;
+    pl->ptable_key[2] = x;
+  }
+  SENSE_CUDA_TRY(cudaMemsetAsync(pl->pints, 0, sizeof(int) * (4 * (size_t)F + 1), st));
+  const int threads = normal_variant_threads(sh.ny, pl->norm_variant);
+  PArgs a{};
+  a.frames = pl->ptable;
+  a.nframes = F;
+  a.nx = sh.nx;
+  a.tiles = pl->norm_tiles;
+  a.chunks = (int)((pl->img / 2 + (size_t)threads * 4 - 1) / ((size_t)threads * 4));
+  a.iters = max_iter;
+  a.ticket = reinterpret_cast<unsigned*>(pl->pints + 4 * F);
+  a.tw = pl->tw_y;
+  a.err = pl->err();
+  const CgState g = pl->cg(tol);
+  a.st.rho = g.rho;
+  a.st.rho0 = g.rho0;
+  a.st.alpha = g.alpha;
+  a.st.beta = g.beta;
+  a.st.resid = g.resid;
+  a.st.iters = g.iters;
+  a.st.outcome = g.outcome;
+  a.st.active = g.active;
+  a.st.nrm_arrive = reinterpret_cast<unsigned*>(pl->pints);
+  a.st.upd_arrive = reinterpret_cast<unsigned*>(pl->pints + F);
+  a.st.nrm_ready = pl->pints + 2 * F;
+  a.st.upd_ready = pl->pints + 3 * F;
+  a.st.part_nrm = pl->part_nrm;
+  a.st.part_upd = pl->part_upd;
+  a.st.tol = tol;
+  if (a.chunks > pl->max_chunks) return fail(SENSE_EINVAL, "internal: update chunks exceed the workspace");
+  PhaseScope ps(pl, SENSE_PHASE_CG_PERSISTENT, st);
+  return launch_status(launch_cg_persistent<St>(sh.ny, pl->norm_variant, a, pl->sms, st), "persistent CG");
+}
 
 template <class St>
 sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const int* lines, int max_iter, double tol,
@@ -403,9 +528,15 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
   SENSE_CUDA_TRY(cudaMemsetAsync(pl->cg(tol).live, 0, sizeof(int), st));
   sense_status rc = run_adjoint<St>(pl, 1, y, S, lines, x, nullptr, tol, st);
   if (rc != SENSE_OK) return rc;
+  if (pl->cg_mode == 1) {
+    if (max_iter > 0) rc = run_cg_persistent<St>(pl, S, lines, x, max_iter, tol, st);
+    if (rc != SENSE_OK) return rc;
+    k_cg_finish<<<(sh.frames + 127) / 128, 128, 0, st>>>(pl->cg(tol), sh.frames, iters_out, resid_out, outcome_out);
+    return launch_status(cudaGetLastError(), "CG finish");
+  }
   {  // kernel attributes are set outside stream capture
     NormalArgs<St> none{};
-    rc = launch_status(launch_normal<St>(sh.ny, true, none, 0, 0, st), "CG normal set-up");
+    rc = launch_status(launch_normal<St>(sh.ny, pl->norm_variant, true, none, 0, st), "CG normal set-up");
     if (rc != SENSE_OK) return rc;
   }
   if (tol <= 0.0) {
@@ -453,21 +584,39 @@ sense_status sense_plan_create(const sense_shape* shape, int device, sense_plan*
   pl->tiles = (sh.nx + W - 1) / W;
   pl->img = (size_t)sh.ny * sh.nx;
   pl->upd_blocks = (int)((pl->img + UPD_PER_BLOCK - 1) / UPD_PER_BLOCK);
+  pl->norm_variant = 0;
+  pl->norm_tiles = (sh.nx + normal_variant_width(sh.ny, 0) - 1) / normal_variant_width(sh.ny, 0);
   pl->part_stride = pl->tiles > pl->upd_blocks ? pl->tiles : pl->upd_blocks;
+  const int max_tiles = (sh.nx + 7) / 8;  // narrowest tile of any variant
+  if (pl->part_stride < max_tiles) pl->part_stride = max_tiles;
+  {
+    int min_threads = 1 << 30;
+    for (int v = 0; v < kNormVariants; ++v) {
+      const int th = normal_variant_threads(sh.ny, v);
+      if (th > 0 && th < min_threads) min_threads = th;
+    }
+    pl->max_chunks = (int)((pl->img / 2 + (size_t)min_threads * 4 - 1) / ((size_t)min_threads * 4));
+  }
   const size_t F = (size_t)sh.frames;
   if ((rc = dalloc(pl, &pl->tw_y, (size_t)sh.ny)) != SENSE_OK ||
       (rc = dalloc(pl, &pl->tw_x, (size_t)sh.nx)) != SENSE_OK ||
       (rc = dalloc(pl, &pl->tmp, F * sh.coils * sh.lines * sh.nx)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->r, F * pl->img)) != SENSE_OK || (rc = dalloc(pl, &pl->p, F * pl->img)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->r, F * pl->img)) != SENSE_OK || (rc = dalloc(pl, &pl->pp[0], F * pl->img)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->pp[1], F * pl->img)) != SENSE_OK ||
       (rc = dalloc(pl, &pl->q, F * pl->img)) != SENSE_OK || (rc = dalloc(pl, &pl->dbl, 5 * F)) != SENSE_OK ||
       (rc = dalloc(pl, &pl->ints, 3 * F + 2)) != SENSE_OK ||
       (rc = dalloc(pl, &pl->counter, F)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->part, F * pl->part_stride)) != SENSE_OK) {
+      (rc = dalloc(pl, &pl->part, F * pl->part_stride)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->ptable, F)) != SENSE_OK || (rc = dalloc(pl, &pl->pints, 4 * F + 1)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->part_nrm, F * (size_t)max_tiles)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->part_upd, F * (size_t)pl->max_chunks)) != SENSE_OK) {
     release(pl);
     delete pl;
     return rc;
   }
   cudaError_t e = cudaMallocHost(&pl->live_host, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&pl->ptable_host, sizeof(PFrame) * F);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->capture_stream, cudaStreamNonBlocking);
   std::vector<float2> ty = twiddles(sh.ny), tx = twiddles(sh.nx);
   if (e == cudaSuccess) e = cudaMemcpy(pl->tw_y, ty.data(), sizeof(float2) * ty.size(), cudaMemcpyHostToDevice);
@@ -588,6 +737,111 @@ sense_status sense_plan_phase_time(sense_plan* pl, int phase, double* ms_total, 
   if (ms_total) *ms_total = pl->phase_ms[phase];
   if (launches) *launches = pl->phase_launches[phase];
   return SENSE_OK;
+}
+
+sense_status sense_plan_set_cg_mode(sense_plan* pl, int mode) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (mode != 0 && mode != 1) return fail(SENSE_EINVAL, "CG mode must be 0 (graph) or 1 (persistent)");
+  pl->cg_mode = mode;
+  return SENSE_OK;
+}
+
+sense_status sense_plan_set_variant(sense_plan* pl, int variant) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  const int W = (variant >= 0 && variant < kNormVariants) ? normal_variant_width(pl->sh.ny, variant) : 0;
+  if (W <= 0) return fail(SENSE_EINVAL, "no such normal-operator variant for ny=" + std::to_string(pl->sh.ny));
+  DeviceGuard guard(pl->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : pl->graphs) cudaGraphExecDestroy(kv.second);  // graphs bake the old variant in
+  pl->graphs.clear();
+  pl->norm_variant = variant;
+  pl->norm_tiles = (pl->sh.nx + W - 1) / W;
+  return SENSE_OK;
+}
+
+int sense_plan_variant(const sense_plan* pl) { return pl ? pl->norm_variant : -1; }
+
+sense_status sense_plan_autotune(sense_plan* pl, const void* S, const int32_t* lines, int* variant_out,
+                                 double* ms_out, void* stream) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (!aligned16(S) || !aligned4(lines)) return fail(SENSE_EINVAL, "S must be 16-byte aligned, lines 4-byte");
+  DeviceGuard guard(pl->device);
+  const sense_shape& sh = pl->sh;
+  const TuneKey key{pl->device, sh.ny, sh.nx, sh.coils, sh.frames, sh.lines, sh.storage};
+  int best = tune_cache_lookup(key);
+  if (ms_out)
+    for (int v = 0; v < kNormVariants; ++v) ms_out[v] = -1.0;
+  cudaStream_t st = as_stream(stream);
+  if (best < 0) {
+    SENSE_CUDA_TRY(cudaMemsetAsync(pl->r, 0, sizeof(float2) * pl->img * sh.frames, st));
+    cudaEvent_t a = nullptr, b = nullptr;
+    SENSE_CUDA_TRY(cudaEventCreate(&a));
+    SENSE_CUDA_TRY(cudaEventCreate(&b));
+    double best_ms = 1e30;
+    const int saved_timing = pl->timing;
+    pl->timing = 0;
+    for (int v = 0; v < kNormVariants; ++v) {
+      if (normal_variant_width(sh.ny, v) <= 0) continue;
+      sense_status rc = sense_plan_set_variant(pl, v);
+      if (rc != SENSE_OK) break;
+      for (int it = 0; it < 3; ++it) {  // warm-up
+        rc = sh.storage == SENSE_STORE_BF16 ? run_normal<StBF16>(pl, pl->r, S, lines, pl->q, st)
+                                            : run_normal<StC64>(pl, pl->r, S, lines, pl->q, st);
+        if (rc != SENSE_OK) break;
+      }
+      const int reps = 10;
+      cudaEventRecord(a, st);
+      for (int it = 0; it < reps && rc == SENSE_OK; ++it)
+        rc = sh.storage == SENSE_STORE_BF16 ? run_normal<StBF16>(pl, pl->r, S, lines, pl->q, st)
+                                            : run_normal<StC64>(pl, pl->r, S, lines, pl->q, st);
+      cudaEventRecord(b, st);
+      if (rc != SENSE_OK) {
+        pl->timing = saved_timing;
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return rc;
+      }
+      float ms = 0.f;
+      cudaEventSynchronize(b);
+      cudaEventElapsedTime(&ms, a, b);
+      const double per = ms / reps;
+      if (ms_out) ms_out[v] = per;
+      if (per < best_ms) {
+        best_ms = per;
+        best = v;
+      }
+    }
+    pl->timing = saved_timing;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (best < 0) return fail(SENSE_ECUDA, "autotune found no runnable variant");
+    tune_cache_store(key, best);
+  }
+  sense_status rc = sense_plan_set_variant(pl, best);
+  if (rc != SENSE_OK) return rc;
+  if (variant_out) *variant_out = best;
+  return SENSE_OK;
+}
+
+sense_status sense_selftest_wait(int device, long max_spins) {
+  if (max_spins < 1 || max_spins > (1L << 20)) return fail(SENSE_EINVAL, "max_spins must be in [1, 2^20]");
+  int ndev = 0;
+  SENSE_CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(SENSE_EINVAL, "device index out of range");
+  DeviceGuard guard(device);
+  int* d = nullptr;  // [0] the flag nobody sets, [1] the result
+  SENSE_CUDA_TRY(cudaMalloc(&d, 2 * sizeof(int)));
+  int res[2] = {0, -1};
+  cudaError_t e = cudaMemcpy(d, res, sizeof(res), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 32>>>(d, max_spins, d + 1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(res, d, sizeof(res), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(SENSE_ECUDA, std::string("wait self-test: ") + cudaGetErrorString(e));
+  if (res[1] == 1) return fail(SENSE_ETIMEOUT, "the bounded wait gave up as designed");
+  return fail(SENSE_ECUDA, "the bounded wait returned without timing out");
 }
 
 sense_status sense_plan_check(sense_plan* pl, void* stream) {

@@ -33,10 +33,13 @@ EXPORTED = (
     "sense_size_supported", "sense_plan_create", "sense_plan_destroy", "sense_plan_workspace_bytes",
     "sense_forward", "sense_adjoint", "sense_normal", "sense_cg_solve", "sense_rss", "sense_c32_to_bf16",
     "sense_plan_check", "sense_last_error", "sense_plan_set_timing", "sense_plan_phase_time",
-    "sense_adjoint_noalloc",
+    "sense_adjoint_noalloc", "sense_plan_set_variant", "sense_plan_variant", "sense_plan_autotune",
+    "sense_plan_set_cg_mode", "sense_selftest_wait",
 )
+NORM_VARIANTS = 4
 
-PHASES = ("rows_fwd", "rows_inv", "fwd_col", "adj_col", "normal", "cg_normal", "cg_update")
+PHASES = ("rows_fwd", "rows_inv", "fwd_col", "adj_col", "normal", "cg_normal", "cg_update", "cg_persistent")
+CG_MODE_GRAPH, CG_MODE_PERSISTENT = 0, 1
 
 
 class SenseError(RuntimeError):
@@ -87,6 +90,16 @@ def load_library(path=LIB_PATH):
     lib.sense_plan_phase_time.restype = st
     lib.sense_adjoint_noalloc.argtypes = [ctypes.POINTER(_Shape), vp, vp, vp, vp, vp]
     lib.sense_adjoint_noalloc.restype = st
+    lib.sense_plan_set_variant.argtypes = [vp, i]
+    lib.sense_plan_set_variant.restype = st
+    lib.sense_plan_variant.argtypes = [vp]
+    lib.sense_plan_variant.restype = i
+    lib.sense_plan_autotune.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), vp]
+    lib.sense_plan_autotune.restype = st
+    lib.sense_plan_set_cg_mode.argtypes = [vp, i]
+    lib.sense_plan_set_cg_mode.restype = st
+    lib.sense_selftest_wait.argtypes = [i, ctypes.c_long]
+    lib.sense_selftest_wait.restype = st
     lib.sense_last_error.argtypes = []
     lib.sense_last_error.restype = ctypes.c_char_p
     _LIB = lib
@@ -212,6 +225,32 @@ def sense_plan_phase_time(plan, phase):
     n = ctypes.c_long()
     _check(load_library().sense_plan_phase_time(plan.handle, idx, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def sense_plan_set_cg_mode(plan, mode):
+    _check(load_library().sense_plan_set_cg_mode(plan.handle, int(mode)))
+
+
+def sense_plan_set_variant(plan, variant):
+    _check(load_library().sense_plan_set_variant(plan.handle, int(variant)))
+
+
+def sense_plan_variant(plan):
+    return load_library().sense_plan_variant(plan.handle)
+
+
+def sense_plan_autotune(plan, S, lines, stream=None):
+    """Time the normal-operator variants on this plan; returns (chosen, {variant: ms})."""
+    v = ctypes.c_int(-1)
+    ms = (ctypes.c_double * NORM_VARIANTS)()
+    _check(load_library().sense_plan_autotune(plan.handle, _ptr(S), _ptr(lines), ctypes.byref(v), ms,
+                                              _stream(stream)))
+    return v.value, {k: ms[k] for k in range(NORM_VARIANTS) if ms[k] >= 0}
+
+
+def sense_selftest_wait(device=0, max_spins=1000):
+    """Returns the status of the bounded-wait self-test (5 = SENSE_ETIMEOUT expected)."""
+    return load_library().sense_selftest_wait(int(device), int(max_spins))
 
 
 def to_bf16_pairs(t, stream=None):

@@ -162,6 +162,7 @@ def test_cg_reuses_captured_graph():
     p = synth.single_slice_64()
     y = oracle.forward(p.x_true, p.S, p.lines) + p.noise
     plan = make_plan(p.S, p.lines)
+    sense.sense_plan_set_cg_mode(plan, sense.CG_MODE_GRAPH)
     a = gpu_cg(y, p.S, p.lines, 10, plan=plan)
     b = gpu_cg(y, p.S, p.lines, 10, plan=plan)
     np.testing.assert_array_equal(a[0], b[0])
@@ -202,3 +203,93 @@ def test_rss(shape):
     _, S, lines, y = _problem(shape, 4000 + sum(shape))
     ny = shape[0]
     assert rel(gpu_rss(y, lines, ny), oracle.rss(_as32(y), lines, ny)) <= OP_TOL
+
+
+VARIANT_SHAPES = [(128, 128, 5, 40, 2), (192, 192, 6, 48, 1), (256, 256, 12, 64, 2), (320, 320, 6, 107, 1),
+                  (384, 384, 4, 96, 1), (256, 96, 3, 64, 1)]
+
+
+@pytest.mark.parametrize("shape", VARIANT_SHAPES, ids=lambda s: "%dx%d_c%d" % s[:3])
+def test_normal_every_variant(shape):
+    ny, nx, C, L, F = shape
+    x, S, lines, _ = _problem(shape, 5000 + sum(shape))
+    expect = oracle.normal(_as32(x), _as32(S), lines)
+    plan = make_plan(S, lines)
+    seen = 0
+    for v in range(sense.NORM_VARIANTS):
+        try:
+            sense.sense_plan_set_variant(plan, v)
+        except sense.SenseError:
+            continue
+        seen += 1
+        out = torch.empty((F, ny, nx), dtype=torch.complex64, device="cuda:0")
+        sense.sense_normal(plan, c64(x), c64(S), i32(lines), out)
+        sense.sense_plan_check(plan)
+        assert rel(out.cpu().numpy(), expect) <= OP_TOL, v
+    assert seen >= 1
+
+
+def test_cg_every_variant_and_autotune():
+    p = synth.cine_256(frames=3)
+    y = oracle.forward(p.x_true, p.S, p.lines) + p.noise
+    xo, io, _, _ = oracle.cg(_as32(y), _as32(p.S), p.lines, 8)
+    plan = make_plan(p.S, p.lines)
+    for v in range(sense.NORM_VARIANTS):
+        try:
+            sense.sense_plan_set_variant(plan, v)
+        except sense.SenseError:
+            continue
+        xg, ig, _, _ = gpu_cg(y, p.S, p.lines, 8, plan=plan)
+        assert rel(xg, xo) <= CG_TOL, v
+    chosen, times = sense.sense_plan_autotune(plan, c64(p.S), i32(p.lines))
+    assert chosen in times and len(times) >= 2
+    assert sense.sense_plan_variant(plan) == chosen
+    print("autotune 256^2 C12 F3:", chosen, times)
+
+
+@pytest.mark.parametrize("which", ["slice64", "cine256", "slices320", "mix192"])
+def test_cg_both_modes_match_oracle(which):
+    """The persistent single-launch CG and the per-phase graph CG both match
+    the oracle; iteration counts and outcomes agree."""
+    if which == "slice64":
+        p = synth.single_slice_64()
+        sel, K = [0], 10
+    elif which == "cine256":
+        p = synth.cine_256(frames=4)
+        sel, K = [0, 1, 2, 3], 12
+    elif which == "slices320":
+        p = synth.slices_320(frames=2)
+        sel, K = [0, 1], 6
+    else:
+        p = synth.mix_instance(dict(n=192, coils=9, frames=3, accel=3, lines=64, centre=12), 77)
+        sel, K = [0, 1, 2], 15
+    y = oracle.forward(p.x_true[sel], p.S, p.lines[sel]) + p.noise[sel]
+    lines = p.lines[sel]
+    xo, io, _, so = oracle.cg(_as32(y), _as32(p.S), lines, K)
+    for mode in (sense.CG_MODE_PERSISTENT, sense.CG_MODE_GRAPH):
+        plan = make_plan(p.S, lines)
+        sense.sense_plan_set_cg_mode(plan, mode)
+        xg, ig, _, sg = gpu_cg(y, p.S, lines, K, plan=plan)
+        assert rel(xg, xo) <= CG_TOL, mode
+        np.testing.assert_array_equal(ig, io)
+        np.testing.assert_array_equal(sg, so)
+
+
+def test_cg_persistent_tolerance_stop():
+    p = synth.cine_256(frames=3)
+    y = oracle.forward(p.x_true, p.S, p.lines) + p.noise
+    tol = 2e-3
+    xo, io, ro, so = oracle.cg(_as32(y), _as32(p.S), p.lines, 60, tol)
+    plan = make_plan(p.S, p.lines)
+    sense.sense_plan_set_cg_mode(plan, sense.CG_MODE_PERSISTENT)
+    xg, ig, rg, sg = gpu_cg(y, p.S, p.lines, 60, tol=tol, plan=plan)
+    assert np.all(sg == sense.CG_CONVERGED) and np.all(rg <= tol)
+    assert np.all(np.abs(ig.astype(int) - io.astype(int)) <= 1)
+
+
+def test_bounded_wait_gives_up_and_device_stays_usable():
+    assert sense.sense_selftest_wait(0, 2000) == 5  # SENSE_ETIMEOUT
+    p = synth.single_slice_64()
+    y = oracle.forward(p.x_true, p.S, p.lines) + p.noise
+    xg, ig, _, _ = gpu_cg(y, p.S, p.lines, 3)
+    assert list(ig) == [3]
