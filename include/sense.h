@@ -156,6 +156,50 @@ sense_status sense_cg_solve(sense_plan* plan, const void* y, const void* S, cons
                             double rel_tol, sense_c32* x_out, int32_t* iters_out, double* rel_resid_out,
                             int32_t* outcome_out, void* stream);
 
+/* ---- Uneven batching ----
+ * A batch holds many independent CG-SENSE problems ("instances") of
+ * different ny x nx, coil count, frame count and line count.  Instances are
+ * grouped by (ny, nx, storage) into size classes; every CG iteration of every
+ * frame of a class runs in one persistent launch (see
+ * sense_plan_set_cg_mode), and the whole solve -- CG start of each instance,
+ * one persistent launch per class, per-instance outputs -- is captured once
+ * per argument set into a CUDA graph and replayed.  Each frame's iterates
+ * depend only on its own data and its class's kernel variant, so an instance
+ * gives the same result alone (a plan with the same variant and persistent
+ * mode) as inside the batch. */
+typedef struct sense_batch sense_batch;
+
+/* Per-instance arguments of a batch solve (device pointers; layouts and
+ * alignment as for sense_cg_solve; the outputs other than x_out may be NULL). */
+typedef struct {
+  const void* y;
+  const void* S;
+  const int32_t* lines;
+  sense_c32* x_out;
+  int32_t* iters_out;
+  double* rel_resid_out;
+  int32_t* outcome_out;
+} sense_batch_io;
+
+/* Create a batch of `count` instances on `device`: one plan per instance
+ * (workspace, CG state) plus per-class scheduling state. */
+sense_status sense_batch_create(const sense_shape* shapes, int count, int device, sense_batch** out);
+sense_status sense_batch_destroy(sense_batch* batch);
+size_t sense_batch_workspace_bytes(const sense_batch* batch);
+/* Number of size classes (persistent launches per solve). */
+int sense_batch_classes(const sense_batch* batch);
+/* Pick each class's normal-operator kernel variant by timing it on the
+ * class member with the most frames (see sense_plan_autotune). */
+sense_status sense_batch_autotune(sense_batch* batch, const sense_batch_io* io, void* stream);
+/* Use kernel variant `variant` for every class of row count `ny`. */
+sense_status sense_batch_set_variant(sense_batch* batch, int ny, int variant);
+/* CG-SENSE on every instance (io[i] for instance i), same stopping rules as
+ * sense_cg_solve, asynchronously on `stream`. */
+sense_status sense_batch_cg_solve(sense_batch* batch, const sense_batch_io* io, int max_iter, double rel_tol,
+                                  void* stream);
+/* Synchronise `stream` and report device-flagged errors of any instance. */
+sense_status sense_batch_check(sense_batch* batch, void* stream);
+
 /* Root sum of squares (Sec. IV-B): out[f][i] = sqrt(sum_c |F2^H(Z_f y_{f,c})[i]|^2),
  * out: [frames][ny][nx] float. S is not used. */
 sense_status sense_rss(sense_plan* plan, const void* y, const int32_t* lines, float* out, void* stream);

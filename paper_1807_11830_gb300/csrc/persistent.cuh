@@ -26,22 +26,25 @@
 
 namespace sense {
 
-// One frame of the table: its instance's maps and its own vectors.
+// One frame of the table: its instance's maps, its own vectors and its own
+// CG scalars (wherever its owner keeps them), so frames of different
+// problems can share one launch.
 struct PFrame {
   const void* S;       // maps [C][N][nx] of the frame's instance (storage type)
   const int* lines;    // this frame's lines [L]
   float2* x;           // [N][nx] image (output)
   float2* r;           // residual
-  float2* p[2];        // search directions, ping-pong by iteration parity
+  float2* p[2];        // search directions, ping-pong by global iteration parity
   float2* q;           // E^H E p
+  double *rho, *rho0, *alpha, *beta, *resid;
+  int *iters, *outcome, *active;
   int coils, L;
+  int k0;              // CG iterations this frame has already done before the launch
 };
 
 struct PState {
-  double *rho, *rho0, *alpha, *beta, *resid;  // [frames]
-  int *iters, *outcome, *active;              // [frames]
   unsigned *nrm_arrive, *upd_arrive;          // [frames] arrivals of the current phase
-  int *nrm_ready, *upd_ready;                 // [frames] iterations whose phase is complete
+  int *nrm_ready, *upd_ready;                 // [frames] launch iterations whose phase is complete
   double *part_nrm, *part_upd;                // [frames][tiles] / [frames][chunks]
   double tol;
 };
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
       }
       if (!ok) atomicOr(a.err, ERR_TIMEOUT);
       s_ok = ok ? 1 : 0;
-      s_active = ok ? __ldcg(g.active + f) : 0;
+      s_active = ok ? __ldcg(fr.active) : 0;
     }
     __syncthreads();
     const bool work = s_ok && s_active;
@@ -136,17 +139,18 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
         }
         __syncthreads();
         const unsigned keep = sampled_bits<C>(s);
+        const int kg = k + fr.k0;  // global iteration index of this frame
         NormalTile nt;
-        nt.p_src = fr.p[k > 0 ? ((k - 1) & 1) : 0];
-        nt.p_dst = fr.p[k & 1];
+        nt.p_src = fr.p[kg > 0 ? ((kg - 1) & 1) : 0];
+        nt.p_dst = fr.p[kg & 1];
         nt.r = fr.r;
         nt.q = fr.q;
         nt.S = fr.S;
         nt.nx = a.nx;
         nt.coils = fr.coils;
         nt.tile = piece;
-        nt.p_update = k > 0 ? 1 : 0;
-        nt.beta = k > 0 ? (float)__ldcg(g.beta + f) : 0.f;
+        nt.p_update = kg > 0 ? 1 : 0;
+        nt.beta = kg > 0 ? (float)__ldcg(fr.beta) : 0.f;
         const float part = normal_tile<C, St, true>(nt, s, keep);
         const double tot = block_sum<T>((double)part, s.red);
         if (threadIdx.x == 0) __stcg(g.part_nrm + (size_t)f * a.tiles + piece, tot);
@@ -162,10 +166,10 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
             double pq = 0.0;
             for (int i = 0; i < a.tiles; ++i) pq += __ldcg(g.part_nrm + (size_t)f * a.tiles + i);
             if (pq > 0.0) {
-              __stcg(g.alpha + f, __ldcg(g.rho + f) / pq);
+              __stcg(fr.alpha, __ldcg(fr.rho) / pq);
             } else {  // breakdown (zero, negative or NaN curvature): freeze the frame
-              __stcg(g.active + f, 0);
-              __stcg(g.outcome + f, CG_BREAKDOWN);
+              __stcg(fr.active, 0);
+              __stcg(fr.outcome, CG_BREAKDOWN);
             }
           }
           __threadfence();
@@ -175,8 +179,8 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
     } else {
       float acc = 0.f;
       if (work) {
-        const float al = (float)__ldcg(g.alpha + f);
-        const float4* pp = reinterpret_cast<const float4*>(fr.p[k & 1]);
+        const float al = (float)__ldcg(fr.alpha);
+        const float4* pp = reinterpret_cast<const float4*>(fr.p[(k + fr.k0) & 1]);
         const float4* qp = reinterpret_cast<const float4*>(fr.q);
         float4* xp = reinterpret_cast<float4*>(fr.x);
         float4* rp = reinterpret_cast<float4*>(fr.r);
@@ -220,17 +224,17 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
           if (s_active) {
             double rho_new = 0.0;
             for (int i = 0; i < a.chunks; ++i) rho_new += __ldcg(g.part_upd + (size_t)f * a.chunks + i);
-            const double rho0 = __ldcg(g.rho0 + f);
-            __stcg(g.iters + f, __ldcg(g.iters + f) + 1);
-            __stcg(g.resid + f, sqrt(rho_new / rho0));
+            const double rho0 = __ldcg(fr.rho0);
+            __stcg(fr.iters, __ldcg(fr.iters) + 1);
+            __stcg(fr.resid, sqrt(rho_new / rho0));
             const bool stop = (rho_new == 0.0) || (g.tol > 0.0 && sqrt(rho_new / rho0) <= g.tol);
             if (stop) {
-              __stcg(g.active + f, 0);
-              __stcg(g.outcome + f, CG_CONVERGED);
+              __stcg(fr.active, 0);
+              __stcg(fr.outcome, CG_CONVERGED);
             } else {
-              __stcg(g.beta + f, rho_new / __ldcg(g.rho + f));
+              __stcg(fr.beta, rho_new / __ldcg(fr.rho));
             }
-            __stcg(g.rho + f, rho_new);
+            __stcg(fr.rho, rho_new);
           }
           __threadfence();
           st_release(g.upd_ready + f, k + 1);

@@ -1,0 +1,98 @@
+// Private definition of the plan object and the host helpers shared by the
+// library's units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+#include "persistent.cuh"
+#include "sense.h"
+
+using sense::CgState;
+using sense::PFrame;
+
+struct sense_plan {
+  sense_shape sh{};
+  int device = 0;
+  int tiles = 0;        // column tiles per frame (adjoint / forward column passes)
+  int norm_variant = 0;  // kernel variant of the normal operator (autotuned)
+  int norm_tiles = 0;    // column tiles per frame of that variant
+  int cg_mode = 1;       // 0: per-phase kernels replayed as CUDA graphs; 1: one persistent launch
+  int sms = 0;           // multiprocessors of the plan's device
+  PFrame* ptable = nullptr;       // device frame table of the persistent kernel
+  PFrame* ptable_host = nullptr;  // pinned staging copy
+  const void* ptable_key[3] = {nullptr, nullptr, nullptr};  // S, lines, x the table was built for
+  int* pints = nullptr;           // nrm_arrive, upd_arrive, nrm_ready, upd_ready ([4][F]), ticket
+  double* part_nrm = nullptr;     // [F][max tiles]
+  double* part_upd = nullptr;     // [F][max chunks]
+  int max_chunks = 0;
+  int upd_blocks = 0;   // CG-update blocks per frame
+  size_t img = 0;       // ny * nx
+  float2* tw_y = nullptr;
+  float2* tw_x = nullptr;
+  float2* tmp = nullptr;  // [F][C][L][nx] intermediate of E / E^H
+  float2* r = nullptr;
+  float2* pp[2] = {nullptr, nullptr};  // search directions, ping-pong between iterations
+  float2* q = nullptr;
+
+  double* dbl = nullptr;  // rho, rho0, alpha, beta, resid  ([5][F])
+  int* ints = nullptr;    // iters, outcome, active ([3][F]), live, err
+  unsigned* counter = nullptr;
+  double* part = nullptr;
+  int part_stride = 0;
+  int* live_host = nullptr;  // pinned
+  size_t ws_bytes = 0;
+  std::vector<void*> allocs;
+  cudaStream_t capture_stream = nullptr;
+  // kernel timers (diagnostic mode): event pairs per launch, summed per phase
+  int timing = 0;
+  double phase_ms[SENSE_PHASE_COUNT] = {};
+  long phase_launches[SENSE_PHASE_COUNT] = {};
+  struct Span { int phase; cudaEvent_t a, b; };
+  std::vector<Span> pending;
+  // CUDA graphs of the CG iteration loop, keyed by the arguments they bake in
+  std::map<std::tuple<const void*, const void*, const void*, int, int, double>, cudaGraphExec_t> graphs;
+
+  CgState cg(double tol) const {
+    CgState g;
+    const int F = sh.frames;
+    g.rho = dbl;
+    g.rho0 = dbl + F;
+    g.alpha = dbl + 2 * F;
+    g.beta = dbl + 3 * F;
+    g.resid = dbl + 4 * F;
+    g.iters = ints;
+    g.outcome = ints + F;
+    g.active = ints + 2 * F;
+    g.live = ints + 3 * F;
+    g.counter = counter;
+    g.part = part;
+    g.part_stride = part_stride;
+    g.tol = tol;
+    return g;
+  }
+  int* err() const { return ints + 3 * sh.frames + 1; }
+};
+
+namespace sense {
+
+// Stores the message sense_last_error() returns on this thread.
+void record_error(const std::string& msg);
+
+// CG start for a plan: b = E^H y into r and p_0, x = 0, per-frame scalars
+// (rho0, active, ...), asynchronously on `st`.
+sense_status plan_cg_start(sense_plan* pl, const void* y, const void* S, const int* lines, float2* x, double tol,
+                           cudaStream_t st);
+
+// Frame-table entries of a plan's frames for the persistent CG kernel.
+void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* x, int k0, PFrame* out);
+
+// Per-frame outputs of a finished CG solve of a plan (iterations, residual,
+// outcome; NULL outputs are skipped).
+sense_status plan_cg_finish(sense_plan* pl, int* iters_out, double* resid_out, int* outcome_out, cudaStream_t st);
+
+}  // namespace sense

@@ -15,6 +15,7 @@
 
 #include "cg_kernels.cuh"
 #include "launch.h"
+#include "plan.h"
 #include "sense.h"
 
 using namespace sense;
@@ -74,68 +75,6 @@ class DeviceGuard {
 
 }  // namespace
 
-struct sense_plan {
-  sense_shape sh{};
-  int device = 0;
-  int tiles = 0;        // column tiles per frame (adjoint / forward column passes)
-  int norm_variant = 0;  // kernel variant of the normal operator (autotuned)
-  int norm_tiles = 0;    // column tiles per frame of that variant
-  int cg_mode = 1;       // 0: per-phase kernels replayed as CUDA graphs; 1: one persistent launch
-  int sms = 0;           // multiprocessors of the plan's device
-  PFrame* ptable = nullptr;       // device frame table of the persistent kernel
-  PFrame* ptable_host = nullptr;  // pinned staging copy
-  const void* ptable_key[3] = {nullptr, nullptr, nullptr};  // S, lines, x the table was built for
-  int* pints = nullptr;           // nrm_arrive, upd_arrive, nrm_ready, upd_ready ([4][F]), ticket
-  double* part_nrm = nullptr;     // [F][max tiles]
-  double* part_upd = nullptr;     // [F][max chunks]
-  int max_chunks = 0;
-  int upd_blocks = 0;   // CG-update blocks per frame
-  size_t img = 0;       // ny * nx
-  float2* tw_y = nullptr;
-  float2* tw_x = nullptr;
-  float2* tmp = nullptr;  // [F][C][L][nx] intermediate of E / E^H
-  float2* r = nullptr;
-  float2* pp[2] = {nullptr, nullptr};  // search directions, ping-pong between iterations
-  float2* q = nullptr;
-
-  double* dbl = nullptr;  // rho, rho0, alpha, beta, resid  ([5][F])
-  int* ints = nullptr;    // iters, outcome, active ([3][F]), live, err
-  unsigned* counter = nullptr;
-  double* part = nullptr;
-  int part_stride = 0;
-  int* live_host = nullptr;  // pinned
-  size_t ws_bytes = 0;
-  std::vector<void*> allocs;
-  cudaStream_t capture_stream = nullptr;
-  // kernel timers (diagnostic mode): event pairs per launch, summed per phase
-  int timing = 0;
-  double phase_ms[SENSE_PHASE_COUNT] = {};
-  long phase_launches[SENSE_PHASE_COUNT] = {};
-  struct Span { int phase; cudaEvent_t a, b; };
-  std::vector<Span> pending;
-  // CUDA graphs of the CG iteration loop, keyed by the arguments they bake in
-  std::map<std::tuple<const void*, const void*, const void*, int, int, double>, cudaGraphExec_t> graphs;
-
-  CgState cg(double tol) const {
-    CgState g;
-    const int F = sh.frames;
-    g.rho = dbl;
-    g.rho0 = dbl + F;
-    g.alpha = dbl + 2 * F;
-    g.beta = dbl + 3 * F;
-    g.resid = dbl + 4 * F;
-    g.iters = ints;
-    g.outcome = ints + F;
-    g.active = ints + 2 * F;
-    g.live = ints + 3 * F;
-    g.counter = counter;
-    g.part = part;
-    g.part_stride = part_stride;
-    g.tol = tol;
-    return g;
-  }
-  int* err() const { return ints + 3 * sh.frames + 1; }
-};
 
 namespace {
 
@@ -470,18 +409,7 @@ sense_status run_cg_persistent(sense_plan* pl, const void* S, const int* lines, 
   const int F = sh.frames;
   if (pl->ptable_key[0] != S || pl->ptable_key[1] != (const void*)lines || pl->ptable_key[2] != (const void*)x) {
     SENSE_CUDA_TRY(cudaStreamSynchronize(st));  // the staging copy may still be read by an earlier call
-    for (int f = 0; f < F; ++f) {
-      PFrame& fr = pl->ptable_host[f];
-      fr.S = S;
-      fr.lines = lines + (size_t)f * sh.lines;
-      fr.x = x + (size_t)f * pl->img;
-      fr.r = pl->r + (size_t)f * pl->img;
-      fr.p[0] = pl->pp[0] + (size_t)f * pl->img;
-      fr.p[1] = pl->pp[1] + (size_t)f * pl->img;
-      fr.q = pl->q + (size_t)f * pl->img;
-      fr.coils = sh.coils;
-      fr.L = sh.lines;
-    }
+    plan_frames(pl, S, lines, x, 0, pl->ptable_host);
     SENSE_CUDA_TRY(cudaMemcpyAsync(pl->ptable, pl->ptable_host, sizeof(PFrame) * F, cudaMemcpyHostToDevice, st));
     pl->ptable_key[0] = S;
     pl->ptable_key[1] = lines;
@@ -499,15 +427,6 @@ sense_status run_cg_persistent(sense_plan* pl, const void* S, const int* lines, 
   a.ticket = reinterpret_cast<unsigned*>(pl->pints + 4 * F);
   a.tw = pl->tw_y;
   a.err = pl->err();
-  const CgState g = pl->cg(tol);
-  a.st.rho = g.rho;
-  a.st.rho0 = g.rho0;
-  a.st.alpha = g.alpha;
-  a.st.beta = g.beta;
-  a.st.resid = g.resid;
-  a.st.iters = g.iters;
-  a.st.outcome = g.outcome;
-  a.st.active = g.active;
   a.st.nrm_arrive = reinterpret_cast<unsigned*>(pl->pints);
   a.st.upd_arrive = reinterpret_cast<unsigned*>(pl->pints + F);
   a.st.nrm_ready = pl->pints + 2 * F;
@@ -560,6 +479,51 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
 }
 
 }  // namespace
+
+namespace sense {
+
+void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* x, int k0, PFrame* out) {
+  const sense_shape& sh = pl->sh;
+  const CgState g = pl->cg(0.0);
+  for (int f = 0; f < sh.frames; ++f) {
+    PFrame& fr = out[f];
+    fr.S = S;
+    fr.lines = lines + (size_t)f * sh.lines;
+    fr.x = x + (size_t)f * pl->img;
+    fr.r = pl->r + (size_t)f * pl->img;
+    fr.p[0] = pl->pp[0] + (size_t)f * pl->img;
+    fr.p[1] = pl->pp[1] + (size_t)f * pl->img;
+    fr.q = pl->q + (size_t)f * pl->img;
+    fr.rho = g.rho + f;
+    fr.rho0 = g.rho0 + f;
+    fr.alpha = g.alpha + f;
+    fr.beta = g.beta + f;
+    fr.resid = g.resid + f;
+    fr.iters = g.iters + f;
+    fr.outcome = g.outcome + f;
+    fr.active = g.active + f;
+    fr.coils = sh.coils;
+    fr.L = sh.lines;
+    fr.k0 = k0;
+  }
+}
+
+sense_status plan_cg_start(sense_plan* pl, const void* y, const void* S, const int* lines, float2* x, double tol,
+                           cudaStream_t st) {
+  const sense_shape& sh = pl->sh;
+  SENSE_CUDA_TRY(cudaMemsetAsync(pl->counter, 0, sizeof(unsigned) * sh.frames, st));
+  SENSE_CUDA_TRY(cudaMemsetAsync(pl->cg(tol).live, 0, sizeof(int), st));
+  if (sh.storage == SENSE_STORE_BF16) return run_adjoint<StBF16>(pl, 1, y, S, lines, x, nullptr, tol, st);
+  return run_adjoint<StC64>(pl, 1, y, S, lines, x, nullptr, tol, st);
+}
+
+sense_status plan_cg_finish(sense_plan* pl, int* iters_out, double* resid_out, int* outcome_out, cudaStream_t st) {
+  const int F = pl->sh.frames;
+  k_cg_finish<<<(F + 127) / 128, 128, 0, st>>>(pl->cg(0.0), F, iters_out, resid_out, outcome_out);
+  return launch_status(cudaGetLastError(), "CG finish");
+}
+
+}  // namespace sense
 
 extern "C" {
 

@@ -35,6 +35,8 @@ EXPORTED = (
     "sense_plan_check", "sense_last_error", "sense_plan_set_timing", "sense_plan_phase_time",
     "sense_adjoint_noalloc", "sense_plan_set_variant", "sense_plan_variant", "sense_plan_autotune",
     "sense_plan_set_cg_mode", "sense_selftest_wait",
+    "sense_batch_create", "sense_batch_destroy", "sense_batch_workspace_bytes", "sense_batch_classes",
+    "sense_batch_autotune", "sense_batch_set_variant", "sense_batch_cg_solve", "sense_batch_check",
 )
 NORM_VARIANTS = 4
 
@@ -51,6 +53,12 @@ class SenseError(RuntimeError):
 class _Shape(ctypes.Structure):
     _fields_ = [("ny", ctypes.c_int), ("nx", ctypes.c_int), ("coils", ctypes.c_int),
                 ("frames", ctypes.c_int), ("lines", ctypes.c_int), ("storage", ctypes.c_int)]
+
+
+class _BatchIO(ctypes.Structure):
+    _fields_ = [("y", ctypes.c_void_p), ("S", ctypes.c_void_p), ("lines", ctypes.c_void_p),
+                ("x_out", ctypes.c_void_p), ("iters_out", ctypes.c_void_p), ("rel_resid_out", ctypes.c_void_p),
+                ("outcome_out", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -100,6 +108,23 @@ def load_library(path=LIB_PATH):
     lib.sense_plan_set_cg_mode.restype = st
     lib.sense_selftest_wait.argtypes = [i, ctypes.c_long]
     lib.sense_selftest_wait.restype = st
+    bp = ctypes.POINTER(_BatchIO)
+    lib.sense_batch_create.argtypes = [ctypes.POINTER(_Shape), i, i, ctypes.POINTER(vp)]
+    lib.sense_batch_create.restype = st
+    lib.sense_batch_destroy.argtypes = [vp]
+    lib.sense_batch_destroy.restype = st
+    lib.sense_batch_workspace_bytes.argtypes = [vp]
+    lib.sense_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.sense_batch_classes.argtypes = [vp]
+    lib.sense_batch_classes.restype = i
+    lib.sense_batch_autotune.argtypes = [vp, bp, vp]
+    lib.sense_batch_autotune.restype = st
+    lib.sense_batch_set_variant.argtypes = [vp, i, i]
+    lib.sense_batch_set_variant.restype = st
+    lib.sense_batch_cg_solve.argtypes = [vp, bp, i, ctypes.c_double, vp]
+    lib.sense_batch_cg_solve.restype = st
+    lib.sense_batch_check.argtypes = [vp, vp]
+    lib.sense_batch_check.restype = st
     lib.sense_last_error.argtypes = []
     lib.sense_last_error.restype = ctypes.c_char_p
     _LIB = lib
@@ -257,3 +282,77 @@ def to_bf16_pairs(t, stream=None):
     """complex64 CUDA tensor -> bfloat16 [..., 2] tensor (RNE, in the library's kernel)."""
     out = torch.empty(tuple(t.shape) + (2,), dtype=torch.bfloat16, device=t.device)
     return sense_c32_to_bf16(t.contiguous(), out, stream)
+
+
+class Batch:
+    """Owns a ``sense_batch*``: many instances, one persistent CG launch per size class."""
+
+    def __init__(self, shapes, device=0):
+        lib = load_library()
+        arr = (_Shape * len(shapes))(*[_Shape(d["ny"], d["nx"], d["coils"], d["frames"], d["lines"],
+                                               d.get("storage", STORE_C64)) for d in shapes])
+        h = ctypes.c_void_p()
+        _check(lib.sense_batch_create(arr, len(shapes), device, ctypes.byref(h)))
+        self.handle = h
+        self.count = len(shapes)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load_library().sense_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def classes(self):
+        return load_library().sense_batch_classes(self.handle)
+
+    @property
+    def workspace_bytes(self):
+        return load_library().sense_batch_workspace_bytes(self.handle)
+
+
+def _batch_io(items):
+    """items: list of dicts with y, S, lines, x_out and optional iters_out, rel_resid_out, outcome_out."""
+    arr = (_BatchIO * len(items))()
+    for k, d in enumerate(items):
+        arr[k] = _BatchIO(*[(_ptr(d.get(name)).value if d.get(name) is not None else None)
+                            for name in ("y", "S", "lines", "x_out", "iters_out", "rel_resid_out", "outcome_out")])
+    return arr
+
+
+def sense_batch_create(shapes, device=0):
+    return Batch(shapes, device)
+
+
+def sense_batch_destroy(batch):
+    batch.close()
+
+
+def sense_batch_workspace_bytes(batch):
+    return batch.workspace_bytes
+
+
+def sense_batch_classes(batch):
+    return batch.classes
+
+
+def sense_batch_autotune(batch, items, stream=None):
+    _check(load_library().sense_batch_autotune(batch.handle, _batch_io(items), _stream(stream)))
+
+
+def sense_batch_set_variant(batch, ny, variant):
+    _check(load_library().sense_batch_set_variant(batch.handle, int(ny), int(variant)))
+
+
+def sense_batch_cg_solve(batch, items, max_iter, rel_tol=0.0, stream=None):
+    _check(load_library().sense_batch_cg_solve(batch.handle, _batch_io(items), int(max_iter), float(rel_tol),
+                                               _stream(stream)))
+
+
+def sense_batch_check(batch, stream=None):
+    _check(load_library().sense_batch_check(batch.handle, _stream(stream)))
