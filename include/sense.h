@@ -200,6 +200,67 @@ sense_status sense_batch_cg_solve(sense_batch* batch, const sense_batch_io* io, 
 /* Synchronise `stream` and report device-flagged errors of any instance. */
 sense_status sense_batch_check(sense_batch* batch, void* stream);
 
+/* ---- Serving: request queue with continuous batching ----
+ * A scheduler thread admits submitted reconstructions in arrival order while
+ * the HBM budget and the live-request limit allow, keeps their k-space, maps
+ * and CG state on the device, and advances every live request by one CG
+ * iteration per tick: one persistent launch per size class runs one
+ * iteration of every live frame of that class, whatever iteration each frame
+ * is at.  A request retires when all its frames have stopped (the stopping
+ * rules of sense_cg_solve) or after max_iter ticks; its image is copied to a
+ * pinned host buffer and its device memory released.  Requests that arrive
+ * while others run join at the next tick.  Each size class uses one kernel
+ * variant (autotuned on the first request of the class), so a request's
+ * result equals the same problem solved alone by a plan with that variant
+ * in persistent mode. */
+typedef struct sense_queue sense_queue;
+
+typedef struct {
+  size_t hbm_budget_bytes; /* device bytes requests may hold; 0 = free memory at creation minus 1 GiB */
+  int max_live;            /* most requests admitted at once; 0 = no limit */
+  int fake_device;         /* 1: no GPU work at all -- each tick sleeps fake_tick_us and every frame
+                              "converges" after min(max_iter, fake_iters) ticks (scheduler tests) */
+  int fake_tick_us;
+  int fake_iters;
+  int autotune;            /* 1: autotune each size class on its first request; 0: variant 0 */
+} sense_queue_cfg;
+
+typedef enum {
+  SENSE_REQ_PENDING = 0, SENSE_REQ_RUNNING = 1, SENSE_REQ_DONE = 2, SENSE_REQ_CANCELLED = 3,
+  SENSE_REQ_FAILED = 4
+} sense_req_state;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, cancelled, failed, refused;
+  uint64_t ticks;
+  double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> result ready, completed requests */
+  size_t hbm_in_use, hbm_budget;
+  int live, pending;
+} sense_queue_stats;
+
+sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_queue** out);
+/* Copies the inputs (host memory, layouts of sense_cg_solve) into pinned
+ * staging before returning; the caller's buffers are free on return.  A
+ * request that could never fit the budget is refused with SENSE_EQUEUE_FULL. */
+sense_status sense_queue_submit(sense_queue* q, const sense_shape* shape, const void* y_host, const void* S_host,
+                                const int32_t* lines_host, int max_iter, double rel_tol, uint64_t* req_id);
+/* Non-blocking state of a request; iters = ticks applied so far. */
+sense_status sense_queue_poll(sense_queue* q, uint64_t req_id, int* state, int* iters);
+/* Block until the request has finished (or timeout_s > 0 elapsed:
+ * SENSE_ETIMEOUT), then copy its image [frames][ny][nx] and, if non-NULL,
+ * per-frame iterations / relative residuals / outcomes to host memory and
+ * forget the request.  SENSE_ENOTFOUND for unknown ids, SENSE_EINVAL for a
+ * cancelled request. */
+sense_status sense_queue_wait(sense_queue* q, uint64_t req_id, sense_c32* x_host, int32_t* iters_host,
+                              double* resid_host, int32_t* outcome_host, double timeout_s);
+/* Cancel a pending or running request (it stops at the next tick boundary). */
+sense_status sense_queue_cancel(sense_queue* q, uint64_t req_id);
+sense_status sense_queue_stats_get(sense_queue* q, sense_queue_stats* out);
+/* Kernel variant the queue uses for a size class (-1 if none yet). */
+int sense_queue_variant(sense_queue* q, int ny, int nx, int storage);
+/* Stop the scheduler (running requests are cancelled) and free everything. */
+sense_status sense_queue_destroy(sense_queue* q);
+
 /* Root sum of squares (Sec. IV-B): out[f][i] = sqrt(sum_c |F2^H(Z_f y_{f,c})[i]|^2),
  * out: [frames][ny][nx] float. S is not used. */
 sense_status sense_rss(sense_plan* plan, const void* y, const int32_t* lines, float* out, void* stream);
@@ -216,6 +277,9 @@ sense_status sense_c32_to_bf16(const sense_c32* in, void* out, size_t count, voi
  *     frame, so frames pipeline and no kernel boundary separates phases.
  *   0: two kernels per iteration (normal operator, update), captured once
  *     per argument set into a CUDA graph and replayed.
+ *   2: the same two kernels per iteration launched directly, no graph (the
+ *     plain per-instance loop that batching and serving are measured
+ *     against).
  * Both give the same iterates up to rounding of the inner products' partial
  * sums (the per-tile and per-chunk partitions differ). */
 sense_status sense_plan_set_cg_mode(sense_plan* plan, int mode);

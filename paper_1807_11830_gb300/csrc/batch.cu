@@ -130,7 +130,6 @@ sense_status run_batch(sense_batch* b, const sense_batch_io* io, const std::vect
       a.st.upd_ready = c.ints + 3 * c.frames;
       a.st.part_nrm = c.part_nrm;
       a.st.part_upd = c.part_upd;
-      a.st.tol = tol;
       cudaError_t e = c.storage == SENSE_STORE_BF16
                           ? launch_cg_persistent<StBF16>(c.ny, c.variant, a, b->sms, st)
                           : launch_cg_persistent<StC64>(c.ny, c.variant, a, b->sms, st);
@@ -307,7 +306,7 @@ sense_status sense_batch_cg_solve(sense_batch* b, const sense_batch_io* io, int 
       size_t off = 0;
       for (int i : c.members) {
         sense_plan* p = b->plans[i];
-        plan_frames(p, io[i].S, io[i].lines, reinterpret_cast<float2*>(io[i].x_out), 0, host.data() + off);
+        plan_frames(p, io[i].S, io[i].lines, reinterpret_cast<float2*>(io[i].x_out), 0, rel_tol, host.data() + off);
         off += p->sh.frames;
       }
       PFrame* dev = nullptr;

@@ -40,13 +40,13 @@ struct PFrame {
   int *iters, *outcome, *active;
   int coils, L;
   int k0;              // CG iterations this frame has already done before the launch
+  double tol;          // relative-residual stopping tolerance (0: none)
 };
 
 struct PState {
   unsigned *nrm_arrive, *upd_arrive;          // [frames] arrivals of the current phase
   int *nrm_ready, *upd_ready;                 // [frames] launch iterations whose phase is complete
   double *part_nrm, *part_upd;                // [frames][tiles] / [frames][chunks]
-  double tol;
 };
 
 struct PArgs {
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
             const double rho0 = __ldcg(fr.rho0);
             __stcg(fr.iters, __ldcg(fr.iters) + 1);
             __stcg(fr.resid, sqrt(rho_new / rho0));
-            const bool stop = (rho_new == 0.0) || (g.tol > 0.0 && sqrt(rho_new / rho0) <= g.tol);
+            const bool stop = (rho_new == 0.0) || (fr.tol > 0.0 && sqrt(rho_new / rho0) <= fr.tol);
             if (stop) {
               __stcg(fr.active, 0);
               __stcg(fr.outcome, CG_CONVERGED);

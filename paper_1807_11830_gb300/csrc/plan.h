@@ -26,6 +26,7 @@ struct sense_plan {
   PFrame* ptable = nullptr;       // device frame table of the persistent kernel
   PFrame* ptable_host = nullptr;  // pinned staging copy
   const void* ptable_key[3] = {nullptr, nullptr, nullptr};  // S, lines, x the table was built for
+  double ptable_tol = -1.0;
   int* pints = nullptr;           // nrm_arrive, upd_arrive, nrm_ready, upd_ready ([4][F]), ticket
   double* part_nrm = nullptr;     // [F][max tiles]
   double* part_upd = nullptr;     // [F][max chunks]
@@ -89,7 +90,8 @@ sense_status plan_cg_start(sense_plan* pl, const void* y, const void* S, const i
                            cudaStream_t st);
 
 // Frame-table entries of a plan's frames for the persistent CG kernel.
-void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* x, int k0, PFrame* out);
+void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* x, int k0, double tol,
+                 PFrame* out);
 
 // Per-frame outputs of a finished CG solve of a plan (iterations, residual,
 // outcome; NULL outputs are skipped).

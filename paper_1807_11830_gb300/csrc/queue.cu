@@ -1,0 +1,711 @@
+// Serving: a request queue with continuous (iteration-level) batching.
+//
+// Submitted reconstructions wait in arrival order.  A scheduler thread
+// admits them while the device-memory budget and the live-request limit
+// allow (strict arrival order: the head of the queue blocks those behind
+// it), uploads their inputs, starts CG (b = E^H y) and then ticks: each tick
+// advances every live frame by one CG iteration, with one persistent launch
+// per size class whose frame table holds the live frames of every request of
+// that class, each at its own iteration.  After a tick the scheduler reads
+// back which frames are still iterating; requests whose frames have all
+// stopped, or that reached max_iter, or were cancelled, retire: their image
+// is copied to pinned host memory and their device memory is freed, making
+// room for the next admissions.
+//
+// fake_device mode runs the same scheduler with no GPU work (each tick
+// sleeps; every frame stops after min(max_iter, fake_iters) ticks), so
+// admission, ordering, refusal and cancellation are testable on a CPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "launch.h"
+#include "plan.h"
+#include "sense.h"
+
+using namespace sense;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+__global__ void k_gather_active(const PFrame* table, int n, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __ldcg(table[i].active);
+}
+
+struct Request {
+  uint64_t id = 0;
+  sense_shape sh{};
+  int max_iter = 0;
+  double tol = 0.0;
+  size_t need = 0;      // device bytes reserved for it
+  size_t y_bytes = 0, s_bytes = 0, l_bytes = 0, x_bytes = 0;
+  // pinned host staging (inputs at submit, outputs at retirement)
+  void* y_h = nullptr;
+  void* s_h = nullptr;
+  int* lines_h = nullptr;
+  float2* x_h = nullptr;
+  int* iters_h = nullptr;
+  double* resid_h = nullptr;
+  int* outcome_h = nullptr;
+  // device
+  sense_plan* plan = nullptr;
+  void* y_d = nullptr;
+  void* s_d = nullptr;
+  int* lines_d = nullptr;
+  float2* x_d = nullptr;
+  int* out_i_d = nullptr;  // iters [F], outcome [F]
+  double* resid_d = nullptr;
+  int ticks = 0;
+  int state = SENSE_REQ_PENDING;
+  bool cancel = false;
+  int status_off = 0;  // position of its frames in the tick's status array
+  int cls = -1;
+  Clock::time_point t_submit, t_done;
+};
+
+struct SizeClass {
+  int ny = 0, nx = 0, storage = 0, variant = -1;
+  int cap = 0;  // frames the buffers hold
+  int* ints = nullptr;
+  double* part_nrm = nullptr;
+  double* part_upd = nullptr;
+  int upd_cap = 0;  // chunks per frame the buffer holds
+  PFrame* table_d = nullptr;
+  PFrame* table_h = nullptr;  // pinned
+  int* status_d = nullptr;
+  int* status_h = nullptr;  // pinned
+};
+
+size_t elem_bytes(int storage) { return storage == SENSE_STORE_BF16 ? 4 : 8; }
+
+}  // namespace
+
+struct sense_queue {
+  int device = 0;
+  sense_queue_cfg cfg{};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> pending;
+  std::vector<Request*> live;  // worker thread only
+  std::map<uint64_t, Request*> reqs;
+  uint64_t next_id = 1;
+  size_t budget = 0, in_use = 0;
+  bool stop = false;
+  std::thread worker;
+  sense_queue_stats st{};
+  std::vector<double> lat_ms;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  std::map<std::tuple<int, int, int>, SizeClass> classes;  // worker thread only
+  std::map<std::tuple<int, int, int>, int> variants;         // guarded by mu
+};
+
+namespace {
+
+void free_host(Request* r) {
+  if (r->y_h) cudaFreeHost(r->y_h);
+  if (r->s_h) cudaFreeHost(r->s_h);
+  if (r->lines_h) cudaFreeHost(r->lines_h);
+  r->y_h = r->s_h = nullptr;
+  r->lines_h = nullptr;
+}
+
+void free_outputs(Request* r) {
+  if (r->x_h) cudaFreeHost(r->x_h);
+  if (r->iters_h) cudaFreeHost(r->iters_h);
+  if (r->resid_h) cudaFreeHost(r->resid_h);
+  if (r->outcome_h) cudaFreeHost(r->outcome_h);
+  r->x_h = nullptr;
+  r->iters_h = nullptr;
+  r->resid_h = nullptr;
+  r->outcome_h = nullptr;
+}
+
+void free_device(Request* r) {
+  if (r->plan) sense_plan_destroy(r->plan);
+  r->plan = nullptr;
+  for (void* p : {r->y_d, r->s_d, (void*)r->lines_d, (void*)r->x_d, (void*)r->out_i_d, (void*)r->resid_d})
+    if (p) cudaFree(p);
+  r->y_d = r->s_d = nullptr;
+  r->lines_d = nullptr;
+  r->x_d = nullptr;
+  r->out_i_d = nullptr;
+  r->resid_d = nullptr;
+}
+
+// Device bytes a request holds while live: its inputs, output and the plan's
+// workspace (CG vectors, the k-space intermediate, scalars), with slack.
+size_t request_need(const sense_shape& sh) {
+  const size_t F = sh.frames, img = (size_t)sh.ny * sh.nx;
+  const size_t e = elem_bytes(sh.storage);
+  const size_t inputs = F * sh.coils * sh.lines * sh.nx * e + (size_t)sh.coils * img * e + F * sh.lines * 4;
+  const size_t outputs = F * img * 8 + F * 16;
+  const size_t plan = F * sh.coils * sh.lines * sh.nx * 8 + 4 * F * img * 8;
+  return inputs + outputs + plan + (size_t)(1 << 20);
+}
+
+void record_done(sense_queue* q, Request* r, int state) {
+  std::lock_guard<std::mutex> lock(q->mu);
+  r->state = state;
+  r->t_done = Clock::now();
+  if (state == SENSE_REQ_DONE) {
+    q->st.completed++;
+    q->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+  } else if (state == SENSE_REQ_CANCELLED) {
+    q->st.cancelled++;
+  } else {
+    q->st.failed++;
+  }
+  q->in_use -= std::min(q->in_use, r->need);
+  q->cv_done.notify_all();
+  q->cv_work.notify_all();
+}
+
+bool ensure_class_capacity(sense_queue* q, SizeClass& c, int frames) {
+  if (c.cap >= frames && c.upd_cap > 0) return true;
+  int cap = std::max(frames, std::max(64, c.cap * 2));
+  // free the old buffers (the stream is idle between ticks)
+  for (void* p : {(void*)c.ints, (void*)c.part_nrm, (void*)c.part_upd, (void*)c.table_d, (void*)c.status_d})
+    if (p) cudaFree(p);
+  if (c.table_h) cudaFreeHost(c.table_h);
+  if (c.status_h) cudaFreeHost(c.status_h);
+  int min_threads = 1 << 30;
+  for (int v = 0; v < kNormVariants; ++v) {
+    const int th = normal_variant_threads(c.ny, v);
+    if (th > 0) min_threads = std::min(min_threads, th);
+  }
+  c.upd_cap = (int)(((size_t)c.ny * c.nx / 2 + (size_t)min_threads * 4 - 1) / ((size_t)min_threads * 4));
+  bool ok = cudaMalloc(&c.ints, sizeof(int) * (4 * (size_t)cap + 1)) == cudaSuccess &&
+            cudaMalloc(&c.part_nrm, sizeof(double) * (size_t)cap * ((c.nx + 7) / 8)) == cudaSuccess &&
+            cudaMalloc(&c.part_upd, sizeof(double) * (size_t)cap * c.upd_cap) == cudaSuccess &&
+            cudaMalloc(&c.table_d, sizeof(PFrame) * cap) == cudaSuccess &&
+            cudaMalloc(&c.status_d, sizeof(int) * cap) == cudaSuccess &&
+            cudaMallocHost(&c.table_h, sizeof(PFrame) * cap) == cudaSuccess &&
+            cudaMallocHost(&c.status_h, sizeof(int) * cap) == cudaSuccess;
+  c.cap = ok ? cap : 0;
+  return ok;
+}
+
+// Upload inputs, create the plan, start CG.  Returns false on failure.
+bool admit_device(sense_queue* q, Request* r, std::string* err) {
+  const sense_shape& sh = r->sh;
+  const size_t F = sh.frames;
+  if (sense_plan_create(&sh, q->device, &r->plan) != SENSE_OK) {
+    *err = sense_last_error();
+    return false;
+  }
+  sense_plan_set_cg_mode(r->plan, 1);
+  bool ok = cudaMalloc(&r->y_d, r->y_bytes) == cudaSuccess && cudaMalloc(&r->s_d, r->s_bytes) == cudaSuccess &&
+            cudaMalloc(&r->lines_d, r->l_bytes) == cudaSuccess && cudaMalloc(&r->x_d, r->x_bytes) == cudaSuccess &&
+            cudaMalloc(&r->out_i_d, sizeof(int) * 2 * F) == cudaSuccess &&
+            cudaMalloc(&r->resid_d, sizeof(double) * F) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    *err = "device allocation failed";
+    return false;
+  }
+  ok = cudaMemcpyAsync(r->y_d, r->y_h, r->y_bytes, cudaMemcpyHostToDevice, q->stream) == cudaSuccess &&
+       cudaMemcpyAsync(r->s_d, r->s_h, r->s_bytes, cudaMemcpyHostToDevice, q->stream) == cudaSuccess &&
+       cudaMemcpyAsync(r->lines_d, r->lines_h, r->l_bytes, cudaMemcpyHostToDevice, q->stream) == cudaSuccess;
+  if (!ok) {
+    *err = "input upload failed";
+    return false;
+  }
+  // kernel variant of the size class: autotuned on its first request, then fixed
+  const auto key = std::make_tuple(sh.ny, sh.nx, sh.storage);
+  int variant = -1;
+  {
+    std::lock_guard<std::mutex> lock(q->mu);
+    auto it = q->variants.find(key);
+    if (it != q->variants.end()) variant = it->second;
+  }
+  if (variant < 0) {
+    variant = 0;
+    if (q->cfg.autotune) {
+      int v = 0;
+      if (sense_plan_autotune(r->plan, r->s_d, r->lines_d, &v, nullptr, q->stream) == SENSE_OK) variant = v;
+    }
+    std::lock_guard<std::mutex> lock(q->mu);
+    q->variants[key] = variant;
+  }
+  if (sense_plan_set_variant(r->plan, variant) != SENSE_OK) {
+    *err = sense_last_error();
+    return false;
+  }
+  if (plan_cg_start(r->plan, r->y_d, r->s_d, r->lines_d, r->x_d, r->tol, q->stream) != SENSE_OK) {
+    *err = sense_last_error();
+    return false;
+  }
+  // the pinned inputs can go once the uploads have run
+  if (cudaStreamSynchronize(q->stream) != cudaSuccess) {
+    *err = "upload / CG start failed";
+    return false;
+  }
+  free_host(r);
+  return true;
+}
+
+// Copy the results of a finished request to pinned host memory.
+bool retire_device(sense_queue* q, Request* r) {
+  const size_t F = r->sh.frames;
+  bool ok = cudaMallocHost(&r->x_h, r->x_bytes) == cudaSuccess &&
+            cudaMallocHost(&r->iters_h, sizeof(int) * F) == cudaSuccess &&
+            cudaMallocHost(&r->outcome_h, sizeof(int) * F) == cudaSuccess &&
+            cudaMallocHost(&r->resid_h, sizeof(double) * F) == cudaSuccess;
+  ok = ok && plan_cg_finish(r->plan, r->out_i_d, r->resid_d, r->out_i_d + F, q->stream) == SENSE_OK;
+  ok = ok && cudaMemcpyAsync(r->x_h, r->x_d, r->x_bytes, cudaMemcpyDeviceToHost, q->stream) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(r->iters_h, r->out_i_d, sizeof(int) * F, cudaMemcpyDeviceToHost, q->stream) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(r->outcome_h, r->out_i_d + F, sizeof(int) * F, cudaMemcpyDeviceToHost, q->stream) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpyAsync(r->resid_h, r->resid_d, sizeof(double) * F, cudaMemcpyDeviceToHost, q->stream) ==
+                 cudaSuccess;
+  ok = ok && cudaStreamSynchronize(q->stream) == cudaSuccess;
+  if (ok && sense_plan_check(r->plan, q->stream) != SENSE_OK) ok = false;
+  free_device(r);
+  return ok;
+}
+
+// One CG iteration of every live frame: one persistent launch per size class.
+bool tick_device(sense_queue* q) {
+  std::map<std::tuple<int, int, int>, std::vector<Request*>> by_class;
+  for (Request* r : q->live) by_class[std::make_tuple(r->sh.ny, r->sh.nx, r->sh.storage)].push_back(r);
+  std::vector<std::pair<SizeClass*, int>> launched;
+  for (auto& kv : by_class) {
+    SizeClass& c = q->classes[kv.first];
+    c.ny = std::get<0>(kv.first);
+    c.nx = std::get<1>(kv.first);
+    c.storage = std::get<2>(kv.first);
+    int frames = 0;
+    for (Request* r : kv.second) frames += r->sh.frames;
+    if (!ensure_class_capacity(q, c, frames)) return false;
+    int off = 0;
+    for (Request* r : kv.second) {
+      r->status_off = off;
+      plan_frames(r->plan, r->s_d, r->lines_d, r->x_d, r->ticks, r->tol, c.table_h + off);
+      off += r->sh.frames;
+    }
+    const int variant = sense_plan_variant(kv.second[0]->plan);
+    const int W = normal_variant_width(c.ny, variant);
+    const int th = normal_variant_threads(c.ny, variant);
+    PArgs a{};
+    a.frames = c.table_d;
+    a.nframes = frames;
+    a.nx = c.nx;
+    a.tiles = (c.nx + W - 1) / W;
+    a.chunks = (int)(((size_t)c.ny * c.nx / 2 + (size_t)th * 4 - 1) / ((size_t)th * 4));
+    a.iters = 1;
+    a.ticket = reinterpret_cast<unsigned*>(c.ints + 4 * frames);
+    a.tw = kv.second[0]->plan->tw_y;
+    a.err = kv.second[0]->plan->err();
+    a.st.nrm_arrive = reinterpret_cast<unsigned*>(c.ints);
+    a.st.upd_arrive = reinterpret_cast<unsigned*>(c.ints + frames);
+    a.st.nrm_ready = c.ints + 2 * frames;
+    a.st.upd_ready = c.ints + 3 * frames;
+    a.st.part_nrm = c.part_nrm;
+    a.st.part_upd = c.part_upd;
+    if (a.chunks > c.upd_cap) return false;
+    bool ok = cudaMemcpyAsync(c.table_d, c.table_h, sizeof(PFrame) * frames, cudaMemcpyHostToDevice, q->stream) ==
+                  cudaSuccess &&
+              cudaMemsetAsync(c.ints, 0, sizeof(int) * (4 * (size_t)frames + 1), q->stream) == cudaSuccess;
+    cudaError_t e = c.storage == SENSE_STORE_BF16 ? launch_cg_persistent<StBF16>(c.ny, variant, a, q->sms, q->stream)
+                                                  : launch_cg_persistent<StC64>(c.ny, variant, a, q->sms, q->stream);
+    if (!ok || e != cudaSuccess) return false;
+    k_gather_active<<<(frames + 255) / 256, 256, 0, q->stream>>>(c.table_d, frames, c.status_d);
+    if (cudaMemcpyAsync(c.status_h, c.status_d, sizeof(int) * frames, cudaMemcpyDeviceToHost, q->stream) !=
+        cudaSuccess)
+      return false;
+    for (Request* r : kv.second) r->cls = (int)launched.size();
+    launched.emplace_back(&c, frames);
+  }
+  if (cudaStreamSynchronize(q->stream) != cudaSuccess) return false;
+  // retire what finished
+  std::vector<Request*> still;
+  for (Request* r : q->live) {
+    r->ticks++;
+    const SizeClass* c = launched[r->cls].first;
+    bool any = false;
+    for (int f = 0; f < r->sh.frames; ++f) any |= c->status_h[r->status_off + f] != 0;
+    bool cancel;
+    {
+      std::lock_guard<std::mutex> lock(q->mu);
+      cancel = r->cancel;
+    }
+    if (cancel) {
+      free_device(r);
+      record_done(q, r, SENSE_REQ_CANCELLED);
+    } else if (!any || r->ticks >= r->max_iter) {
+      const bool ok = retire_device(q, r);
+      record_done(q, r, ok ? SENSE_REQ_DONE : SENSE_REQ_FAILED);
+    } else {
+      still.push_back(r);
+    }
+  }
+  q->live.swap(still);
+  return true;
+}
+
+void tick_fake(sense_queue* q) {
+  if (q->cfg.fake_tick_us > 0) std::this_thread::sleep_for(std::chrono::microseconds(q->cfg.fake_tick_us));
+  std::vector<Request*> still;
+  for (Request* r : q->live) {
+    r->ticks++;
+    bool cancel;
+    {
+      std::lock_guard<std::mutex> lock(q->mu);
+      cancel = r->cancel;
+    }
+    const int stop_at = std::min(r->max_iter, q->cfg.fake_iters > 0 ? q->cfg.fake_iters : r->max_iter);
+    if (cancel) {
+      record_done(q, r, SENSE_REQ_CANCELLED);
+    } else if (r->ticks >= stop_at) {
+      const size_t F = r->sh.frames;
+      r->x_h = static_cast<float2*>(calloc(r->x_bytes / sizeof(float2), sizeof(float2)));
+      r->iters_h = static_cast<int*>(calloc(F, sizeof(int)));
+      r->outcome_h = static_cast<int*>(calloc(F, sizeof(int)));
+      r->resid_h = static_cast<double*>(calloc(F, sizeof(double)));
+      for (size_t f = 0; f < F; ++f) {
+        r->iters_h[f] = r->ticks;
+        r->outcome_h[f] = r->ticks >= r->max_iter ? SENSE_CG_MAXITER : SENSE_CG_CONVERGED;
+      }
+      free(r->y_h);
+      free(r->s_h);
+      free(r->lines_h);
+      r->y_h = r->s_h = nullptr;
+      r->lines_h = nullptr;
+      record_done(q, r, SENSE_REQ_DONE);
+    } else {
+      still.push_back(r);
+    }
+  }
+  q->live.swap(still);
+}
+
+void worker_main(sense_queue* q) {
+  if (!q->cfg.fake_device) cudaSetDevice(q->device);
+  for (;;) {
+    std::vector<Request*> admit;
+    {
+      std::unique_lock<std::mutex> lock(q->mu);
+      q->cv_work.wait(lock, [&] { return q->stop || !q->pending.empty() || !q->live.empty(); });
+      if (q->stop) break;
+      while (!q->pending.empty()) {
+        Request* r = q->pending.front();
+        if (r->cancel) {
+          q->pending.pop_front();
+          r->state = SENSE_REQ_CANCELLED;
+          r->t_done = Clock::now();
+          q->st.cancelled++;
+          q->cv_done.notify_all();
+          continue;
+        }
+        const size_t n_live = q->live.size() + admit.size();
+        if (q->cfg.max_live > 0 && (int)n_live >= q->cfg.max_live) break;
+        if (q->in_use + r->need > q->budget) break;  // arrival order: the head waits for room
+        q->pending.pop_front();
+        q->in_use += r->need;
+        r->state = SENSE_REQ_RUNNING;
+        q->st.admitted++;
+        admit.push_back(r);
+      }
+    }
+    for (Request* r : admit) {
+      std::string err;
+      if (q->cfg.fake_device || admit_device(q, r, &err)) {
+        q->live.push_back(r);
+      } else {
+        free_device(r);
+        record_done(q, r, SENSE_REQ_FAILED);
+      }
+    }
+    if (q->live.empty()) continue;
+    if (q->cfg.fake_device) {
+      tick_fake(q);
+    } else if (!tick_device(q)) {
+      for (Request* r : q->live) {
+        free_device(r);
+        record_done(q, r, SENSE_REQ_FAILED);
+      }
+      q->live.clear();
+    }
+    std::lock_guard<std::mutex> lock(q->mu);
+    q->st.ticks++;
+  }
+  // shutdown: cancel what is left
+  for (Request* r : q->live) {
+    if (!q->cfg.fake_device) free_device(r);
+    record_done(q, r, SENSE_REQ_CANCELLED);
+  }
+  q->live.clear();
+}
+
+double percentile(std::vector<double> v, double p) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const double pos = p * (v.size() - 1);
+  const size_t lo = (size_t)pos;
+  const size_t hi = std::min(lo + 1, v.size() - 1);
+  return v[lo] + (pos - lo) * (v[hi] - v[lo]);
+}
+
+sense_status qfail(sense_status s, const std::string& m) {
+  record_error(m);
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_queue** out) {
+  if (!out) return qfail(SENSE_EINVAL, "out is NULL");
+  *out = nullptr;
+  sense_queue* q = new sense_queue();
+  if (cfg) q->cfg = *cfg;
+  q->device = device;
+  if (!q->cfg.fake_device) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+      delete q;
+      return qfail(SENSE_EINVAL, "device index out of range (or no CUDA device)");
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    cudaDeviceGetAttribute(&q->sms, cudaDevAttrMultiProcessorCount, device);
+    const cudaError_t e = cudaStreamCreateWithFlags(&q->stream, cudaStreamNonBlocking);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+      delete q;
+      return qfail(SENSE_ECUDA, "queue stream creation failed");
+    }
+    const size_t reserve = (size_t)1 << 30;
+    q->budget = q->cfg.hbm_budget_bytes ? q->cfg.hbm_budget_bytes : (free_b > reserve ? free_b - reserve : 0);
+  } else {
+    q->budget = q->cfg.hbm_budget_bytes ? q->cfg.hbm_budget_bytes : ((size_t)1 << 40);
+  }
+  q->st.hbm_budget = q->budget;
+  q->worker = std::thread(worker_main, q);
+  *out = q;
+  return SENSE_OK;
+}
+
+sense_status sense_queue_submit(sense_queue* q, const sense_shape* shape, const void* y_host, const void* S_host,
+                                const int32_t* lines_host, int max_iter, double rel_tol, uint64_t* req_id) {
+  if (!q || !shape || !y_host || !S_host || !lines_host || !req_id)
+    return qfail(SENSE_EINVAL, "queue, shape, inputs and req_id are required");
+  const sense_shape& sh = *shape;
+  if (sh.frames < 1 || sh.coils < 1 || sh.lines < 1 || sh.lines > sh.ny || max_iter < 1 || !(rel_tol >= 0.0))
+    return qfail(SENSE_EINVAL, "bad shape, max_iter or rel_tol");
+  if (sh.storage != SENSE_STORE_C64 && sh.storage != SENSE_STORE_BF16) return qfail(SENSE_EINVAL, "bad storage");
+  if (!sense_size_supported(sh.ny) || !sense_size_supported(sh.nx))
+    return qfail(SENSE_EUNSUPPORTED_SIZE, "no compiled transform for this ny / nx");
+  Request* r = new Request();
+  r->sh = sh;
+  r->max_iter = max_iter;
+  r->tol = rel_tol;
+  r->need = request_need(sh);
+  const size_t F = sh.frames, img = (size_t)sh.ny * sh.nx, e = elem_bytes(sh.storage);
+  r->y_bytes = F * sh.coils * sh.lines * sh.nx * e;
+  r->s_bytes = (size_t)sh.coils * img * e;
+  r->l_bytes = F * sh.lines * sizeof(int);
+  r->x_bytes = F * img * sizeof(float2);
+  {
+    std::lock_guard<std::mutex> lock(q->mu);
+    q->st.submitted++;
+    if (r->need > q->budget) {
+      q->st.refused++;
+      delete r;
+      return qfail(SENSE_EQUEUE_FULL, "request needs more device memory than the queue's budget");
+    }
+  }
+  bool ok;
+  if (q->cfg.fake_device) {
+    r->y_h = malloc(r->y_bytes);
+    r->s_h = malloc(r->s_bytes);
+    r->lines_h = static_cast<int*>(malloc(r->l_bytes));
+    ok = r->y_h && r->s_h && r->lines_h;
+  } else {
+    ok = cudaMallocHost(&r->y_h, r->y_bytes) == cudaSuccess && cudaMallocHost(&r->s_h, r->s_bytes) == cudaSuccess &&
+         cudaMallocHost(&r->lines_h, r->l_bytes) == cudaSuccess;
+  }
+  if (!ok) {
+    if (q->cfg.fake_device) {
+      free(r->y_h);
+      free(r->s_h);
+      free(r->lines_h);
+    } else {
+      free_host(r);
+    }
+    delete r;
+    return qfail(SENSE_ENOMEM, "pinned staging allocation failed");
+  }
+  memcpy(r->y_h, y_host, r->y_bytes);
+  memcpy(r->s_h, S_host, r->s_bytes);
+  memcpy(r->lines_h, lines_host, r->l_bytes);
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lock(q->mu);
+    r->id = q->next_id++;
+    q->reqs[r->id] = r;
+    q->pending.push_back(r);
+    *req_id = r->id;
+  }
+  q->cv_work.notify_all();
+  return SENSE_OK;
+}
+
+sense_status sense_queue_poll(sense_queue* q, uint64_t id, int* state, int* iters) {
+  if (!q) return qfail(SENSE_EINVAL, "queue is NULL");
+  std::lock_guard<std::mutex> lock(q->mu);
+  auto it = q->reqs.find(id);
+  if (it == q->reqs.end()) return qfail(SENSE_ENOTFOUND, "unknown request id");
+  if (state) *state = it->second->state;
+  if (iters) *iters = it->second->ticks;
+  return SENSE_OK;
+}
+
+sense_status sense_queue_wait(sense_queue* q, uint64_t id, sense_c32* x_host, int32_t* iters_host, double* resid_host,
+                              int32_t* outcome_host, double timeout_s) {
+  if (!q) return qfail(SENSE_EINVAL, "queue is NULL");
+  Request* r = nullptr;
+  {
+    std::unique_lock<std::mutex> lock(q->mu);
+    auto it = q->reqs.find(id);
+    if (it == q->reqs.end()) return qfail(SENSE_ENOTFOUND, "unknown request id");
+    r = it->second;
+    auto finished = [&] { return r->state >= SENSE_REQ_DONE; };
+    if (timeout_s > 0) {
+      if (!q->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s), finished))
+        return qfail(SENSE_ETIMEOUT, "request not finished within the timeout");
+    } else {
+      q->cv_done.wait(lock, finished);
+    }
+    q->reqs.erase(it);
+  }
+  sense_status rc = SENSE_OK;
+  if (r->state == SENSE_REQ_DONE) {
+    const size_t F = r->sh.frames;
+    if (x_host) memcpy(x_host, r->x_h, r->x_bytes);
+    if (iters_host) memcpy(iters_host, r->iters_h, sizeof(int) * F);
+    if (resid_host) memcpy(resid_host, r->resid_h, sizeof(double) * F);
+    if (outcome_host) memcpy(outcome_host, r->outcome_h, sizeof(int) * F);
+  } else if (r->state == SENSE_REQ_CANCELLED) {
+    rc = qfail(SENSE_EINVAL, "request was cancelled");
+  } else {
+    rc = qfail(SENSE_ECUDA, "request failed on the device");
+  }
+  if (q->cfg.fake_device) {
+    free(r->x_h);
+    free(r->iters_h);
+    free(r->resid_h);
+    free(r->outcome_h);
+    free(r->y_h);
+    free(r->s_h);
+    free(r->lines_h);
+  } else {
+    free_outputs(r);
+    free_host(r);
+  }
+  delete r;
+  return rc;
+}
+
+sense_status sense_queue_cancel(sense_queue* q, uint64_t id) {
+  if (!q) return qfail(SENSE_EINVAL, "queue is NULL");
+  {
+    std::lock_guard<std::mutex> lock(q->mu);
+    auto it = q->reqs.find(id);
+    if (it == q->reqs.end()) return qfail(SENSE_ENOTFOUND, "unknown request id");
+    it->second->cancel = true;
+  }
+  q->cv_work.notify_all();
+  return SENSE_OK;
+}
+
+sense_status sense_queue_stats_get(sense_queue* q, sense_queue_stats* out) {
+  if (!q || !out) return qfail(SENSE_EINVAL, "queue and out are required");
+  std::lock_guard<std::mutex> lock(q->mu);
+  *out = q->st;
+  out->p50_ms = percentile(q->lat_ms, 0.50);
+  out->p99_ms = percentile(q->lat_ms, 0.99);
+  double sum = 0.0, mx = 0.0;
+  for (double v : q->lat_ms) {
+    sum += v;
+    mx = std::max(mx, v);
+  }
+  out->mean_ms = q->lat_ms.empty() ? 0.0 : sum / q->lat_ms.size();
+  out->max_ms = mx;
+  out->hbm_in_use = q->in_use;
+  out->hbm_budget = q->budget;
+  int running = 0;
+  for (auto& kv : q->reqs)
+    if (kv.second->state == SENSE_REQ_RUNNING) ++running;
+  out->live = running;
+  out->pending = (int)q->pending.size();
+  return SENSE_OK;
+}
+
+int sense_queue_variant(sense_queue* q, int ny, int nx, int storage) {
+  if (!q) return -1;
+  std::lock_guard<std::mutex> lock(q->mu);
+  auto it = q->variants.find(std::make_tuple(ny, nx, storage));
+  return it == q->variants.end() ? -1 : it->second;
+}
+
+sense_status sense_queue_destroy(sense_queue* q) {
+  if (!q) return SENSE_OK;
+  {
+    std::lock_guard<std::mutex> lock(q->mu);
+    q->stop = true;
+    for (Request* r : q->pending) {
+      r->state = SENSE_REQ_CANCELLED;
+      q->st.cancelled++;
+    }
+  }
+  q->cv_work.notify_all();
+  if (q->worker.joinable()) q->worker.join();
+  for (auto& kv : q->reqs) {
+    Request* r = kv.second;
+    if (q->cfg.fake_device) {
+      free(r->x_h);
+      free(r->iters_h);
+      free(r->resid_h);
+      free(r->outcome_h);
+      free(r->y_h);
+      free(r->s_h);
+      free(r->lines_h);
+    } else {
+      free_device(r);
+      free_outputs(r);
+      free_host(r);
+    }
+    delete r;
+  }
+  if (!q->cfg.fake_device) {
+    for (auto& kv : q->classes) {
+      SizeClass& c = kv.second;
+      for (void* p : {(void*)c.ints, (void*)c.part_nrm, (void*)c.part_upd, (void*)c.table_d, (void*)c.status_d})
+        if (p) cudaFree(p);
+      if (c.table_h) cudaFreeHost(c.table_h);
+      if (c.status_h) cudaFreeHost(c.status_h);
+    }
+    if (q->stream) cudaStreamDestroy(q->stream);
+  }
+  delete q;
+  return SENSE_OK;
+}
+
+}  // extern "C"

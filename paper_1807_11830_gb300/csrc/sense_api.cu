@@ -323,7 +323,7 @@ sense_status run_cg_chunk(sense_plan* pl, const void* S, const int* lines, float
 template <class St>
 sense_status cg_chunk_graph(sense_plan* pl, const void* S, const int* lines, float2* x, int first, int count,
                             double tol, cudaStream_t st) {
-  if (pl->timing) return run_cg_chunk<St>(pl, S, lines, x, first, count, tol, st);
+  if (pl->timing || pl->cg_mode == 2) return run_cg_chunk<St>(pl, S, lines, x, first, count, tol, st);
   const int first_key = first == 0 ? 0 : 1 + (first & 1);  // p_update and ping-pong parity
   auto key = std::make_tuple(S, (const void*)lines, (const void*)x, first_key, count, tol);
   auto it = pl->graphs.find(key);
@@ -407,13 +407,15 @@ sense_status run_cg_persistent(sense_plan* pl, const void* S, const int* lines, 
                                cudaStream_t st) {
   const sense_shape& sh = pl->sh;
   const int F = sh.frames;
-  if (pl->ptable_key[0] != S || pl->ptable_key[1] != (const void*)lines || pl->ptable_key[2] != (const void*)x) {
+  if (pl->ptable_key[0] != S || pl->ptable_key[1] != (const void*)lines || pl->ptable_key[2] != (const void*)x ||
+      pl->ptable_tol != tol) {
     SENSE_CUDA_TRY(cudaStreamSynchronize(st));  // the staging copy may still be read by an earlier call
-    plan_frames(pl, S, lines, x, 0, pl->ptable_host);
+    plan_frames(pl, S, lines, x, 0, tol, pl->ptable_host);
     SENSE_CUDA_TRY(cudaMemcpyAsync(pl->ptable, pl->ptable_host, sizeof(PFrame) * F, cudaMemcpyHostToDevice, st));
     pl->ptable_key[0] = S;
     pl->ptable_key[1] = lines;
     pl->ptable_key[2] = x;
+    pl->ptable_tol = tol;
   }
   SENSE_CUDA_TRY(cudaMemsetAsync(pl->pints, 0, sizeof(int) * (4 * (size_t)F + 1), st));
   const int threads = normal_variant_threads(sh.ny, pl->norm_variant);
@@ -433,7 +435,6 @@ sense_status run_cg_persistent(sense_plan* pl, const void* S, const int* lines, 
   a.st.upd_ready = pl->pints + 3 * F;
   a.st.part_nrm = pl->part_nrm;
   a.st.part_upd = pl->part_upd;
-  a.st.tol = tol;
   if (a.chunks > pl->max_chunks) return fail(SENSE_EINVAL, "internal: update chunks exceed the workspace");
   PhaseScope ps(pl, SENSE_PHASE_CG_PERSISTENT, st);
   return launch_status(launch_cg_persistent<St>(sh.ny, pl->norm_variant, a, pl->sms, st), "persistent CG");
@@ -482,7 +483,8 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
 
 namespace sense {
 
-void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* x, int k0, PFrame* out) {
+void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* x, int k0, double tol,
+                 PFrame* out) {
   const sense_shape& sh = pl->sh;
   const CgState g = pl->cg(0.0);
   for (int f = 0; f < sh.frames; ++f) {
@@ -505,6 +507,7 @@ void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* 
     fr.coils = sh.coils;
     fr.L = sh.lines;
     fr.k0 = k0;
+    fr.tol = tol;
   }
 }
 
@@ -705,7 +708,7 @@ sense_status sense_plan_phase_time(sense_plan* pl, int phase, double* ms_total, 
 
 sense_status sense_plan_set_cg_mode(sense_plan* pl, int mode) {
   if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
-  if (mode != 0 && mode != 1) return fail(SENSE_EINVAL, "CG mode must be 0 (graph) or 1 (persistent)");
+  if (mode < 0 || mode > 2) return fail(SENSE_EINVAL, "CG mode must be 0 (graph), 1 (persistent) or 2 (direct)");
   pl->cg_mode = mode;
   return SENSE_OK;
 }

@@ -37,11 +37,14 @@ EXPORTED = (
     "sense_plan_set_cg_mode", "sense_selftest_wait",
     "sense_batch_create", "sense_batch_destroy", "sense_batch_workspace_bytes", "sense_batch_classes",
     "sense_batch_autotune", "sense_batch_set_variant", "sense_batch_cg_solve", "sense_batch_check",
+    "sense_queue_create", "sense_queue_submit", "sense_queue_poll", "sense_queue_wait", "sense_queue_cancel",
+    "sense_queue_stats_get", "sense_queue_variant", "sense_queue_destroy",
 )
+REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = 0, 1, 2, 3, 4
 NORM_VARIANTS = 4
 
 PHASES = ("rows_fwd", "rows_inv", "fwd_col", "adj_col", "normal", "cg_normal", "cg_update", "cg_persistent")
-CG_MODE_GRAPH, CG_MODE_PERSISTENT = 0, 1
+CG_MODE_GRAPH, CG_MODE_PERSISTENT, CG_MODE_DIRECT = 0, 1, 2
 
 
 class SenseError(RuntimeError):
@@ -59,6 +62,19 @@ class _BatchIO(ctypes.Structure):
     _fields_ = [("y", ctypes.c_void_p), ("S", ctypes.c_void_p), ("lines", ctypes.c_void_p),
                 ("x_out", ctypes.c_void_p), ("iters_out", ctypes.c_void_p), ("rel_resid_out", ctypes.c_void_p),
                 ("outcome_out", ctypes.c_void_p)]
+
+
+class _QueueCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_live", ctypes.c_int), ("fake_device", ctypes.c_int),
+                ("fake_tick_us", ctypes.c_int), ("fake_iters", ctypes.c_int), ("autotune", ctypes.c_int)]
+
+
+class _QueueStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("refused", ctypes.c_uint64),
+                ("ticks", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("hbm_in_use", ctypes.c_size_t),
+                ("hbm_budget", ctypes.c_size_t), ("live", ctypes.c_int), ("pending", ctypes.c_int)]
 
 
 _LIB = None
@@ -125,6 +141,23 @@ def load_library(path=LIB_PATH):
     lib.sense_batch_cg_solve.restype = st
     lib.sense_batch_check.argtypes = [vp, vp]
     lib.sense_batch_check.restype = st
+    lib.sense_queue_create.argtypes = [i, ctypes.POINTER(_QueueCfg), ctypes.POINTER(vp)]
+    lib.sense_queue_create.restype = st
+    lib.sense_queue_submit.argtypes = [vp, ctypes.POINTER(_Shape), vp, vp, vp, i, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_uint64)]
+    lib.sense_queue_submit.restype = st
+    lib.sense_queue_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.sense_queue_poll.restype = st
+    lib.sense_queue_wait.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp, ctypes.c_double]
+    lib.sense_queue_wait.restype = st
+    lib.sense_queue_cancel.argtypes = [vp, ctypes.c_uint64]
+    lib.sense_queue_cancel.restype = st
+    lib.sense_queue_stats_get.argtypes = [vp, ctypes.POINTER(_QueueStats)]
+    lib.sense_queue_stats_get.restype = st
+    lib.sense_queue_variant.argtypes = [vp, i, i, i]
+    lib.sense_queue_variant.restype = i
+    lib.sense_queue_destroy.argtypes = [vp]
+    lib.sense_queue_destroy.restype = st
     lib.sense_last_error.argtypes = []
     lib.sense_last_error.restype = ctypes.c_char_p
     _LIB = lib
@@ -356,3 +389,97 @@ def sense_batch_cg_solve(batch, items, max_iter, rel_tol=0.0, stream=None):
 
 def sense_batch_check(batch, stream=None):
     _check(load_library().sense_batch_check(batch.handle, _stream(stream)))
+
+
+def _np_ptr(a):
+    import numpy as np  # host buffers of the queue are numpy arrays
+    if a is None:
+        return None
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Queue:
+    """Owns a ``sense_queue*`` (scheduler thread + device-resident requests).
+    Host buffers are numpy arrays: y, S complex64 (or uint16 [...,2] bf16
+    bits), lines int32."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0, max_live=0, fake_device=False, fake_tick_us=0,
+                 fake_iters=0, autotune=False):
+        cfg = _QueueCfg(hbm_budget_bytes, max_live, 1 if fake_device else 0, fake_tick_us, fake_iters,
+                        1 if autotune else 0)
+        h = ctypes.c_void_p()
+        _check(load_library().sense_queue_create(device, ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, shape, y, S, lines, max_iter, rel_tol=0.0):
+        sh = _Shape(shape["ny"], shape["nx"], shape["coils"], shape["frames"], shape["lines"],
+                    shape.get("storage", STORE_C64))
+        rid = ctypes.c_uint64()
+        _check(load_library().sense_queue_submit(self.handle, ctypes.byref(sh), _np_ptr(y), _np_ptr(S),
+                                                 _np_ptr(lines), int(max_iter), float(rel_tol), ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, rid):
+        st_, it = ctypes.c_int(), ctypes.c_int()
+        _check(load_library().sense_queue_poll(self.handle, rid, ctypes.byref(st_), ctypes.byref(it)))
+        return st_.value, it.value
+
+    def wait(self, rid, x=None, iters=None, resid=None, outcome=None, timeout_s=0.0):
+        _check(load_library().sense_queue_wait(self.handle, rid, _np_ptr(x), _np_ptr(iters), _np_ptr(resid),
+                                               _np_ptr(outcome), float(timeout_s)))
+
+    def cancel(self, rid):
+        _check(load_library().sense_queue_cancel(self.handle, rid))
+
+    def stats(self):
+        s_ = _QueueStats()
+        _check(load_library().sense_queue_stats_get(self.handle, ctypes.byref(s_)))
+        return {k: getattr(s_, k) for k, _ in _QueueStats._fields_}
+
+    def variant(self, ny, nx, storage=STORE_C64):
+        return load_library().sense_queue_variant(self.handle, ny, nx, storage)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load_library().sense_queue_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sense_queue_create(device=0, **cfg):
+    return Queue(device, **cfg)
+
+
+def sense_queue_submit(q, shape, y, S, lines, max_iter, rel_tol=0.0):
+    return q.submit(shape, y, S, lines, max_iter, rel_tol)
+
+
+def sense_queue_poll(q, rid):
+    return q.poll(rid)
+
+
+def sense_queue_wait(q, rid, x=None, iters=None, resid=None, outcome=None, timeout_s=0.0):
+    return q.wait(rid, x, iters, resid, outcome, timeout_s)
+
+
+def sense_queue_cancel(q, rid):
+    return q.cancel(rid)
+
+
+def sense_queue_stats_get(q):
+    return q.stats()
+
+
+def sense_queue_variant(q, ny, nx, storage=STORE_C64):
+    return q.variant(ny, nx, storage)
+
+
+def sense_queue_destroy(q):
+    q.close()

@@ -1,0 +1,148 @@
+"""Scheduler logic of the serving queue, on the CPU (fake-device mode: no GPU
+work; every frame stops after min(max_iter, fake_iters) ticks).
+
+Covers arrival-order admission, the live-request limit, admission by the
+memory budget, refusal of requests that can never fit, cancellation of
+pending and running requests, waits with a timeout and unknown ids.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1807_11830_gb300 import build as sense_build
+from paper_1807_11830_gb300 import sense
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    sense_build.build()
+    sense.load_library()
+
+
+def _req(n=64, coils=4, frames=2, lines=16):
+    shape = dict(ny=n, nx=n, coils=coils, frames=frames, lines=lines)
+    y = np.zeros((frames, coils, lines, n), np.complex64)
+    S = np.zeros((coils, n, n), np.complex64)
+    ln = np.tile(np.arange(lines, dtype=np.int32), (frames, 1))
+    return shape, y, S, ln
+
+
+def test_all_requests_complete_in_order_with_one_live():
+    q = sense.Queue(fake_device=True, fake_tick_us=200, fake_iters=3, max_live=1)
+    ids = [q.submit(*_req(), max_iter=10) for _ in range(6)]
+    done_order = []
+    pending = set(ids)
+    while pending:
+        for rid in list(pending):
+            st, _ = q.poll(rid)
+            if st == sense.REQ_DONE:
+                done_order.append(rid)
+                pending.discard(rid)
+        time.sleep(0.001)
+    assert done_order == ids  # one live request at a time: strict arrival order
+    for rid in ids:
+        it = np.zeros(2, np.int32)
+        oc = np.zeros(2, np.int32)
+        q.wait(rid, iters=it, outcome=oc)
+        assert list(it) == [3, 3] and list(oc) == [sense.CG_CONVERGED] * 2
+    st = q.stats()
+    assert st["completed"] == 6 and st["admitted"] == 6 and st["ticks"] >= 18
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    q.close()
+
+
+def test_iteration_level_batching_runs_requests_together():
+    q = sense.Queue(fake_device=True, fake_tick_us=2000, fake_iters=20)
+    ids = [q.submit(*_req(), max_iter=20) for _ in range(5)]
+    peak = 0
+    for _ in range(50):
+        peak = max(peak, q.stats()["live"])
+        time.sleep(0.001)
+    assert peak >= 2  # several requests advance in the same ticks
+    for rid in ids:
+        q.wait(rid)
+    st = q.stats()
+    assert st["ticks"] < 5 * 20  # far fewer ticks than a serial loop would need
+    q.close()
+
+
+def test_budget_admission_and_refusal():
+    shape, y, S, ln = _req()
+    # find one request's need by a budget that refuses it
+    q = sense.Queue(fake_device=True, hbm_budget_bytes=1024)
+    with pytest.raises(sense.SenseError) as ei:
+        q.submit(shape, y, S, ln, max_iter=5)
+    assert ei.value.status == 7  # SENSE_EQUEUE_FULL
+    assert q.stats()["refused"] == 1
+    q.close()
+    # the exact need of one request, by bisection on the refusal boundary
+    lo, hi = 1024, 1 << 30  # refused at lo, accepted at hi
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        qq = sense.Queue(fake_device=True, hbm_budget_bytes=mid)
+        try:
+            qq.submit(shape, y, S, ln, max_iter=1)
+            hi = mid
+        except sense.SenseError:
+            lo = mid
+        qq.close()
+    need = hi
+    q = sense.Queue(fake_device=True, hbm_budget_bytes=2 * need + need // 2, fake_tick_us=500, fake_iters=10)
+    ids = [q.submit(shape, y, S, ln, max_iter=10) for _ in range(6)]
+    peak = 0
+    for _ in range(400):
+        st = q.stats()
+        peak = max(peak, st["live"])
+        assert st["hbm_in_use"] <= st["hbm_budget"]
+        if st["completed"] == 6:
+            break
+        time.sleep(0.001)
+    for rid in ids:
+        q.wait(rid)
+    assert peak == 2  # two fit the budget, the third waits for one to retire
+    q.close()
+
+
+def test_cancel_pending_and_running():
+    q = sense.Queue(fake_device=True, fake_tick_us=1000, fake_iters=50, max_live=1)
+    a = q.submit(*_req(), max_iter=50)
+    b = q.submit(*_req(), max_iter=50)
+    time.sleep(0.01)
+    assert q.poll(a)[0] == sense.REQ_RUNNING and q.poll(b)[0] == sense.REQ_PENDING
+    q.cancel(b)
+    q.cancel(a)
+    with pytest.raises(sense.SenseError):
+        q.wait(a)
+    with pytest.raises(sense.SenseError):
+        q.wait(b)
+    c = q.submit(*_req(), max_iter=2)
+    q.wait(c)
+    st = q.stats()
+    assert st["cancelled"] == 2 and st["completed"] == 1
+    q.close()
+
+
+def test_unknown_ids_and_wait_timeout():
+    q = sense.Queue(fake_device=True, fake_tick_us=2000, fake_iters=100)
+    with pytest.raises(sense.SenseError) as ei:
+        q.poll(12345)
+    assert ei.value.status == 8
+    rid = q.submit(*_req(), max_iter=100)
+    with pytest.raises(sense.SenseError) as ei:
+        q.wait(rid, timeout_s=0.01)
+    assert ei.value.status == 5
+    q.cancel(rid)
+    q.close()
+
+
+def test_bad_submissions():
+    q = sense.Queue(fake_device=True)
+    shape, y, S, ln = _req()
+    bad = dict(shape, ny=100, nx=100)
+    with pytest.raises(sense.SenseError) as ei:
+        q.submit(bad, y, S, ln, max_iter=3)
+    assert ei.value.status == 2
+    with pytest.raises(sense.SenseError):
+        q.submit(shape, y, S, ln, max_iter=0)
+    q.close()
