@@ -49,6 +49,12 @@ def parse_args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=20)
+    ap.add_argument("--workload", default="cine", choices=("cine", "mix", "serve"),
+                    help="cine: the headline line; mix: 512-instance uneven batch vs the plain loop; "
+                         "serve: Poisson request streams through the serving queue vs serial plain solves")
+    ap.add_argument("--mix-count", type=int, default=512)
+    ap.add_argument("--serve-rates", default="50,200,800")
+    ap.add_argument("--serve-requests", type=int, default=160)
     ap.add_argument("--cg-mode", default="auto", choices=("auto", "graph", "persistent"),
                     help="CG iteration scheme; 'auto' times both briefly and keeps the faster")
     ap.add_argument("--normal-variant", default="auto",
@@ -422,10 +428,206 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# uneven batching: 512 seeded instances, one persistent launch per size class
+# ---------------------------------------------------------------------------
+def mix_inputs(args, dev):
+    """Seeded mix: shapes from synth.draw_mix; maps from the coil model,
+    cached per (n, coils); lines per instance; k-space seeded complex
+    Gaussian on the device (the CG cost does not depend on the values)."""
+    import torch
+
+    from paper_1807_11830_gb300 import sense, synth
+
+    specs = synth.draw_mix(args.mix_count)
+    smaps = {}
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1810)
+    inst = []
+    for k, sp in enumerate(specs):
+        n, C, F, L = sp["n"], sp["coils"], sp["frames"], sp["lines"]
+        if (n, C) not in smaps:
+            smaps[(n, C)] = torch.from_numpy(synth.sensitivities(C, n, n).astype(np.complex64)).to(dev)
+        lines = synth.mask_lines(n, L, sp["centre"], F, synth.rng_for(20000 + k))
+        y = torch.randn((F, C, L, n), dtype=torch.complex64, device=dev, generator=gen) * 1e-2
+        inst.append(dict(spec=sp, S=smaps[(n, C)], lines=torch.from_numpy(lines).to(dev), y=y,
+                         x=torch.empty((F, n, n), dtype=torch.complex64, device=dev)))
+    return specs, inst
+
+
+def run_mix(args):
+    import torch
+
+    from paper_1807_11830_gb300 import sense
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sense.load_library()
+    ITER = 20
+    t0 = time.time()
+    specs, inst = mix_inputs(args, dev)
+    shapes = [dict(ny=sp["n"], nx=sp["n"], coils=sp["coils"], frames=sp["frames"], lines=sp["lines"])
+              for sp in specs]
+    batch = sense.Batch(shapes)
+    items = [dict(y=d["y"], S=d["S"], lines=d["lines"], x_out=d["x"]) for d in inst]
+    sense.sense_batch_autotune(batch, items)
+    setup_s = time.time() - t0
+    frames = sum(sp["frames"] for sp in specs)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 1)):
+        sense.sense_batch_cg_solve(batch, items, ITER)
+    torch.cuda.synchronize(dev)
+    ms = []
+    for k in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sense.sense_batch_cg_solve(batch, items, ITER)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    sense.sense_batch_check(batch)
+    batch_ms = statistics.median(ms)
+    ws = batch.workspace_bytes
+    batch.close()
+    # plain per-instance loop: the same kernels, per-iteration launches, no graphs, one instance at a time
+    plans = []
+    for d, sp in zip(inst, specs):
+        pl = sense.Plan(sp["n"], sp["n"], sp["coils"], sp["frames"], sp["lines"])
+        sense.sense_plan_set_cg_mode(pl, sense.CG_MODE_DIRECT)
+        plans.append(pl)
+    for pl, d in zip(plans, inst):  # warm-up (kernel attributes, caches)
+        sense.sense_cg_solve(pl, d["y"], d["S"], d["lines"], 1, 0.0, d["x"])
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for pl, d in zip(plans, inst):
+        sense.sense_cg_solve(pl, d["y"], d["S"], d["lines"], ITER, 0.0, d["x"])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = e0.elapsed_time(e1)
+    for pl in plans:
+        pl.close()
+    apps = frames * ITER
+    line = {
+        "metric": METRIC, "value": apps / (batch_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "uneven batch: %d instances (n in {128,192,256,384}, coils 8..32, frames 1..30, "
+                               "R in {2,3,4,6}), %d CG iterations" % (len(specs), ITER),
+                   "frames": frames, "size_classes": len(set(sp["n"] for sp in specs)),
+                   "l2": "working set far larger than L2"},
+        "plain_loop": {"value": apps / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,
+                       "kind": "same kernels, per-iteration launches, one instance at a time"},
+        "speedup_vs_plain": plain_ms / batch_ms,
+        "workspace_gb": ws / 1e9, "setup_s": setup_s,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# serving: Poisson request streams through the queue
+# ---------------------------------------------------------------------------
+def run_serve(args):
+    import torch
+
+    from paper_1807_11830_gb300 import sense, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sense.load_library()
+    MAXIT, TOL = 100, 1e-4
+    # a pool of request shapes drawn from the mix distribution; k-space = E x + noise made by the library's E
+    specs = synth.draw_mix(24, seed=1811)
+    pool = []
+    for k, sp in enumerate(specs):
+        p = synth.mix_instance(sp, 30000 + k)
+        F, n = p.x_true.shape[0], p.x_true.shape[1]
+        C, L = p.S.shape[0], p.lines.shape[1]
+        plan = sense.Plan(n, n, C, F, L)
+        S_d = torch.from_numpy(p.S.astype(np.complex64)).to(dev)
+        l_d = torch.from_numpy(p.lines).to(dev)
+        y_d = torch.empty((F, C, L, n), dtype=torch.complex64, device=dev)
+        sense.sense_forward(plan, torch.from_numpy(p.x_true.astype(np.complex64)).to(dev), S_d, l_d, y_d)
+        y_d += torch.from_numpy(p.noise.astype(np.complex64)).to(dev)
+        # serial plain solve time of this request: inputs in from pinned host memory, the same
+        # kernels with per-iteration launches, image back to pinned host memory
+        sense.sense_plan_set_cg_mode(plan, sense.CG_MODE_DIRECT)
+        x_d = torch.empty((F, n, n), dtype=torch.complex64, device=dev)
+        y_h, S_h, l_h = y_d.cpu().pin_memory(), S_d.cpu().pin_memory(), l_d.cpu().pin_memory()
+        x_h = torch.empty(x_d.shape, dtype=x_d.dtype).pin_memory()
+
+        def serial_solve():
+            y_d.copy_(y_h, non_blocking=True)
+            S_d.copy_(S_h, non_blocking=True)
+            l_d.copy_(l_h, non_blocking=True)
+            sense.sense_cg_solve(plan, y_d, S_d, l_d, MAXIT, TOL, x_d)
+            x_h.copy_(x_d, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        serial_solve()
+        t = time.perf_counter()
+        for _ in range(2):
+            serial_solve()
+        solve_s = (time.perf_counter() - t) / 2
+        pool.append(dict(shape=dict(ny=n, nx=n, coils=C, frames=F, lines=L), y=y_d.cpu().numpy(),
+                         S=p.S.astype(np.complex64), lines=p.lines, solve_s=solve_s, frames=F, n=n))
+        plan.close()
+    results = {}
+    for rate in [float(r) for r in args.serve_rates.split(",")]:
+        count = args.serve_requests
+        arrivals = synth.poisson_arrivals(rate, count, seed=int(rate) + 1811)
+        picks = synth.rng_for(int(rate) + 7).integers(0, len(pool), size=count)
+        q = sense.Queue(device=0)
+        t0 = time.perf_counter()
+        ids = []
+        for a, pk in zip(arrivals, picks):
+            now = time.perf_counter() - t0
+            if a > now:
+                time.sleep(a - now)
+            e = pool[pk]
+            ids.append(q.submit(e["shape"], e["y"], e["S"], e["lines"], MAXIT, TOL))
+        for rid in ids:
+            q.wait(rid)
+        wall = time.perf_counter() - t0
+        st = q.stats()
+        q.close()
+        # serial plain solves of the same stream: one at a time in arrival order
+        finish, lat = 0.0, []
+        for a, pk in zip(arrivals, picks):
+            start = max(a, finish)
+            finish = start + pool[pk]["solve_s"]
+            lat.append((finish - a) * 1e3)
+        frames = sum(pool[pk]["frames"] for pk in picks)
+        results[str(int(rate))] = {
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "solves_per_s": count / wall, "ticks": st["ticks"],
+            "serial_plain": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                             "solves_per_s": count / finish,
+                             "kind": "one request at a time in arrival order; per-request time measured on the "
+                                     "GPU with host copies, plain per-iteration launches"},
+            "requests": count, "frames": frames,
+        }
+    line = {
+        "metric": "served recon latency p50/p99 (ms) and solves/s", "value": results[max(results, key=float)]["solves_per_s"],
+        "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving: Poisson arrivals, sizes from the uneven-batch distribution, "
+                               "CG to a relative residual of 1e-4 or 100 iterations",
+                   "pool_shapes": len(pool)},
+        "rates": results,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "mix":
+        return run_mix(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -204,9 +204,9 @@ sense_status sense_batch_check(sense_batch* batch, void* stream);
  * A scheduler thread admits submitted reconstructions in arrival order while
  * the HBM budget and the live-request limit allow, keeps their k-space, maps
  * and CG state on the device, and advances every live request by one CG
- * iteration per tick: one persistent launch per size class runs one
- * iteration of every live frame of that class, whatever iteration each frame
- * is at.  A request retires when all its frames have stopped (the stopping
+ * iteration per tick (iters_per_tick of them): one persistent launch per size
+ * class runs the iterations of every live frame of that class, whatever
+ * iteration each frame is at.  A request retires when all its frames have stopped (the stopping
  * rules of sense_cg_solve) or after max_iter ticks; its image is copied to a
  * pinned host buffer and its device memory released.  Requests that arrive
  * while others run join at the next tick.  Each size class uses one kernel
@@ -223,6 +223,8 @@ typedef struct {
   int fake_tick_us;
   int fake_iters;
   int autotune;            /* 1: autotune each size class on its first request; 0: variant 0 */
+  int iters_per_tick;      /* CG iterations per tick (0 = 10); each frame still stops at its own
+                              max_iter / tolerance inside the tick, new requests join between ticks */
 } sense_queue_cfg;
 
 typedef enum {

@@ -40,6 +40,7 @@ struct PFrame {
   int *iters, *outcome, *active;
   int coils, L;
   int k0;              // CG iterations this frame has already done before the launch
+  int kmax;            // the frame does no work at global iterations >= kmax
   double tol;          // relative-residual stopping tolerance (0: none)
 };
 
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
       }
       if (!ok) atomicOr(a.err, ERR_TIMEOUT);
       s_ok = ok ? 1 : 0;
-      s_active = ok ? __ldcg(fr.active) : 0;
+      s_active = (ok && k + fr.k0 < fr.kmax) ? __ldcg(fr.active) : 0;
     }
     __syncthreads();
     const bool work = s_ok && s_active;

@@ -22,6 +22,8 @@ struct sense_plan {
   int norm_variant = 0;  // kernel variant of the normal operator (autotuned)
   int norm_tiles = 0;    // column tiles per frame of that variant
   int cg_mode = 1;       // 0: per-phase kernels replayed as CUDA graphs; 1: one persistent launch
+  cudaStream_t pool = nullptr;  // non-null: workspace is stream-ordered (cudaMallocAsync) on this stream
+  bool own_tw = true;           // false: twiddle tables are shared and owned elsewhere
   int sms = 0;           // multiprocessors of the plan's device
   PFrame* ptable = nullptr;       // device frame table of the persistent kernel
   PFrame* ptable_host = nullptr;  // pinned staging copy
@@ -92,6 +94,18 @@ sense_status plan_cg_start(sense_plan* pl, const void* y, const void* S, const i
 // Frame-table entries of a plan's frames for the persistent CG kernel.
 void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* x, int k0, double tol,
                  PFrame* out);
+
+// A plan whose workspace comes from the device's stream-ordered pool on `st`
+// and whose twiddle tables are the caller's (shared per size): no device-wide
+// synchronisation on creation or destruction.  For request-scoped plans.
+sense_status plan_create_pooled(const sense_shape* shape, int device, cudaStream_t st, const float2* tw_y,
+                                const float2* tw_x, sense_plan** out);
+void plan_destroy_pooled(sense_plan* pl);
+// Select the normal-operator variant without synchronising (the plan has no
+// captured graphs).
+sense_status plan_set_variant_nosync(sense_plan* pl, int variant);
+// exp(-2 pi i m / n), m < n, in FP64 rounded once to FP32 (host table).
+std::vector<float2> plan_twiddles(int n);
 
 // Per-frame outputs of a finished CG solve of a plan (iterations, residual,
 // outcome; NULL outputs are skipped).

@@ -66,7 +66,8 @@ struct Request {
   float2* x_d = nullptr;
   int* out_i_d = nullptr;  // iters [F], outcome [F]
   double* resid_d = nullptr;
-  int ticks = 0;
+  int* err_h = nullptr;     // device error flags of its plan, read at retirement
+  int ticks = 0;            // CG iterations applied (capped at max_iter)
   int state = SENSE_REQ_PENDING;
   bool cancel = false;
   int status_off = 0;  // position of its frames in the tick's status array
@@ -109,34 +110,77 @@ struct sense_queue {
   int sms = 0;
   std::map<std::tuple<int, int, int>, SizeClass> classes;  // worker thread only
   std::map<std::tuple<int, int, int>, int> variants;         // guarded by mu
+  std::map<int, float2*> twiddles;                            // device tables per length (worker thread)
+  // pinned host staging, recycled between requests (cudaMallocHost is slow)
+  std::mutex pin_mu;
+  std::map<size_t, std::vector<void*>> pin_free;
+  size_t pin_cached = 0;
 };
 
 namespace {
 
-void free_host(Request* r) {
-  if (r->y_h) cudaFreeHost(r->y_h);
-  if (r->s_h) cudaFreeHost(r->s_h);
-  if (r->lines_h) cudaFreeHost(r->lines_h);
+constexpr size_t kPinnedCacheBytes = (size_t)4 << 30;
+
+size_t pin_round(size_t b) { return (b + 4095) & ~(size_t)4095; }
+
+void* pin_get(sense_queue* q, size_t bytes) {
+  bytes = pin_round(bytes);
+  {
+    std::lock_guard<std::mutex> lock(q->pin_mu);
+    auto it = q->pin_free.find(bytes);
+    if (it != q->pin_free.end() && !it->second.empty()) {
+      void* p = it->second.back();
+      it->second.pop_back();
+      q->pin_cached -= bytes;
+      return p;
+    }
+  }
+  void* p = nullptr;
+  return cudaMallocHost(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+
+void pin_put(sense_queue* q, void* p, size_t bytes) {
+  if (!p) return;
+  bytes = pin_round(bytes);
+  {
+    std::lock_guard<std::mutex> lock(q->pin_mu);
+    if (q->pin_cached + bytes <= kPinnedCacheBytes) {
+      q->pin_free[bytes].push_back(p);
+      q->pin_cached += bytes;
+      return;
+    }
+  }
+  cudaFreeHost(p);
+}
+
+void free_host(sense_queue* q, Request* r) {
+  pin_put(q, r->y_h, r->y_bytes);
+  pin_put(q, r->s_h, r->s_bytes);
+  pin_put(q, r->lines_h, r->l_bytes);
   r->y_h = r->s_h = nullptr;
   r->lines_h = nullptr;
 }
 
-void free_outputs(Request* r) {
-  if (r->x_h) cudaFreeHost(r->x_h);
-  if (r->iters_h) cudaFreeHost(r->iters_h);
-  if (r->resid_h) cudaFreeHost(r->resid_h);
-  if (r->outcome_h) cudaFreeHost(r->outcome_h);
+void free_outputs(sense_queue* q, Request* r) {
+  const size_t F = r->sh.frames;
+  pin_put(q, r->x_h, r->x_bytes);
+  pin_put(q, r->iters_h, sizeof(int) * F);
+  pin_put(q, r->resid_h, sizeof(double) * F);
+  pin_put(q, r->outcome_h, sizeof(int) * F);
+  pin_put(q, r->err_h, sizeof(int));
+  r->err_h = nullptr;
   r->x_h = nullptr;
   r->iters_h = nullptr;
   r->resid_h = nullptr;
   r->outcome_h = nullptr;
 }
 
-void free_device(Request* r) {
-  if (r->plan) sense_plan_destroy(r->plan);
+// Stream-ordered release of a request's device memory (no device-wide sync).
+void free_device(Request* r, cudaStream_t st) {
+  if (r->plan) plan_destroy_pooled(r->plan);
   r->plan = nullptr;
   for (void* p : {r->y_d, r->s_d, (void*)r->lines_d, (void*)r->x_d, (void*)r->out_i_d, (void*)r->resid_d})
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, st);
   r->y_d = r->s_d = nullptr;
   r->lines_d = nullptr;
   r->x_d = nullptr;
@@ -197,27 +241,52 @@ bool ensure_class_capacity(sense_queue* q, SizeClass& c, int frames) {
   return ok;
 }
 
-// Upload inputs, create the plan, start CG.  Returns false on failure.
+const float2* twiddle_table(sense_queue* q, int n) {
+  auto it = q->twiddles.find(n);
+  if (it != q->twiddles.end()) return it->second;
+  const std::vector<float2> host = plan_twiddles(n);
+  float2* d = nullptr;
+  if (cudaMalloc(&d, sizeof(float2) * n) != cudaSuccess) return nullptr;
+  if (cudaMemcpy(d, host.data(), sizeof(float2) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  q->twiddles[n] = d;
+  return d;
+}
+
+// Upload inputs, create the plan (stream-ordered workspace, shared twiddle
+// tables), start CG.  Everything is queued on the queue's stream; nothing
+// synchronises.  Returns false on failure.
 bool admit_device(sense_queue* q, Request* r, std::string* err) {
   const sense_shape& sh = r->sh;
   const size_t F = sh.frames;
-  if (sense_plan_create(&sh, q->device, &r->plan) != SENSE_OK) {
+  cudaStream_t st = q->stream;
+  const float2* twy = twiddle_table(q, sh.ny);
+  const float2* twx = twiddle_table(q, sh.nx);
+  if (!twy || !twx) {
+    *err = "twiddle table set-up failed";
+    return false;
+  }
+  if (plan_create_pooled(&sh, q->device, st, twy, twx, &r->plan) != SENSE_OK) {
     *err = sense_last_error();
     return false;
   }
-  sense_plan_set_cg_mode(r->plan, 1);
-  bool ok = cudaMalloc(&r->y_d, r->y_bytes) == cudaSuccess && cudaMalloc(&r->s_d, r->s_bytes) == cudaSuccess &&
-            cudaMalloc(&r->lines_d, r->l_bytes) == cudaSuccess && cudaMalloc(&r->x_d, r->x_bytes) == cudaSuccess &&
-            cudaMalloc(&r->out_i_d, sizeof(int) * 2 * F) == cudaSuccess &&
-            cudaMalloc(&r->resid_d, sizeof(double) * F) == cudaSuccess;
+  r->plan->cg_mode = 1;
+  bool ok = cudaMallocAsync(&r->y_d, r->y_bytes, st) == cudaSuccess &&
+            cudaMallocAsync(&r->s_d, r->s_bytes, st) == cudaSuccess &&
+            cudaMallocAsync((void**)&r->lines_d, r->l_bytes, st) == cudaSuccess &&
+            cudaMallocAsync((void**)&r->x_d, r->x_bytes, st) == cudaSuccess &&
+            cudaMallocAsync((void**)&r->out_i_d, sizeof(int) * 2 * F, st) == cudaSuccess &&
+            cudaMallocAsync((void**)&r->resid_d, sizeof(double) * F, st) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     *err = "device allocation failed";
     return false;
   }
-  ok = cudaMemcpyAsync(r->y_d, r->y_h, r->y_bytes, cudaMemcpyHostToDevice, q->stream) == cudaSuccess &&
-       cudaMemcpyAsync(r->s_d, r->s_h, r->s_bytes, cudaMemcpyHostToDevice, q->stream) == cudaSuccess &&
-       cudaMemcpyAsync(r->lines_d, r->lines_h, r->l_bytes, cudaMemcpyHostToDevice, q->stream) == cudaSuccess;
+  ok = cudaMemcpyAsync(r->y_d, r->y_h, r->y_bytes, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+       cudaMemcpyAsync(r->s_d, r->s_h, r->s_bytes, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+       cudaMemcpyAsync(r->lines_d, r->lines_h, r->l_bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
   if (!ok) {
     *err = "input upload failed";
     return false;
@@ -234,50 +303,44 @@ bool admit_device(sense_queue* q, Request* r, std::string* err) {
     variant = 0;
     if (q->cfg.autotune) {
       int v = 0;
-      if (sense_plan_autotune(r->plan, r->s_d, r->lines_d, &v, nullptr, q->stream) == SENSE_OK) variant = v;
+      if (sense_plan_autotune(r->plan, r->s_d, r->lines_d, &v, nullptr, st) == SENSE_OK) variant = v;
     }
     std::lock_guard<std::mutex> lock(q->mu);
     q->variants[key] = variant;
   }
-  if (sense_plan_set_variant(r->plan, variant) != SENSE_OK) {
+  if (plan_set_variant_nosync(r->plan, variant) != SENSE_OK) {
     *err = sense_last_error();
     return false;
   }
-  if (plan_cg_start(r->plan, r->y_d, r->s_d, r->lines_d, r->x_d, r->tol, q->stream) != SENSE_OK) {
+  if (plan_cg_start(r->plan, r->y_d, r->s_d, r->lines_d, r->x_d, r->tol, st) != SENSE_OK) {
     *err = sense_last_error();
     return false;
   }
-  // the pinned inputs can go once the uploads have run
-  if (cudaStreamSynchronize(q->stream) != cudaSuccess) {
-    *err = "upload / CG start failed";
-    return false;
-  }
-  free_host(r);
   return true;
 }
 
-// Copy the results of a finished request to pinned host memory.
-bool retire_device(sense_queue* q, Request* r) {
+// Queue the result copies of a finished request (to its pinned buffers).
+bool retire_enqueue(sense_queue* q, Request* r) {
   const size_t F = r->sh.frames;
-  bool ok = cudaMallocHost(&r->x_h, r->x_bytes) == cudaSuccess &&
-            cudaMallocHost(&r->iters_h, sizeof(int) * F) == cudaSuccess &&
-            cudaMallocHost(&r->outcome_h, sizeof(int) * F) == cudaSuccess &&
-            cudaMallocHost(&r->resid_h, sizeof(double) * F) == cudaSuccess;
-  ok = ok && plan_cg_finish(r->plan, r->out_i_d, r->resid_d, r->out_i_d + F, q->stream) == SENSE_OK;
-  ok = ok && cudaMemcpyAsync(r->x_h, r->x_d, r->x_bytes, cudaMemcpyDeviceToHost, q->stream) == cudaSuccess;
-  ok = ok && cudaMemcpyAsync(r->iters_h, r->out_i_d, sizeof(int) * F, cudaMemcpyDeviceToHost, q->stream) == cudaSuccess;
-  ok = ok && cudaMemcpyAsync(r->outcome_h, r->out_i_d + F, sizeof(int) * F, cudaMemcpyDeviceToHost, q->stream) ==
+  cudaStream_t st = q->stream;
+  bool ok = plan_cg_finish(r->plan, r->out_i_d, r->resid_d, r->out_i_d + F, st) == SENSE_OK;
+  ok = ok && cudaMemcpyAsync(r->x_h, r->x_d, r->x_bytes, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(r->iters_h, r->out_i_d, sizeof(int) * F, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(r->outcome_h, r->out_i_d + F, sizeof(int) * F, cudaMemcpyDeviceToHost, st) ==
                  cudaSuccess;
-  ok = ok && cudaMemcpyAsync(r->resid_h, r->resid_d, sizeof(double) * F, cudaMemcpyDeviceToHost, q->stream) ==
-                 cudaSuccess;
-  ok = ok && cudaStreamSynchronize(q->stream) == cudaSuccess;
-  if (ok && sense_plan_check(r->plan, q->stream) != SENSE_OK) ok = false;
-  free_device(r);
+  ok = ok && cudaMemcpyAsync(r->resid_h, r->resid_d, sizeof(double) * F, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(r->err_h, r->plan->err(), sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess;
   return ok;
 }
 
-// One CG iteration of every live frame: one persistent launch per size class.
+// One tick: iters_per_tick CG iterations of every live frame, one persistent
+// launch per size class; frames stop at their own max_iter / tolerance inside
+// the launch.  Then one stream synchronisation reads back which frames still
+// iterate; finished requests queue their result copies, a second
+// synchronisation completes those, and their memory is released in stream
+// order.
 bool tick_device(sense_queue* q) {
+  const int m = q->cfg.iters_per_tick > 0 ? q->cfg.iters_per_tick : 10;
   std::map<std::tuple<int, int, int>, std::vector<Request*>> by_class;
   for (Request* r : q->live) by_class[std::make_tuple(r->sh.ny, r->sh.nx, r->sh.storage)].push_back(r);
   std::vector<std::pair<SizeClass*, int>> launched;
@@ -293,6 +356,7 @@ bool tick_device(sense_queue* q) {
     for (Request* r : kv.second) {
       r->status_off = off;
       plan_frames(r->plan, r->s_d, r->lines_d, r->x_d, r->ticks, r->tol, c.table_h + off);
+      for (int f = 0; f < r->sh.frames; ++f) c.table_h[off + f].kmax = r->max_iter;
       off += r->sh.frames;
     }
     const int variant = sense_plan_variant(kv.second[0]->plan);
@@ -304,7 +368,7 @@ bool tick_device(sense_queue* q) {
     a.nx = c.nx;
     a.tiles = (c.nx + W - 1) / W;
     a.chunks = (int)(((size_t)c.ny * c.nx / 2 + (size_t)th * 4 - 1) / ((size_t)th * 4));
-    a.iters = 1;
+    a.iters = m;
     a.ticket = reinterpret_cast<unsigned*>(c.ints + 4 * frames);
     a.tw = kv.second[0]->plan->tw_y;
     a.err = kv.second[0]->plan->err();
@@ -329,10 +393,9 @@ bool tick_device(sense_queue* q) {
     launched.emplace_back(&c, frames);
   }
   if (cudaStreamSynchronize(q->stream) != cudaSuccess) return false;
-  // retire what finished
-  std::vector<Request*> still;
+  std::vector<Request*> still, finished, cancelled;
   for (Request* r : q->live) {
-    r->ticks++;
+    r->ticks = std::min(r->ticks + m, r->max_iter);
     const SizeClass* c = launched[r->cls].first;
     bool any = false;
     for (int f = 0; f < r->sh.frames; ++f) any |= c->status_h[r->status_off + f] != 0;
@@ -341,15 +404,25 @@ bool tick_device(sense_queue* q) {
       std::lock_guard<std::mutex> lock(q->mu);
       cancel = r->cancel;
     }
-    if (cancel) {
-      free_device(r);
-      record_done(q, r, SENSE_REQ_CANCELLED);
-    } else if (!any || r->ticks >= r->max_iter) {
-      const bool ok = retire_device(q, r);
-      record_done(q, r, ok ? SENSE_REQ_DONE : SENSE_REQ_FAILED);
-    } else {
+    if (cancel)
+      cancelled.push_back(r);
+    else if (!any || r->ticks >= r->max_iter)
+      finished.push_back(r);
+    else
       still.push_back(r);
-    }
+  }
+  std::vector<bool> ok(finished.size());
+  for (size_t i = 0; i < finished.size(); ++i) ok[i] = retire_enqueue(q, finished[i]);
+  if (!finished.empty() && cudaStreamSynchronize(q->stream) != cudaSuccess)
+    for (size_t i = 0; i < finished.size(); ++i) ok[i] = false;
+  for (size_t i = 0; i < finished.size(); ++i) {
+    Request* r = finished[i];
+    free_device(r, q->stream);
+    record_done(q, r, (ok[i] && *r->err_h == 0) ? SENSE_REQ_DONE : SENSE_REQ_FAILED);
+  }
+  for (Request* r : cancelled) {
+    free_device(r, q->stream);
+    record_done(q, r, SENSE_REQ_CANCELLED);
   }
   q->live.swap(still);
   return true;
@@ -424,7 +497,7 @@ void worker_main(sense_queue* q) {
       if (q->cfg.fake_device || admit_device(q, r, &err)) {
         q->live.push_back(r);
       } else {
-        free_device(r);
+        free_device(r, q->stream);
         record_done(q, r, SENSE_REQ_FAILED);
       }
     }
@@ -433,7 +506,7 @@ void worker_main(sense_queue* q) {
       tick_fake(q);
     } else if (!tick_device(q)) {
       for (Request* r : q->live) {
-        free_device(r);
+        free_device(r, q->stream);
         record_done(q, r, SENSE_REQ_FAILED);
       }
       q->live.clear();
@@ -443,7 +516,7 @@ void worker_main(sense_queue* q) {
   }
   // shutdown: cancel what is left
   for (Request* r : q->live) {
-    if (!q->cfg.fake_device) free_device(r);
+    if (!q->cfg.fake_device) free_device(r, q->stream);
     record_done(q, r, SENSE_REQ_CANCELLED);
   }
   q->live.clear();
@@ -485,6 +558,12 @@ sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_qu
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     cudaDeviceGetAttribute(&q->sms, cudaDevAttrMultiProcessorCount, device);
+    // keep freed request memory in the device's stream-ordered pool for reuse
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     const cudaError_t e = cudaStreamCreateWithFlags(&q->stream, cudaStreamNonBlocking);
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
@@ -538,8 +617,15 @@ sense_status sense_queue_submit(sense_queue* q, const sense_shape* shape, const 
     r->lines_h = static_cast<int*>(malloc(r->l_bytes));
     ok = r->y_h && r->s_h && r->lines_h;
   } else {
-    ok = cudaMallocHost(&r->y_h, r->y_bytes) == cudaSuccess && cudaMallocHost(&r->s_h, r->s_bytes) == cudaSuccess &&
-         cudaMallocHost(&r->lines_h, r->l_bytes) == cudaSuccess;
+    r->y_h = pin_get(q, r->y_bytes);
+    r->s_h = pin_get(q, r->s_bytes);
+    r->lines_h = static_cast<int*>(pin_get(q, r->l_bytes));
+    r->x_h = static_cast<float2*>(pin_get(q, r->x_bytes));
+    r->iters_h = static_cast<int*>(pin_get(q, sizeof(int) * F));
+    r->outcome_h = static_cast<int*>(pin_get(q, sizeof(int) * F));
+    r->resid_h = static_cast<double*>(pin_get(q, sizeof(double) * F));
+    r->err_h = static_cast<int*>(pin_get(q, sizeof(int)));
+    ok = r->y_h && r->s_h && r->lines_h && r->x_h && r->iters_h && r->outcome_h && r->resid_h && r->err_h;
   }
   if (!ok) {
     if (q->cfg.fake_device) {
@@ -547,7 +633,8 @@ sense_status sense_queue_submit(sense_queue* q, const sense_shape* shape, const 
       free(r->s_h);
       free(r->lines_h);
     } else {
-      free_host(r);
+      free_host(q, r);
+      free_outputs(q, r);
     }
     delete r;
     return qfail(SENSE_ENOMEM, "pinned staging allocation failed");
@@ -616,8 +703,8 @@ sense_status sense_queue_wait(sense_queue* q, uint64_t id, sense_c32* x_host, in
     free(r->s_h);
     free(r->lines_h);
   } else {
-    free_outputs(r);
-    free_host(r);
+    free_outputs(q, r);
+    free_host(q, r);
   }
   delete r;
   return rc;
@@ -688,9 +775,9 @@ sense_status sense_queue_destroy(sense_queue* q) {
       free(r->s_h);
       free(r->lines_h);
     } else {
-      free_device(r);
-      free_outputs(r);
-      free_host(r);
+      free_device(r, q->stream);
+      free_outputs(q, r);
+      free_host(q, r);
     }
     delete r;
   }
@@ -702,7 +789,14 @@ sense_status sense_queue_destroy(sense_queue* q) {
       if (c.table_h) cudaFreeHost(c.table_h);
       if (c.status_h) cudaFreeHost(c.status_h);
     }
-    if (q->stream) cudaStreamDestroy(q->stream);
+    for (auto& kv : q->twiddles) cudaFree(kv.second);
+    for (auto& kv : q->pin_free)
+      for (void* p : kv.second) cudaFreeHost(p);
+    q->pin_free.clear();
+    if (q->stream) {
+      cudaStreamSynchronize(q->stream);
+      cudaStreamDestroy(q->stream);
+    }
   }
   delete q;
   return SENSE_OK;

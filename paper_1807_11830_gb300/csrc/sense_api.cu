@@ -119,7 +119,7 @@ template <class T>
 sense_status dalloc(sense_plan* pl, T** out, size_t count) {
   void* ptr = nullptr;
   const size_t bytes = count * sizeof(T);
-  cudaError_t e = cudaMalloc(&ptr, bytes ? bytes : 16);
+  cudaError_t e = pl->pool ? cudaMallocAsync(&ptr, bytes ? bytes : 16, pl->pool) : cudaMalloc(&ptr, bytes ? bytes : 16);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(SENSE_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
@@ -134,7 +134,12 @@ void release(sense_plan* pl) {
   collect_spans(pl);
   for (auto& kv : pl->graphs) cudaGraphExecDestroy(kv.second);
   pl->graphs.clear();
-  for (void* ptr : pl->allocs) cudaFree(ptr);
+  for (void* ptr : pl->allocs) {
+    if (pl->pool)
+      cudaFreeAsync(ptr, pl->pool);
+    else
+      cudaFree(ptr);
+  }
   pl->allocs.clear();
   if (pl->live_host) cudaFreeHost(pl->live_host);
   pl->live_host = nullptr;
@@ -481,6 +486,48 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
 
 }  // namespace
 
+namespace {
+
+// Sizes and workspace of a plan (allocation only; tables and zeroing follow).
+sense_status plan_allocate(sense_plan* pl) {
+  const sense_shape& sh = pl->sh;
+  const int W = col_width(sh.ny);
+  pl->tiles = (sh.nx + W - 1) / W;
+  pl->img = (size_t)sh.ny * sh.nx;
+  pl->upd_blocks = (int)((pl->img + UPD_PER_BLOCK - 1) / UPD_PER_BLOCK);
+  pl->norm_variant = 0;
+  pl->norm_tiles = (sh.nx + normal_variant_width(sh.ny, 0) - 1) / normal_variant_width(sh.ny, 0);
+  pl->part_stride = pl->tiles > pl->upd_blocks ? pl->tiles : pl->upd_blocks;
+  const int max_tiles = (sh.nx + 7) / 8;  // narrowest tile of any variant
+  if (pl->part_stride < max_tiles) pl->part_stride = max_tiles;
+  {
+    int min_threads = 1 << 30;
+    for (int v = 0; v < kNormVariants; ++v) {
+      const int th = normal_variant_threads(sh.ny, v);
+      if (th > 0 && th < min_threads) min_threads = th;
+    }
+    pl->max_chunks = (int)((pl->img / 2 + (size_t)min_threads * 4 - 1) / ((size_t)min_threads * 4));
+  }
+  const size_t F = (size_t)sh.frames;
+  sense_status rc = SENSE_OK;
+  if ((pl->own_tw && ((rc = dalloc(pl, &pl->tw_y, (size_t)sh.ny)) != SENSE_OK ||
+                      (rc = dalloc(pl, &pl->tw_x, (size_t)sh.nx)) != SENSE_OK)) ||
+      (rc = dalloc(pl, &pl->tmp, F * sh.coils * sh.lines * sh.nx)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->r, F * pl->img)) != SENSE_OK || (rc = dalloc(pl, &pl->pp[0], F * pl->img)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->pp[1], F * pl->img)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->q, F * pl->img)) != SENSE_OK || (rc = dalloc(pl, &pl->dbl, 5 * F)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->ints, 3 * F + 2)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->counter, F)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->part, F * pl->part_stride)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->ptable, F)) != SENSE_OK || (rc = dalloc(pl, &pl->pints, 4 * F + 1)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->part_nrm, F * (size_t)max_tiles)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->part_upd, F * (size_t)pl->max_chunks)) != SENSE_OK)
+    return rc;
+  return SENSE_OK;
+}
+
+}  // namespace
+
 namespace sense {
 
 void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* x, int k0, double tol,
@@ -507,6 +554,7 @@ void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* 
     fr.coils = sh.coils;
     fr.L = sh.lines;
     fr.k0 = k0;
+    fr.kmax = 1 << 30;
     fr.tol = tol;
   }
 }
@@ -518,6 +566,53 @@ sense_status plan_cg_start(sense_plan* pl, const void* y, const void* S, const i
   SENSE_CUDA_TRY(cudaMemsetAsync(pl->cg(tol).live, 0, sizeof(int), st));
   if (sh.storage == SENSE_STORE_BF16) return run_adjoint<StBF16>(pl, 1, y, S, lines, x, nullptr, tol, st);
   return run_adjoint<StC64>(pl, 1, y, S, lines, x, nullptr, tol, st);
+}
+
+std::vector<float2> plan_twiddles(int n) { return twiddles(n); }
+
+sense_status plan_create_pooled(const sense_shape* shape, int device, cudaStream_t st, const float2* tw_y,
+                                const float2* tw_x, sense_plan** out) {
+  *out = nullptr;
+  sense_status rc = check_shape(shape);
+  if (rc != SENSE_OK) return rc;
+  sense_plan* pl = new sense_plan();
+  pl->sh = *shape;
+  pl->device = device;
+  pl->pool = st;
+  pl->own_tw = false;
+  pl->tw_y = const_cast<float2*>(tw_y);
+  pl->tw_x = const_cast<float2*>(tw_x);
+  if ((rc = plan_allocate(pl)) != SENSE_OK) {
+    release(pl);
+    delete pl;
+    return rc;
+  }
+  const size_t F = (size_t)pl->sh.frames;
+  cudaError_t e = cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->counter, 0, sizeof(unsigned) * F, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->ints, 0, sizeof(int) * (3 * F + 2), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pl->dbl, 0, sizeof(double) * 5 * F, st);
+  if (e != cudaSuccess) {
+    release(pl);
+    delete pl;
+    return fail(SENSE_ECUDA, std::string("pooled plan set-up: ") + cudaGetErrorString(e));
+  }
+  *out = pl;
+  return SENSE_OK;
+}
+
+void plan_destroy_pooled(sense_plan* pl) {
+  if (!pl) return;
+  release(pl);
+  delete pl;
+}
+
+sense_status plan_set_variant_nosync(sense_plan* pl, int variant) {
+  const int W = (variant >= 0 && variant < kNormVariants) ? normal_variant_width(pl->sh.ny, variant) : 0;
+  if (W <= 0) return fail(SENSE_EINVAL, "no such normal-operator variant");
+  pl->norm_variant = variant;
+  pl->norm_tiles = (pl->sh.nx + W - 1) / W;
+  return SENSE_OK;
 }
 
 sense_status plan_cg_finish(sense_plan* pl, int* iters_out, double* resid_out, int* outcome_out, cudaStream_t st) {
@@ -534,6 +629,7 @@ int sense_size_supported(int n) { return size_supported(n) ? 1 : 0; }
 
 const char* sense_last_error(void) { return g_last_error.c_str(); }
 
+
 sense_status sense_plan_create(const sense_shape* shape, int device, sense_plan** out) {
   if (!out) return fail(SENSE_EINVAL, "out is NULL");
   *out = nullptr;
@@ -547,36 +643,8 @@ sense_status sense_plan_create(const sense_shape* shape, int device, sense_plan*
   pl->sh = *shape;
   pl->device = device;
   const sense_shape& sh = pl->sh;
-  const int W = col_width(sh.ny);
-  pl->tiles = (sh.nx + W - 1) / W;
-  pl->img = (size_t)sh.ny * sh.nx;
-  pl->upd_blocks = (int)((pl->img + UPD_PER_BLOCK - 1) / UPD_PER_BLOCK);
-  pl->norm_variant = 0;
-  pl->norm_tiles = (sh.nx + normal_variant_width(sh.ny, 0) - 1) / normal_variant_width(sh.ny, 0);
-  pl->part_stride = pl->tiles > pl->upd_blocks ? pl->tiles : pl->upd_blocks;
-  const int max_tiles = (sh.nx + 7) / 8;  // narrowest tile of any variant
-  if (pl->part_stride < max_tiles) pl->part_stride = max_tiles;
-  {
-    int min_threads = 1 << 30;
-    for (int v = 0; v < kNormVariants; ++v) {
-      const int th = normal_variant_threads(sh.ny, v);
-      if (th > 0 && th < min_threads) min_threads = th;
-    }
-    pl->max_chunks = (int)((pl->img / 2 + (size_t)min_threads * 4 - 1) / ((size_t)min_threads * 4));
-  }
   const size_t F = (size_t)sh.frames;
-  if ((rc = dalloc(pl, &pl->tw_y, (size_t)sh.ny)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->tw_x, (size_t)sh.nx)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->tmp, F * sh.coils * sh.lines * sh.nx)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->r, F * pl->img)) != SENSE_OK || (rc = dalloc(pl, &pl->pp[0], F * pl->img)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->pp[1], F * pl->img)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->q, F * pl->img)) != SENSE_OK || (rc = dalloc(pl, &pl->dbl, 5 * F)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->ints, 3 * F + 2)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->counter, F)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->part, F * pl->part_stride)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->ptable, F)) != SENSE_OK || (rc = dalloc(pl, &pl->pints, 4 * F + 1)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->part_nrm, F * (size_t)max_tiles)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->part_upd, F * (size_t)pl->max_chunks)) != SENSE_OK) {
+  if ((rc = plan_allocate(pl)) != SENSE_OK) {
     release(pl);
     delete pl;
     return rc;

@@ -111,7 +111,7 @@ def test_queue_budget_holds_requests_back():
         except sense.SenseError:
             lo = mid
         qq.close()
-    q = sense.Queue(device=0, hbm_budget_bytes=hi + hi // 2)
+    q = sense.Queue(device=0, hbm_budget_bytes=hi + hi // 2, iters_per_tick=1)
     ids = [q.submit(shape, yh, Sh, ln, max_iter=6) for _ in range(4)]
     for rid in ids:
         q.wait(rid)
