@@ -66,6 +66,38 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
 
 
+def max_over_ranks(values, world, device=None):
+    """Element-wise maximum of per-rank timings (a list of floats) over all
+    ranks of the default process group; identity for one rank."""
+    import torch
+
+    if world <= 1:
+        return list(values)
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def instance_cost(spec):
+    """Relative cost of one instance of the uneven batch: frames x coils x
+    transform work of an n x n image (n^2 log2 n)."""
+    n = spec["n"]
+    return spec["frames"] * spec["coils"] * n * n * np.log2(n)
+
+
+def shard_instances(specs, world, rank):
+    """Longest-processing-time-first assignment of instances to ranks: the
+    instances never exchange data, so each rank solves its own share."""
+    order = sorted(range(len(specs)), key=lambda i: -instance_cost(specs[i]))
+    load = [0.0] * world
+    owner = [0] * len(specs)
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        owner[i] = r
+        load[r] += instance_cost(specs[i])
+    return [i for i in range(len(specs)) if owner[i] == rank]
+
+
 def base_config(world):
     return {
         "workload": WORKLOAD, "ny": N, "nx": N, "frames": FRAMES, "coils": COILS, "lines": N // ACCEL,
@@ -358,10 +390,7 @@ def run_ours(args):
     sense.sense_plan_set_timing(plan, False)
 
     # max over ranks
-    tot = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
-    total_ms, e2e_ms = float(tot[0]), float(tot[1])
+    total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], world, dev)
 
     apps_per_step = FRAMES * ITERS
     value = apps_per_step * world * args.steps / (total_ms / 1e3)
@@ -460,12 +489,18 @@ def run_mix(args):
 
     from paper_1807_11830_gb300 import sense
 
-    dev = torch.device("cuda", 0)
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     sense.load_library()
     ITER = 20
     t0 = time.time()
     specs, inst = mix_inputs(args, dev)
+    if world > 1:  # independent instances: each rank solves its longest-first share
+        mine = shard_instances(specs, world, rank)
+        specs, inst = [specs[i] for i in mine], [inst[i] for i in mine]
     shapes = [dict(ny=sp["n"], nx=sp["n"], coils=sp["coils"], frames=sp["frames"], lines=sp["lines"])
               for sp in specs]
     batch = sense.Batch(shapes)
@@ -507,9 +542,17 @@ def run_mix(args):
     plain_ms = e0.elapsed_time(e1)
     for pl in plans:
         pl.close()
+    batch_ms, plain_ms = max_over_ranks([batch_ms, plain_ms], world, dev)
+    if world > 1:
+        tot = torch.tensor([frames], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tot)
+        frames = int(tot.item())
+        torch.distributed.destroy_process_group()
+        if rank != 0:
+            return 0
     apps = frames * ITER
     line = {
-        "metric": METRIC, "value": apps / (batch_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": apps / (batch_ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "uneven batch: %d instances (n in {128,192,256,384}, coils 8..32, frames 1..30, "
