@@ -306,6 +306,12 @@ sense_status sense_batch_cg_solve(sense_batch* b, const sense_batch_io* io, int 
       size_t off = 0;
       for (int i : c.members) {
         sense_plan* p = b->plans[i];
+        sense_status trc = plan_prepare_tmap(p, io[i].S, st);
+        if (trc != SENSE_OK) {
+          for (PFrame* t : g.tables) cudaFree(t);
+          cudaSetDevice(prev);
+          return trc;
+        }
         plan_frames(p, io[i].S, io[i].lines, reinterpret_cast<float2*>(io[i].x_out), 0, rel_tol, host.data() + off);
         off += p->sh.frames;
       }

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "engine.cuh"
+#include "tma.cuh"
 
 namespace sense {
 
@@ -22,6 +23,7 @@ constexpr int CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXITER = 2, CG_BREAKDOWN = 3
 struct StC64 {
   using T = float2;
   __device__ __forceinline__ static float2 ld(const T* p, size_t i) { return __ldg(p + i); }
+  __device__ __forceinline__ static float2 lds(const T* p, int i) { return p[i]; }  // shared memory
   __device__ __forceinline__ static void st(T* p, size_t i, float2 v) { p[i] = v; }
 };
 
@@ -33,6 +35,7 @@ struct StBF16 {
     memcpy(&h, &u, 4);
     return __bfloat1622float2(h);
   }
+  __device__ __forceinline__ static float2 lds(const T* p, int i) { return __bfloat1622float2(p[i]); }
   __device__ __forceinline__ static void st(T* p, size_t i, float2 v) { p[i] = __float22bfloat162_rn(v); }
 };
 
@@ -79,7 +82,7 @@ SENSE_NORM_VARIANT(192, 1, 1, Col<16, 16, Radices<12, 16>>)
 SENSE_NORM_VARIANT(192, 2, 2, Col<24, 16, Radices<8, 3, 8>>)
 SENSE_NORM_VARIANT(256, 1, 2, Col<32, 16, Radices<8, 4, 8>>)
 SENSE_NORM_VARIANT(256, 2, 1, Col<16, 16, Radices<16, 16>>)
-SENSE_NORM_VARIANT(256, 3, 4, Col<32, 8, Radices<8, 4, 8>>)
+SENSE_NORM_VARIANT(256, 3, 2, Col<32, 8, Radices<8, 4, 8>>)
 SENSE_NORM_VARIANT(320, 1, 1, Col<20, 16, Radices<16, 20>>)
 SENSE_NORM_VARIANT(320, 2, 2, Col<40, 8, Radices<8, 4, 10>>)
 SENSE_NORM_VARIANT(384, 1, 1, Col<24, 16, Radices<16, 24>>)

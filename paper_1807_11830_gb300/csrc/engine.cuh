@@ -80,7 +80,21 @@ struct Col {
   __device__ __forceinline__ int xrow(int j, int n) const { return n * P0 + (t + T * j); }
   // frequency index held in k[j][m]: b + Q_{S-1} m
   __device__ __forceinline__ int krow(int j, int m) const { return (t + T * j) + QL * m; }
-  __device__ __forceinline__ int sidx(int row) const { return row * W + c; }
+  // Shared-memory slot of (row, column).  With W = 8 a half-warp covers the
+  // rows of two adjacent phases t, t + 1 (t even).  Every stage's pair of rows
+  // either starts at an even row and differs by 1, or (the last stage, rows
+  // b*RL + n) differs by RL; flipping bit 0 of the row when (row / RL) is odd
+  // makes the second kind differ by RL +- 1 and leaves the first kind alone,
+  // so both hit disjoint bank halves.  Needs RL even, which every W = 8
+  // configuration has.
+  __device__ __forceinline__ int sidx(int row) const {
+    if constexpr (W == 8) {
+      static_assert(RL % 2 == 0, "W = 8 needs an even last radix");
+      return (row ^ ((row / RL) & 1)) * W + c;
+    } else {
+      return row * W + c;
+    }
+  }
 
   // ---- forward stages ----
   // stage 0: registers in, (S > 1) shared out

@@ -17,7 +17,7 @@ namespace sense {
 
 // shared-memory bytes of the column kernels for configuration C
 template <class C>
-constexpr size_t col_smem_bytes_c() {
+__host__ __device__ constexpr size_t col_smem_bytes_c() {
   constexpr int N = C::N;
   return sizeof(float2) * (size_t)N            // twiddles
          + 2 * sizeof(float2) * (size_t)N * C::W  // two exchange buffers
@@ -26,7 +26,7 @@ constexpr size_t col_smem_bytes_c() {
 }
 
 template <int N>
-constexpr size_t col_smem_bytes() {
+__host__ __device__ constexpr size_t col_smem_bytes() {
   return col_smem_bytes_c<typename Cfg<N>::C>();
 }
 
@@ -448,6 +448,110 @@ __device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem&
       } else {
         a.out[idx] = qv;
       }
+    }
+  return part;
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged variant of normal_tile (CG mode): the maps of each coil arrive
+// as one [N][W] tile in shared memory by a 2D bulk tensor copy, double
+// buffered.  Fill i of the block goes to buffer i & 1 and completes phase
+// (i >> 1) & 1 of that buffer's mbarrier.  The caller has issued the fill of
+// this tile's first coil (fill index nfill); the fill of coil c + 1 is issued
+// after coil c's forward transform, whose barriers guarantee that every
+// thread has finished reading that buffer two coils back.
+// ---------------------------------------------------------------------------
+template <class C, class St>
+struct SStage {
+  typename St::T* buf[2];
+  uint64_t* bar;  // [2]
+  const void* tmap;
+  static constexpr unsigned BYTES = (unsigned)(C::N * C::W * sizeof(typename St::T));
+  // thread 0: copy the [N][W] map tile of coil c, columns tile*W.., into fill slot i
+  __device__ __forceinline__ void issue(unsigned i, int tile, int c) const {
+    typename St::T* dst = buf[i & 1];
+    uint64_t* b = bar + (i & 1);
+    tmap_acquire(tmap);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(b, BYTES);
+    if constexpr (C::N <= 256) {
+      tma_load_2d(dst, tmap, tile * C::W, c * C::N, b);
+    } else {
+      tma_load_2d(dst, tmap, tile * C::W, c * C::N, b);
+      tma_load_2d(dst + (C::N / 2) * C::W, tmap, tile * C::W, c * C::N + C::N / 2, b);
+    }
+  }
+};
+
+template <class C, class St>
+__device__ __forceinline__ float normal_tile_tma(const NormalTile& a, const ColSmem& s, unsigned keep,
+                                                 const SStage<C, St>& sg, unsigned nfill, int* err) {
+  constexpr int N = C::N;
+  const C col;
+  const int x = a.tile * C::W + col.c;
+  const bool xin = x < a.nx;
+  float2 p[C::J0][C::R0], q[C::J0][C::R0];
+#pragma unroll
+  for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+    for (int n = 0; n < C::R0; ++n) {
+      float2 v = make_float2(0.f, 0.f);
+      if (col.ok0(j) && xin) {
+        const size_t idx = (size_t)col.xrow(j, n) * a.nx + x;
+        v = __ldcg(a.p_src + idx);
+        if (a.p_update) {
+          const float2 rv = __ldcg(a.r + idx);
+          v = make_float2(fmaf(a.beta, v.x, rv.x), fmaf(a.beta, v.y, rv.y));
+          __stcg(a.p_dst + idx, v);
+        }
+      }
+      p[j][n] = v;
+      q[j][n] = make_float2(0.f, 0.f);
+    }
+
+  float2* bufs[2] = {s.buf0, s.buf1};
+#pragma unroll 1
+  for (int c = 0; c < a.coils; ++c) {
+    const unsigned i = nfill + (unsigned)c;
+    if (!mbar_wait(sg.bar + (i & 1), (i >> 1) & 1u)) atomicOr(err, ERR_TIMEOUT);
+    const typename St::T* sb = sg.buf[i & 1];
+    float2 xr[C::J0][C::R0];
+    float2 kr[C::JL][C::RL];
+#pragma unroll
+    for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+      for (int n = 0; n < C::R0; ++n) {
+        const float2 sv = col.ok0(j) ? St::lds(sb, col.xrow(j, n) * C::W + col.c) : make_float2(0.f, 0.f);
+        xr[j][n] = cmul(sv, p[j][n]);
+      }
+    col.fwd(xr, kr, bufs, s.tw);
+    if (threadIdx.x == 0 && c + 1 < a.coils) sg.issue(i + 1, a.tile, c + 1);
+#pragma unroll
+    for (int j = 0; j < C::JL; ++j)
+#pragma unroll
+      for (int m = 0; m < C::RL; ++m)
+        if (!((keep >> (j * C::RL + m)) & 1u)) kr[j][m] = make_float2(0.f, 0.f);
+    col.inv(kr, xr, bufs, s.tw);
+#pragma unroll
+    for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+      for (int n = 0; n < C::R0; ++n) {
+        const float2 sv = col.ok0(j) ? St::lds(sb, col.xrow(j, n) * C::W + col.c) : make_float2(0.f, 0.f);
+        q[j][n] = cfma_conj(q[j][n], sv, xr[j][n]);
+      }
+  }
+
+  const float invN = 1.0f / (float)N;
+  float part = 0.f;
+#pragma unroll
+  for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+    for (int n = 0; n < C::R0; ++n) {
+      if (!(col.ok0(j) && xin)) continue;
+      const size_t idx = (size_t)col.xrow(j, n) * a.nx + x;
+      const float2 qv = cscale(q[j][n], invN);
+      __stcg(a.q + idx, qv);
+      part = fmaf(p[j][n].x, qv.x, fmaf(p[j][n].y, qv.y, part));
     }
   return part;
 }

@@ -60,7 +60,8 @@ cudaError_t persistent_nv(const PArgs& a, int sms, cudaStream_t s) {
   } else {
     using C = typename NormCfg<N, V>::C;
     static unsigned long long done = 0;
-    constexpr size_t sm = col_smem_bytes_c<C>();
+    constexpr size_t sm = persistent_smem_bytes<C, St>();
+    static_assert(sm <= 227 * 1024, "persistent kernel shared memory");
     cudaError_t e = ensure_smem(k_cg_persistent<N, V, St>, sm, &done);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

@@ -39,6 +39,7 @@ struct PFrame {
   double *rho, *rho0, *alpha, *beta, *resid;
   int *iters, *outcome, *active;
   int coils, L;
+  const void* tmap;    // TMA descriptor of S ([C*N] rows x nx, box W x min(N, N/2 if N > 256))
   int k0;              // CG iterations this frame has already done before the launch
   int kmax;            // the frame does no work at global iterations >= kmax
   double tol;          // relative-residual stopping tolerance (0: none)
@@ -81,14 +82,33 @@ __device__ __forceinline__ bool wait_at_least(const int* flag, int target, long 
   return true;
 }
 
+// shared memory of the persistent kernel: two map tiles, then the column
+// kernels' layout, then two mbarriers
+template <class C, class St>
+__host__ __device__ constexpr size_t persistent_smem_bytes() {
+  return 2 * (size_t)C::N * C::W * sizeof(typename St::T) + ((col_smem_bytes_c<C>() + 7) & ~(size_t)7) + 16;
+}
+
 template <int N, int V, class St, int TH = NormCfg<N, V>::C::THREADS, int MINB = NormCfg<N, V>::MINB>
 __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
   using C = typename NormCfg<N, V>::C;
+  using E = typename St::T;
   constexpr int T = C::THREADS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const ColSmem s = col_smem_c<C>(smem_raw);
+  constexpr size_t SB = (size_t)N * C::W * sizeof(E);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  SStage<C, St> sg;
+  sg.buf[0] = reinterpret_cast<E*>(smem_raw);
+  sg.buf[1] = reinterpret_cast<E*>(smem_raw + SB);
+  const ColSmem s = col_smem_c<C>(smem_raw + 2 * SB);
+  sg.bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * SB + ((col_smem_bytes_c<C>() + 7) & ~(size_t)7));
   __shared__ int s_ticket, s_ok, s_active;
   for (int i = threadIdx.x; i < N; i += T) s.tw[i] = a.tw[i];
+  if (threadIdx.x == 0) {
+    mbar_init(sg.bar, 1);
+    mbar_init(sg.bar + 1, 1);
+    mbar_fence_init();
+  }
+  unsigned nfill = 0;  // map tiles requested so far by this block (same in every thread)
 
   const int per_iter = a.nframes * (a.tiles + a.chunks);
   const long total = (long)per_iter * a.iters;
@@ -127,6 +147,8 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
 
     if (normal) {
       if (work) {
+        sg.tmap = fr.tmap;
+        if (threadIdx.x == 0) sg.issue(nfill, piece, 0);  // first coil's maps, overlapping the set-up below
         // line map of this frame
         for (int i = threadIdx.x; i < N; i += T) s.map[i] = -1;
         __syncthreads();
@@ -152,7 +174,8 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
         nt.tile = piece;
         nt.p_update = kg > 0 ? 1 : 0;
         nt.beta = kg > 0 ? (float)__ldcg(fr.beta) : 0.f;
-        const float part = normal_tile<C, St, true>(nt, s, keep);
+        const float part = normal_tile_tma<C, St>(nt, s, keep, sg, nfill, a.err);
+        nfill += (unsigned)fr.coils;
         const double tot = block_sum<T>((double)part, s.red);
         if (threadIdx.x == 0) __stcg(g.part_nrm + (size_t)f * a.tiles + piece, tot);
       }

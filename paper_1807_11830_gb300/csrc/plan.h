@@ -1,6 +1,7 @@
 // Private definition of the plan object and the host helpers shared by the
 // library's units (not part of the C ABI).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <map>
@@ -23,6 +24,10 @@ struct sense_plan {
   int norm_tiles = 0;    // column tiles per frame of that variant
   int cg_mode = 1;       // 0: per-phase kernels replayed as CUDA graphs; 1: one persistent launch
   cudaStream_t pool = nullptr;  // non-null: workspace is stream-ordered (cudaMallocAsync) on this stream
+  CUtensorMap tmap_host;        // TMA descriptor of the maps S for the persistent kernel
+  CUtensorMap* tmap_d = nullptr;
+  const void* tmap_S = nullptr; // S and tile width the descriptor was encoded for
+  int tmap_W = 0;
   bool own_tw = true;           // false: twiddle tables are shared and owned elsewhere
   int sms = 0;           // multiprocessors of the plan's device
   PFrame* ptable = nullptr;       // device frame table of the persistent kernel
@@ -106,6 +111,10 @@ void plan_destroy_pooled(sense_plan* pl);
 sense_status plan_set_variant_nosync(sense_plan* pl, int variant);
 // exp(-2 pi i m / n), m < n, in FP64 rounded once to FP32 (host table).
 std::vector<float2> plan_twiddles(int n);
+
+// Encode (when S or the kernel variant changed) the TMA descriptor of S and
+// queue its upload on `st`.  Must not run during stream capture.
+sense_status plan_prepare_tmap(sense_plan* pl, const void* S, cudaStream_t st);
 
 // Per-frame outputs of a finished CG solve of a plan (iterations, residual,
 // outcome; NULL outputs are skipped).

@@ -312,6 +312,10 @@ bool admit_device(sense_queue* q, Request* r, std::string* err) {
     *err = sense_last_error();
     return false;
   }
+  if (plan_prepare_tmap(r->plan, r->s_d, st) != SENSE_OK) {
+    *err = sense_last_error();
+    return false;
+  }
   if (plan_cg_start(r->plan, r->y_d, r->s_d, r->lines_d, r->x_d, r->tol, st) != SENSE_OK) {
     *err = sense_last_error();
     return false;

@@ -412,6 +412,10 @@ sense_status run_cg_persistent(sense_plan* pl, const void* S, const int* lines, 
                                cudaStream_t st) {
   const sense_shape& sh = pl->sh;
   const int F = sh.frames;
+  {
+    sense_status rc = plan_prepare_tmap(pl, S, st);
+    if (rc != SENSE_OK) return rc;
+  }
   if (pl->ptable_key[0] != S || pl->ptable_key[1] != (const void*)lines || pl->ptable_key[2] != (const void*)x ||
       pl->ptable_tol != tol) {
     SENSE_CUDA_TRY(cudaStreamSynchronize(st));  // the staging copy may still be read by an earlier call
@@ -521,7 +525,8 @@ sense_status plan_allocate(sense_plan* pl) {
       (rc = dalloc(pl, &pl->part, F * pl->part_stride)) != SENSE_OK ||
       (rc = dalloc(pl, &pl->ptable, F)) != SENSE_OK || (rc = dalloc(pl, &pl->pints, 4 * F + 1)) != SENSE_OK ||
       (rc = dalloc(pl, &pl->part_nrm, F * (size_t)max_tiles)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->part_upd, F * (size_t)pl->max_chunks)) != SENSE_OK)
+      (rc = dalloc(pl, &pl->part_upd, F * (size_t)pl->max_chunks)) != SENSE_OK ||
+      (rc = dalloc(pl, &pl->tmap_d, 1)) != SENSE_OK)
     return rc;
   return SENSE_OK;
 }
@@ -553,6 +558,7 @@ void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* 
     fr.active = g.active + f;
     fr.coils = sh.coils;
     fr.L = sh.lines;
+    fr.tmap = pl->tmap_d;
     fr.k0 = k0;
     fr.kmax = 1 << 30;
     fr.tol = tol;
@@ -569,6 +575,52 @@ sense_status plan_cg_start(sense_plan* pl, const void* y, const void* S, const i
 }
 
 std::vector<float2> plan_twiddles(int n) { return twiddles(n); }
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+}  // namespace
+
+sense_status plan_prepare_tmap(sense_plan* pl, const void* S, cudaStream_t st) {
+  const sense_shape& sh = pl->sh;
+  const int W = normal_variant_width(sh.ny, pl->norm_variant);
+  if (pl->tmap_S == S && pl->tmap_W == W) return SENSE_OK;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return fail(SENSE_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const bool bf16 = sh.storage == SENSE_STORE_BF16;
+  const cuuint64_t elem = bf16 ? 4 : 8;
+  // S viewed as a 2D tensor: [coils * ny] rows of nx elements
+  const cuuint64_t dims[2] = {(cuuint64_t)sh.nx, (cuuint64_t)sh.coils * sh.ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)sh.nx * elem};
+  const cuuint32_t box[2] = {(cuuint32_t)W, (cuuint32_t)(sh.ny <= 256 ? sh.ny : sh.ny / 2)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(&pl->tmap_host, bf16 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 2,
+                         const_cast<void*>(S), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(SENSE_EINVAL, "TMA descriptor of S rejected (code " + std::to_string((int)r) + ")");
+  // pageable source: the copy is staged before this call returns
+  SENSE_CUDA_TRY(cudaMemcpyAsync(pl->tmap_d, &pl->tmap_host, sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+  pl->tmap_S = S;
+  pl->tmap_W = W;
+  return SENSE_OK;
+}
 
 sense_status plan_create_pooled(const sense_shape* shape, int device, cudaStream_t st, const float2* tw_y,
                                 const float2* tw_x, sense_plan** out) {

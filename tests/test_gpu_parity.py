@@ -293,3 +293,23 @@ def test_bounded_wait_gives_up_and_device_stays_usable():
     y = oracle.forward(p.x_true, p.S, p.lines) + p.noise
     xg, ig, _, _ = gpu_cg(y, p.S, p.lines, 3)
     assert list(ig) == [3]
+
+
+@pytest.mark.parametrize("n", [8, 12, 16, 20, 32, 64, 96, 128, 160, 192, 256, 320, 384])
+def test_cg_persistent_every_length(n):
+    """Persistent CG (maps staged into shared memory by TMA) at every
+    compiled length, including tiles wider than the image (nx < 16)."""
+    rng = synth.rng_for(7000 + n)
+    C, F = 3, 2
+    L = max(1, n // 3)
+    S = synth.sensitivities(C, n, n)
+    lines = synth.mask_lines(n, L, min(4, L), F, rng)
+    x = synth.random_complex((F, n, n), rng)
+    y = oracle.forward(x, S, lines)
+    K = 6
+    xo, io, _, so = oracle.cg(_as32(y), _as32(S), lines, K)
+    plan = make_plan(S, lines)
+    sense.sense_plan_set_cg_mode(plan, sense.CG_MODE_PERSISTENT)
+    xg, ig, _, sg = gpu_cg(y, S, lines, K, plan=plan)
+    assert rel(xg, xo) <= CG_TOL
+    np.testing.assert_array_equal(ig, io)
