@@ -295,14 +295,18 @@ sense_status sense_plan_set_variant(sense_plan* plan, int variant);
 int sense_plan_variant(const sense_plan* plan);
 
 /* Autotuner: time every variant of the normal-operator kernel on this plan's
- * shape with the caller's S and lines (device pointers; the plan's own CG
- * vectors serve as scratch input and output), keep the fastest and return it
- * in *variant_out.  ms_out (may be NULL) receives the mean milliseconds per
- * launch of each variant (kernel variants that do not exist get -1); it must
- * hold 4 values.  Results are cached per (device, shape, storage) for the
- * process, and appended to the file named by the environment variable
- * SENSE_AUTOTUNE_CACHE when set (read back on first use).  A cached shape is
- * not re-timed.  Synchronises `stream`. */
+ * shape with the caller's S and lines (device pointers), keep the fastest and
+ * return it in *variant_out.  What is timed follows the plan's CG mode: in
+ * persistent mode (the default) a 10-iteration CG solve with a constant
+ * k-space right-hand side, in temporary device buffers the call allocates and
+ * frees; in the graph and direct modes one normal-operator launch, with the
+ * plan's own CG vectors as scratch.  ms_out (may be NULL) receives the mean
+ * milliseconds per timed unit of each variant (kernel variants that do not
+ * exist get -1); it must hold 4 values.  Results are cached per (device,
+ * shape, storage, timed mode) for the process, and appended to the file named
+ * by the environment variable SENSE_AUTOTUNE_CACHE when set (read back on
+ * first use).  A cached shape is not re-timed.  Synchronises `stream`;
+ * device-flagged errors are reported as by sense_plan_check. */
 sense_status sense_plan_autotune(sense_plan* plan, const void* S, const int32_t* lines, int* variant_out,
                                  double* ms_out, void* stream);
 

@@ -358,12 +358,13 @@ sense_status cg_chunk_graph(sense_plan* pl, const void* S, const int* lines, flo
 }
 
 // ---- autotune cache: in-process map, optionally mirrored to a text file ----
-// (SENSE_AUTOTUNE_CACHE=path; one "device ny nx coils frames lines storage variant" per line)
+// (SENSE_AUTOTUNE_CACHE=path; one "device ny nx coils frames lines storage mode variant" per line,
+// mode 1 for a persistent-CG timing, 0 for a normal-operator launch timing)
 struct TuneKey {
-  int device, ny, nx, coils, frames, lines, storage;
+  int device, ny, nx, coils, frames, lines, storage, mode;
   bool operator<(const TuneKey& o) const {
-    return std::tie(device, ny, nx, coils, frames, lines, storage) <
-           std::tie(o.device, o.ny, o.nx, o.coils, o.frames, o.lines, o.storage);
+    return std::tie(device, ny, nx, coils, frames, lines, storage, mode) <
+           std::tie(o.device, o.ny, o.nx, o.coils, o.frames, o.lines, o.storage, o.mode);
   }
 };
 std::mutex g_tune_mutex;
@@ -379,8 +380,8 @@ void tune_load_file_locked() {
   if (!fh) return;
   TuneKey k{};
   int v = 0;
-  while (std::fscanf(fh, "%d %d %d %d %d %d %d %d", &k.device, &k.ny, &k.nx, &k.coils, &k.frames, &k.lines,
-                     &k.storage, &v) == 8)
+  while (std::fscanf(fh, "%d %d %d %d %d %d %d %d %d", &k.device, &k.ny, &k.nx, &k.coils, &k.frames, &k.lines,
+                     &k.storage, &k.mode, &v) == 9)
     if (v >= 0 && v < kNormVariants && normal_variant_width(k.ny, v) > 0) g_tune[k] = v;
   std::fclose(fh);
 }
@@ -400,7 +401,8 @@ void tune_cache_store(const TuneKey& k, int v) {
   if (!path || !*path) return;
   FILE* fh = std::fopen(path, "a");
   if (!fh) return;
-  std::fprintf(fh, "%d %d %d %d %d %d %d %d\n", k.device, k.ny, k.nx, k.coils, k.frames, k.lines, k.storage, v);
+  std::fprintf(fh, "%d %d %d %d %d %d %d %d %d\n", k.device, k.ny, k.nx, k.coils, k.frames, k.lines, k.storage,
+               k.mode, v);
   std::fclose(fh);
 }
 
@@ -854,40 +856,57 @@ sense_status sense_plan_autotune(sense_plan* pl, const void* S, const int32_t* l
   if (!aligned16(S) || !aligned4(lines)) return fail(SENSE_EINVAL, "S must be 16-byte aligned, lines 4-byte");
   DeviceGuard guard(pl->device);
   const sense_shape& sh = pl->sh;
-  const TuneKey key{pl->device, sh.ny, sh.nx, sh.coils, sh.frames, sh.lines, sh.storage};
+  const bool persistent = pl->cg_mode == 1;
+  const TuneKey key{pl->device, sh.ny, sh.nx, sh.coils, sh.frames, sh.lines, sh.storage, persistent ? 1 : 0};
   int best = tune_cache_lookup(key);
   if (ms_out)
     for (int v = 0; v < kNormVariants; ++v) ms_out[v] = -1.0;
   cudaStream_t st = as_stream(stream);
   if (best < 0) {
-    SENSE_CUDA_TRY(cudaMemsetAsync(pl->r, 0, sizeof(float2) * pl->img * sh.frames, st));
+    // Persistent mode times a short fixed-length CG solve, whose cost the
+    // kernel variant decides together with the block count per SM; the
+    // right-hand side is a constant k-space pattern on the sampled lines, so
+    // no frame breaks down early.  Otherwise one normal-operator launch.
+    const bool bf16 = sh.storage == SENSE_STORE_BF16;
+    const size_t y_bytes = (size_t)sh.frames * sh.coils * sh.lines * sh.nx * (bf16 ? 4 : 8);
+    void* y_tmp = nullptr;
+    float2* x_tmp = nullptr;
+    if (persistent) {
+      SENSE_CUDA_TRY(cudaStreamSynchronize(st));
+      SENSE_CUDA_TRY(cudaMalloc(&y_tmp, y_bytes));
+      if (cudaMalloc(&x_tmp, sizeof(float2) * pl->img * sh.frames) != cudaSuccess) {
+        cudaFree(y_tmp);
+        return fail(SENSE_ENOMEM, "autotune scratch");
+      }
+      cudaMemsetAsync(y_tmp, 0x3c, y_bytes, st);  // every component 0x3c3c.. > 0
+    } else {
+      SENSE_CUDA_TRY(cudaMemsetAsync(pl->r, 0, sizeof(float2) * pl->img * sh.frames, st));
+    }
+    constexpr int kTuneIters = 10;
+    auto run_once = [&]() -> sense_status {
+      if (persistent)
+        return bf16 ? run_cg_solve<StBF16>(pl, y_tmp, S, lines, kTuneIters, 0.0, x_tmp, nullptr, nullptr, nullptr, st)
+                    : run_cg_solve<StC64>(pl, y_tmp, S, lines, kTuneIters, 0.0, x_tmp, nullptr, nullptr, nullptr, st);
+      return bf16 ? run_normal<StBF16>(pl, pl->r, S, lines, pl->q, st)
+                  : run_normal<StC64>(pl, pl->r, S, lines, pl->q, st);
+    };
     cudaEvent_t a = nullptr, b = nullptr;
-    SENSE_CUDA_TRY(cudaEventCreate(&a));
-    SENSE_CUDA_TRY(cudaEventCreate(&b));
+    sense_status rc = SENSE_OK;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+      rc = fail(SENSE_ECUDA, "autotune events");
     double best_ms = 1e30;
+    const int warm = persistent ? 1 : 3, reps = persistent ? 3 : 10;
     const int saved_timing = pl->timing;
     pl->timing = 0;
-    for (int v = 0; v < kNormVariants; ++v) {
+    for (int v = 0; v < kNormVariants && rc == SENSE_OK; ++v) {
       if (normal_variant_width(sh.ny, v) <= 0) continue;
-      sense_status rc = sense_plan_set_variant(pl, v);
+      rc = sense_plan_set_variant(pl, v);
+      for (int it = 0; it < warm && rc == SENSE_OK; ++it) rc = run_once();
       if (rc != SENSE_OK) break;
-      for (int it = 0; it < 3; ++it) {  // warm-up
-        rc = sh.storage == SENSE_STORE_BF16 ? run_normal<StBF16>(pl, pl->r, S, lines, pl->q, st)
-                                            : run_normal<StC64>(pl, pl->r, S, lines, pl->q, st);
-        if (rc != SENSE_OK) break;
-      }
-      const int reps = 10;
       cudaEventRecord(a, st);
-      for (int it = 0; it < reps && rc == SENSE_OK; ++it)
-        rc = sh.storage == SENSE_STORE_BF16 ? run_normal<StBF16>(pl, pl->r, S, lines, pl->q, st)
-                                            : run_normal<StC64>(pl, pl->r, S, lines, pl->q, st);
+      for (int it = 0; it < reps && rc == SENSE_OK; ++it) rc = run_once();
       cudaEventRecord(b, st);
-      if (rc != SENSE_OK) {
-        pl->timing = saved_timing;
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-        return rc;
-      }
+      if (rc != SENSE_OK) break;
       float ms = 0.f;
       cudaEventSynchronize(b);
       cudaEventElapsedTime(&ms, a, b);
@@ -899,8 +918,15 @@ sense_status sense_plan_autotune(sense_plan* pl, const void* S, const int32_t* l
       }
     }
     pl->timing = saved_timing;
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (persistent) {
+      cudaStreamSynchronize(st);
+      cudaFree(y_tmp);
+      cudaFree(x_tmp);
+    }
+    if (rc == SENSE_OK) rc = sense_plan_check(pl, stream);
+    if (rc != SENSE_OK) return rc;
     if (best < 0) return fail(SENSE_ECUDA, "autotune found no runnable variant");
     tune_cache_store(key, best);
   }

@@ -241,10 +241,21 @@ def test_cg_every_variant_and_autotune():
             continue
         xg, ig, _, _ = gpu_cg(y, p.S, p.lines, 8, plan=plan)
         assert rel(xg, xo) <= CG_TOL, v
+    # persistent mode (the default) times short CG solves on scratch buffers
     chosen, times = sense.sense_plan_autotune(plan, c64(p.S), i32(p.lines))
     assert chosen in times and len(times) >= 2
     assert sense.sense_plan_variant(plan) == chosen
-    print("autotune 256^2 C12 F3:", chosen, times)
+    print("autotune persistent 256^2 C12 F3:", chosen, times)
+    xg, ig, _, _ = gpu_cg(y, p.S, p.lines, 8, plan=plan)  # the plan's own state is intact
+    assert rel(xg, xo) <= CG_TOL
+    # the graph mode is timed (and cached) separately, per launch
+    sense.sense_plan_set_cg_mode(plan, sense.CG_MODE_GRAPH)
+    chosen_g, times_g = sense.sense_plan_autotune(plan, c64(p.S), i32(p.lines))
+    assert chosen_g in times_g and set(times_g) == set(times)
+    assert max(times_g.values()) < min(times.values())  # one launch vs ten iterations
+    print("autotune graph 256^2 C12 F3:", chosen_g, times_g)
+    xg, ig, _, _ = gpu_cg(y, p.S, p.lines, 8, plan=plan)
+    assert rel(xg, xo) <= CG_TOL
 
 
 @pytest.mark.parametrize("which", ["slice64", "cine256", "slices320", "mix192"])
