@@ -39,6 +39,11 @@ WORKLOAD = "cine 256x256, 20 frames, 12 coils, R=4 (64 lines, 16 centre), 30 CG-
 METRIC = "E^H·E applications/s"
 UNIT = "applications/s"
 FLUSH_BYTES = 512 << 20
+PAPER_WORKLOAD = ("paper reconstruction: 16 frames x 160x160, 8 coils, fully sampled; "
+                  "2D inverse FFT + root-sum-of-squares (Sec. V)")
+PAPER_METRIC, PAPER_UNIT = "reconstructions/s", "reconstructions/s"
+# OpenCLIPER's own time for this workload on a GTX 970 (Table II: clFFT 1.361 ms + RSS 0.252 ms): context
+PAPER_GTX970_MS = 1.361 + 0.252
 
 
 def parse_args():
@@ -49,9 +54,10 @@ def parse_args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=20)
-    ap.add_argument("--workload", default="cine", choices=("cine", "mix", "serve"),
+    ap.add_argument("--workload", default="cine", choices=("cine", "mix", "serve", "paper"),
                     help="cine: the headline line; mix: 512-instance uneven batch vs the plain loop; "
-                         "serve: Poisson request streams through the serving queue vs serial plain solves")
+                         "serve: Poisson request streams through the serving queue vs serial plain solves; "
+                         "paper: the paper's timed FFT + RSS reconstruction (and the Eq. 1 combine)")
     ap.add_argument("--mix-count", type=int, default=512)
     ap.add_argument("--serve-rates", default="50,200,800")
     ap.add_argument("--serve-requests", type=int, default=160)
@@ -144,6 +150,8 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
+    if args.workload == "paper":
+        return run_reference_paper(args)
     import oracle
 
     threads = oracle.threads()
@@ -663,6 +671,219 @@ def run_serve(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# the paper's timed workload: fully sampled 2D inverse FFT + RSS (and Eq. 1)
+# ---------------------------------------------------------------------------
+_PAPER_ORACLE = {}
+
+
+def paper_oracle_inputs():
+    """k-space of the paper workload made once by the oracle's E (untimed)."""
+    if not _PAPER_ORACLE:
+        import oracle
+        from paper_1807_11830_gb300 import synth
+
+        p = synth.paper_160()
+        S = p.S.astype(np.complex64).astype(np.complex128)
+        y = oracle.forward(p.x_true.astype(np.complex64), S, p.lines) + p.noise
+        _PAPER_ORACLE.update(y=y, lines=p.lines, n=p.x_true.shape[1])
+    return _PAPER_ORACLE
+
+
+def paper_oracle_sample(min_seconds):
+    """Oracle FFT + RSS reconstructions of the whole workload, repeated for at
+    least `min_seconds`.  Returns (reconstructions/s, wall, count, threads)."""
+    import oracle
+
+    d = paper_oracle_inputs()
+    count, t0 = 0, time.perf_counter()
+    while True:
+        oracle.rss(d["y"], d["lines"], d["n"])
+        count += 1
+        wall = time.perf_counter() - t0
+        if wall >= min_seconds:
+            return count / wall, wall, count, min(oracle.threads(), d["y"].shape[0])
+
+
+def run_reference_paper(args):
+    for _ in range(args.warmup):
+        paper_oracle_sample(0.0)
+    walls, count = [], 0
+    for _ in range(args.steps):
+        _, wall, c, threads = paper_oracle_sample(0.0)
+        walls.append(wall)
+        count += c
+    value = count / sum(walls)
+    line = {
+        "metric": PAPER_METRIC, "value": value, "unit": PAPER_UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": PAPER_WORKLOAD, "ny": 160, "nx": 160, "frames": 16, "coils": 8},
+        "cpu_baseline": {"value": value, "unit": PAPER_UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "one whole reconstruction (16 frames x 8 coils) per step"},
+        "e2e": {"value": value, "unit": PAPER_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_paper(args):
+    import torch
+
+    from paper_1807_11830_gb300 import build as sense_build
+    from paper_1807_11830_gb300 import sense, synth
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if not os.path.exists(sense.LIB_PATH):
+        sense_build.build()
+    sense.load_library()
+
+    p = synth.paper_160()
+    F, C, n = p.x_true.shape[0], p.S.shape[0], p.x_true.shape[1]
+    plan = sense.Plan(n, n, C, F, n, device=local_rank)
+    x_true = torch.from_numpy(p.x_true.astype(np.complex64)).to(dev)
+    S = torch.from_numpy(p.S.astype(np.complex64)).to(dev)
+    lines = torch.from_numpy(p.lines).to(dev)
+    y = torch.empty((F, C, n, n), dtype=torch.complex64, device=dev)
+    sense.sense_forward(plan, x_true, S, lines, y)
+    y += torch.from_numpy(p.noise.astype(np.complex64)).to(dev)
+    out = torch.empty((F, n, n), dtype=torch.float32, device=dev)
+    combined = torch.empty((F, n, n), dtype=torch.complex64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        sense.sense_rss(plan, y, lines, out, stream=stream)
+
+    def step_eq1():
+        sense.sense_adjoint(plan, y, S, lines, combined, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+        step_eq1()
+    torch.cuda.synchronize(dev)
+    sense.sense_plan_check(plan)
+
+    def timed(fn):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        barrier()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            fn()
+            ends[k].record(stream)
+        barrier()
+        return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    t_wall0 = time.time()
+    step_ms = timed(step)
+    t_wall1 = time.time()
+    eq1_ms = timed(step_eq1)
+
+    # end to end: pinned k-space in, RSS image out, inside the timed region
+    y_h = y.cpu().pin_memory()
+    lines_h = lines.cpu().pin_memory()
+    out_h = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+    y_d = torch.empty_like(y)
+    lines_d = torch.empty_like(lines)
+
+    def e2e_step():
+        y_d.copy_(y_h, non_blocking=True)
+        lines_d.copy_(lines_h, non_blocking=True)
+        sense.sense_rss(plan, y_d, lines_d, out, stream=stream)
+        out_h.copy_(out, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    e2e_list = timed(e2e_step)
+    clocks.stop()
+
+    # per-kernel times with the plan's event timers
+    sense.sense_plan_set_timing(plan, True)
+    for _ in range(5):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize(dev)
+    phase = {}
+    for name in sense.PHASES:
+        ms, cnt = sense.sense_plan_phase_time(plan, name)
+        if cnt:
+            phase[name] = ms / cnt
+    sense.sense_plan_set_timing(plan, False)
+    sense.sense_plan_check(plan)
+
+    total_ms, eq1_total, e2e_total = max_over_ranks([sum(step_ms), sum(eq1_ms), sum(e2e_list)], world, dev)
+    value = world * args.steps / (total_ms / 1e3)
+    if rank == 0:
+        hbm_gbs, _, peak_src = peaks()
+        cimg = 8.0 * F * C * n * n  # one pass over the complex k-space (or its row-transformed copy)
+        kernel_bytes = {"rows_inv": 2 * cimg, "adj_col": cimg + 4.0 * F * n * n}
+        dom = max(kernel_bytes, key=lambda k: phase.get(k, 0.0))
+        dur_s = phase[dom] / 1e3
+        achieved = kernel_bytes[dom] / dur_s / 1e9
+        roofline = {
+            "kernel": {"rows_inv": "k_rows<160,+1> (inverse x-transforms of every k-space row)",
+                       "adj_col": "k_adj_col<160,c64,rss> (inverse y-transforms, |.|^2 summed over coils, sqrt)"}[dom],
+            "bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
+            "traffic": None, "peak_source": "%s hbm_gbs (copy)" % peak_src,
+            "algorithmic_mb_per_launch": kernel_bytes[dom] / 1e6, "duration_us": dur_s * 1e6,
+            "whole_op_minimum_mb": (cimg + 4.0 * F * n * n) / 1e6,
+        }
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            v, wall, cnt, threads = paper_oracle_sample(10.0)
+            cpu = {"value": v, "unit": PAPER_UNIT, "cores": threads, "kind": "oracle",
+                   "sample": "%d whole reconstructions (16 frames x 8 coils, FP64), %.1f s" % (cnt, wall)}
+        paper_value = 1e3 / PAPER_GTX970_MS
+        line = {
+            "metric": PAPER_METRIC, "value": value, "unit": PAPER_UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": value / paper_value, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": PAPER_WORKLOAD, "ny": n, "nx": n, "frames": F, "coils": C,
+                       "l2": "flushed before every timed step (512 MiB device write)",
+                       "parallelism": "replicas x%d (independent problems, no collective)" % world},
+            "baseline_context": "OpenCLIPER on a GTX 970, clFFT 1.361 ms + RSS 0.252 ms (Table II): "
+                                "another machine, context only",
+            "e2e": {"value": world * args.steps / (e2e_total / 1e3), "unit": PAPER_UNIT,
+                    "h2d_bytes_per_step": int(y.numel() * 8 + lines.numel() * 4),
+                    "d2h_bytes_per_step": int(out.numel() * 4), "ms_per_step": e2e_total / args.steps},
+            "eq1_combine": {"value": world * args.steps / (eq1_total / 1e3), "unit": PAPER_UNIT,
+                            "ms_per_step": eq1_total / args.steps,
+                            "kind": "sense_adjoint with every line sampled: sum_c conj(S_c) F^-1(Y_c)"},
+            "gpu_launches": 2 * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks.summary(t_wall0, t_wall1),
+            "kernels_us": {k: round(v * 1e3, 2) for k, v in phase.items()},
+            "step_ms_p50": statistics.median(step_ms), "step_ms_min": min(step_ms),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    plan.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -671,6 +892,8 @@ def main():
         return run_mix(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "paper":
+        return run_paper(args)
     return run_ours(args)
 
 

@@ -200,6 +200,20 @@ MIX_SIZES = (128, 192, 256, 384)
 MIX_ACCEL = (2, 3, 4, 6)
 
 
+def paper_160(seed=BASE_SEED + 5, frames=16, noise_sigma=1e-3):
+    """The shapes of the timed reconstruction of Sec. V (16 cine frames of
+    160x160, 8 coils, fully sampled Cartesian k-space), with 10-ellipse
+    phantoms; it feeds the 2D inverse FFT + root-sum-of-squares and the
+    Eq. 1 combine."""
+    rng = rng_for(seed)
+    n, C = 160, 8
+    x = phantom(n, n, 10, rng, frames=frames, period=frames)
+    S = sensitivities(C, n, n)
+    lines = full_lines(n, frames)
+    nz = complex_noise((frames, C, n, n), noise_sigma, rng)
+    return Problem("paper 160x160 F%d C8 full" % frames, x, S, lines, nz, 0)
+
+
 def draw_mix(count=512, seed=BASE_SEED + 3):
     """Instance shapes of the uneven-batching workload: n from
     {128,192,256,384}, coils U{8..32}, frames U{1..30}, R from {2,3,4,6}."""

@@ -205,6 +205,18 @@ def test_rss(shape):
     assert rel(gpu_rss(y, lines, ny), oracle.rss(_as32(y), lines, ny)) <= OP_TOL
 
 
+def test_paper_workload_full_size():
+    """The paper's timed reconstruction at its full shape (16 frames of
+    160x160, 8 coils, fully sampled), as the bench runs it: the FFT + RSS
+    image and the Eq. 1 combine, every output element against the oracle."""
+    p = synth.paper_160()
+    S32 = _as32(p.S)
+    y = oracle.forward(p.x_true.astype(np.complex64), S32, p.lines) + p.noise
+    assert y.shape == (16, 8, 160, 160)
+    assert rel(gpu_rss(y, p.lines, 160), oracle.rss(_as32(y), p.lines, 160)) <= OP_TOL
+    assert rel(gpu_adjoint(y, p.S, p.lines), oracle.adjoint(_as32(y), S32, p.lines)) <= OP_TOL
+
+
 VARIANT_SHAPES = [(128, 128, 5, 40, 2), (192, 192, 6, 48, 1), (256, 256, 12, 64, 2), (320, 320, 6, 107, 1),
                   (384, 384, 4, 96, 1), (256, 96, 3, 64, 1)]
 
