@@ -193,7 +193,7 @@ sense_status sense_batch_create(const sense_shape* shapes, int count, int device
       const size_t img2 = (size_t)c.ny * c.nx / 2;
       c.part_upd_cap = (img2 + (size_t)min_threads * 4 - 1) / ((size_t)min_threads * 4);
       if ((rc = balloc(b, &c.ints, 4 * (size_t)c.frames + 1)) != SENSE_OK) break;
-      if ((rc = balloc(b, &c.part_nrm, (size_t)c.frames * ((c.nx + 7) / 8))) != SENSE_OK) break;
+      if ((rc = balloc(b, &c.part_nrm, (size_t)c.frames * ((c.nx + 3) / 4))) != SENSE_OK) break;
       if ((rc = balloc(b, &c.part_upd, (size_t)c.frames * c.part_upd_cap)) != SENSE_OK) break;
     }
   }

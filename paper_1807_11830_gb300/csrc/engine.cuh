@@ -49,7 +49,7 @@ struct Col {
   static constexpr int T = T_, W = W_;
   static constexpr int THREADS = T * W;
   static_assert(S >= 1, "at least one stage");
-  static_assert(W == 8 || W == 16 || W == 32, "tile width");
+  static_assert(W == 4 || W == 8 || W == 16 || W == 32, "tile width");
   static_assert(THREADS % 32 == 0, "block size must be a multiple of 32");
 
   template <int s>
@@ -80,17 +80,19 @@ struct Col {
   __device__ __forceinline__ int xrow(int j, int n) const { return n * P0 + (t + T * j); }
   // frequency index held in k[j][m]: b + Q_{S-1} m
   __device__ __forceinline__ int krow(int j, int m) const { return (t + T * j) + QL * m; }
-  // Shared-memory slot of (row, column).  With W = 8 a half-warp covers the
-  // rows of two adjacent phases t, t + 1 (t even).  Every stage's pair of rows
-  // either starts at an even row and differs by 1, or (the last stage, rows
-  // b*RL + n) differs by RL; flipping bit 0 of the row when (row / RL) is odd
-  // makes the second kind differ by RL +- 1 and leaves the first kind alone,
-  // so both hit disjoint bank halves.  Needs RL even, which every W = 8
-  // configuration has.
+  // Shared-memory slot of (row, column).  A half-warp covers the rows of
+  // G = 16 / W adjacent phases t .. t + G - 1 (t a multiple of G; G = 1 for
+  // W >= 16, which is conflict-free as is).  Every stage's rows for those
+  // phases either are G consecutive rows starting at a multiple of G, or
+  // (the last stage, rows b*RL + n) are RL apart.  XOR-ing the low bits of
+  // the row with (row / RL) mod G leaves the first kind a permutation of
+  // the same G rows and spreads the second kind over all G residues, so
+  // both fill 16 distinct 8-byte bank pairs.  Needs RL a multiple of G.
   __device__ __forceinline__ int sidx(int row) const {
-    if constexpr (W == 8) {
-      static_assert(RL % 2 == 0, "W = 8 needs an even last radix");
-      return (row ^ ((row / RL) & 1)) * W + c;
+    if constexpr (W < 16) {
+      constexpr int G = 16 / W;
+      static_assert(RL % G == 0, "the last radix must be a multiple of 16 / W");
+      return (row ^ ((row / RL) & (G - 1))) * W + c;
     } else {
       return row * W + c;
     }

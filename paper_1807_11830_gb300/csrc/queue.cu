@@ -231,7 +231,7 @@ bool ensure_class_capacity(sense_queue* q, SizeClass& c, int frames) {
   }
   c.upd_cap = (int)(((size_t)c.ny * c.nx / 2 + (size_t)min_threads * 4 - 1) / ((size_t)min_threads * 4));
   bool ok = cudaMalloc(&c.ints, sizeof(int) * (4 * (size_t)cap + 1)) == cudaSuccess &&
-            cudaMalloc(&c.part_nrm, sizeof(double) * (size_t)cap * ((c.nx + 7) / 8)) == cudaSuccess &&
+            cudaMalloc(&c.part_nrm, sizeof(double) * (size_t)cap * ((c.nx + 3) / 4)) == cudaSuccess &&
             cudaMalloc(&c.part_upd, sizeof(double) * (size_t)cap * c.upd_cap) == cudaSuccess &&
             cudaMalloc(&c.table_d, sizeof(PFrame) * cap) == cudaSuccess &&
             cudaMalloc(&c.status_d, sizeof(int) * cap) == cudaSuccess &&

@@ -504,7 +504,7 @@ sense_status plan_allocate(sense_plan* pl) {
   pl->norm_variant = 0;
   pl->norm_tiles = (sh.nx + normal_variant_width(sh.ny, 0) - 1) / normal_variant_width(sh.ny, 0);
   pl->part_stride = pl->tiles > pl->upd_blocks ? pl->tiles : pl->upd_blocks;
-  const int max_tiles = (sh.nx + 7) / 8;  // narrowest tile of any variant
+  const int max_tiles = (sh.nx + 3) / 4;  // narrowest tile of any variant
   if (pl->part_stride < max_tiles) pl->part_stride = max_tiles;
   {
     int min_threads = 1 << 30;
