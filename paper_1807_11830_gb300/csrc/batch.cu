@@ -110,6 +110,8 @@ sense_status run_batch(sense_batch* b, const sense_batch_io* io, const std::vect
     for (int i : c.members) {
       sense_status rc = plan_cg_start(b->plans[i], io[i].y, io[i].S, io[i].lines,
                                       reinterpret_cast<float2*>(io[i].x_out), tol, st);
+      const void* maps = nullptr;  // refresh S^T (its buffer exists) for lane-major variants
+      if (rc == SENSE_OK) rc = plan_maps(b->plans[i], io[i].S, st, &maps);
       if (rc != SENSE_OK) return rc;
     }
     if (max_iter > 0) {
@@ -306,13 +308,15 @@ sense_status sense_batch_cg_solve(sense_batch* b, const sense_batch_io* io, int 
       size_t off = 0;
       for (int i : c.members) {
         sense_plan* p = b->plans[i];
-        sense_status trc = plan_prepare_tmap(p, io[i].S, st);
+        const bool transposed = plan_maps_transposed(p);
+        sense_status trc = transposed ? plan_maps_buffer(p) : plan_prepare_tmap(p, io[i].S, st);
         if (trc != SENSE_OK) {
           for (PFrame* t : g.tables) cudaFree(t);
           cudaSetDevice(prev);
           return trc;
         }
-        plan_frames(p, io[i].S, io[i].lines, reinterpret_cast<float2*>(io[i].x_out), 0, rel_tol, host.data() + off);
+        plan_frames(p, transposed ? p->maps_t : io[i].S, io[i].lines, reinterpret_cast<float2*>(io[i].x_out), 0,
+                    rel_tol, host.data() + off);
         off += p->sh.frames;
       }
       PFrame* dev = nullptr;

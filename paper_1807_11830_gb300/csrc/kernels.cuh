@@ -556,9 +556,250 @@ __device__ __forceinline__ float normal_tile_tma(const NormalTile& a, const ColS
   return part;
 }
 
+// ---------------------------------------------------------------------------
+// Lane-major tiles (WCol configurations): each column is transformed by the
+// lanes of one warp, so the coil loop has no block-wide barrier.
+//   maps: a transposed copy S^T [C][nx][N] (k_transpose_maps), so one
+//         column's maps are N contiguous elements; each warp brings its own
+//         columns for the next coil into a per-warp double buffer with a 1D
+//         bulk copy completed on a per-warp mbarrier.
+//   p, q: row-major images, staged once per tile through shared memory
+//         (coalesced global access, transposed to [column][row]).
+// ---------------------------------------------------------------------------
+template <class C, class St>
+struct WSmem {
+  float2* tw;   // stage twiddle tables (C::TWN)
+  float2* buf0;  // W * CP
+  float2* buf1;
+  double* red;   // 32
+  short* map;    // N
+  typename St::T* sbuf;  // [warps][2][32 / T * N]
+  uint64_t* bar;         // [warps][2]
+};
+
+template <class C, class St>
+__host__ __device__ constexpr size_t wcol_smem_bytes() {
+  constexpr int warps = C::THREADS / 32;
+  constexpr size_t per_slot = (size_t)(32 / C::T) * C::N * sizeof(typename St::T);
+  size_t b = sizeof(float2) * ((size_t)C::TWN + 2 * (size_t)C::W * C::CP) + 32 * sizeof(double) +
+             sizeof(short) * (size_t)C::N;
+  b = (b + 15) & ~(size_t)15;
+  b += (size_t)warps * 2 * per_slot;
+  b += (size_t)warps * 2 * sizeof(uint64_t);
+  return b;
+}
+
+template <class C, class St>
+__device__ __forceinline__ WSmem<C, St> wcol_smem(unsigned char* base) {
+  WSmem<C, St> s;
+  s.tw = reinterpret_cast<float2*>(base);
+  s.buf0 = s.tw + C::TWN;
+  s.buf1 = s.buf0 + C::W * C::CP;
+  s.red = reinterpret_cast<double*>(s.buf1 + C::W * C::CP);
+  s.map = reinterpret_cast<short*>(s.red + 32);
+  size_t off = sizeof(float2) * ((size_t)C::TWN + 2 * (size_t)C::W * C::CP) + 32 * sizeof(double) +
+               sizeof(short) * (size_t)C::N;
+  off = (off + 15) & ~(size_t)15;
+  s.sbuf = reinterpret_cast<typename St::T*>(base + off);
+  constexpr int warps = C::THREADS / 32;
+  off += (size_t)warps * 2 * (size_t)(32 / C::T) * C::N * sizeof(typename St::T);
+  s.bar = reinterpret_cast<uint64_t*>(base + off);
+  return s;
+}
+
+// Stage twiddle tables from the full table tw[m] = exp(-2 pi i m / N):
+// table s holds tw[r k Q_s] at (k - 1) P_s + r.
+template <class C, class Rad, int s>
+__device__ __forceinline__ void wcol_fill_stage(float2* dst, const float2* tw) {
+  if constexpr (s < Rad::S - 1) {
+    constexpr int R = Rad::radix(s), P = Rad::P(s), Q = Rad::Q(s);
+    for (int i = threadIdx.x; i < (R - 1) * P; i += C::THREADS) {
+      const int k = i / P + 1, r = i - (k - 1) * P;
+      dst[C::twoff(s) + i] = tw[r * k * Q];
+    }
+    wcol_fill_stage<C, Rad, s + 1>(dst, tw);
+  }
+}
+
+template <class C>
+struct WColRad;
+template <int T, int W, class Rad, class Lay>
+struct WColRad<WCol<T, W, Rad, Lay>> {
+  using type = Rad;
+};
+
+// Block start: stage tables and the per-warp barriers (thread 0 initialises
+// them; the caller's next __syncthreads publishes both).
+template <class C, class St>
+__device__ __forceinline__ void wcol_setup(const WSmem<C, St>& s, const float2* tw) {
+  wcol_fill_stage<C, typename WColRad<C>::type, 0>(s.tw, tw);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2 * (C::THREADS / 32); ++i) mbar_init(s.bar + i, 1);
+    mbar_fence_init();
+  }
+}
+
+// line map of a frame: map[row] = index in the frame's line list, or -1
+template <int N, int THREADS>
+__device__ __forceinline__ void build_linemap(short* map, const int* ln, int L, int* err) {
+  for (int i = threadIdx.x; i < N; i += THREADS) map[i] = -1;
+  __syncthreads();
+  for (int l = threadIdx.x; l < L; l += THREADS) {
+    const int v = __ldg(ln + l);
+    const bool good = v >= 0 && v < N && (l == 0 || __ldg(ln + l - 1) < v);
+    if (good)
+      map[v] = (short)l;
+    else
+      atomicOr(err, ERR_LINES);
+  }
+  __syncthreads();
+}
+
+// One tile: `fill` counts the map copies this block has issued before (the
+// same number in every thread); the tile issues a.coils more.  Returns this
+// thread's share of Re<p, q> (CG) as normal_tile does.
+template <class C, class St, bool CG>
+__device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSmem<C, St>& s, unsigned keep,
+                                                  unsigned fill, int* err) {
+  constexpr int N = C::N, W = C::W, T = C::T, CW = 32 / T, CP = C::CP;
+  using E = typename St::T;
+  const C col;
+  const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+  const int x0 = a.tile * W;
+  const int xw = x0 + warp * CW;  // first column of this warp
+  int ncw = a.nx - xw;
+  ncw = ncw < 0 ? 0 : (ncw > CW ? CW : ncw);
+  const bool xin = x0 + col.c < a.nx;
+  const E* ST = static_cast<const E*>(a.S);
+  E* sb0 = s.sbuf + (size_t)warp * 2 * CW * N;
+  uint64_t* bar = s.bar + 2 * warp;
+  const unsigned bytes = (unsigned)(ncw * N * (int)sizeof(E));
+
+  // lane 0: maps of coil `coil` for this warp's columns into slot i & 1
+  auto issue = [&](unsigned i, int coil) {
+    uint64_t* b = bar + (i & 1);
+    if (ncw > 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(b, bytes);
+      bulk_load(sb0 + (i & 1) * CW * N, ST + ((size_t)coil * a.nx + xw) * N, bytes, b);
+    } else {
+      mbar_arrive(b);  // keeps the barrier's phases in step with `fill`
+    }
+  };
+  if (lane == 0) issue(fill, 0);
+
+  // p (CG: p = r + beta p_prev, written back) staged as [column][row]
+  for (int i = threadIdx.x; i < N * W; i += C::THREADS) {
+    const int row = i / W, cc = i - row * W, xx = x0 + cc;
+    float2 v = make_float2(0.f, 0.f);
+    if (xx < a.nx) {
+      const size_t idx = (size_t)row * a.nx + xx;
+      if (CG) {
+        v = __ldcg(a.p_src + idx);
+        if (a.p_update) {
+          const float2 rv = __ldcg(a.r + idx);
+          v = make_float2(fmaf(a.beta, v.x, rv.x), fmaf(a.beta, v.y, rv.y));
+          __stcg(a.p_dst + idx, v);
+        }
+      } else {
+        v = __ldg(a.x + idx);
+      }
+    }
+    s.buf0[cc * CP + row] = v;
+  }
+  __syncthreads();
+  float2 p[C::J0][C::R0], q[C::J0][C::R0];
+#pragma unroll
+  for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+    for (int n = 0; n < C::R0; ++n) {
+      p[j][n] = col.ok0(j) ? s.buf0[col.c * CP + col.xrow(j, n)] : make_float2(0.f, 0.f);
+      q[j][n] = make_float2(0.f, 0.f);
+    }
+
+  float2* bufs[2] = {s.buf0, s.buf1};
+  const int cw = col.c - warp * CW;  // column within the warp
+#pragma unroll 1
+  for (int c = 0; c < a.coils; ++c) {
+    const unsigned i = fill + (unsigned)c;
+    __syncwarp();  // every lane is done with slot (i + 1) & 1 and with its p reads
+    if (lane == 0 && c + 1 < a.coils) issue(i + 1, c + 1);
+    if (!mbar_wait(bar + (i & 1), (i >> 1) & 1u)) atomicOr(err, ERR_TIMEOUT);
+    const E* sc = sb0 + (i & 1) * CW * N + cw * N;
+    float2 xr[C::J0][C::R0];
+    float2 kr[C::JL][C::RL];
+#pragma unroll
+    for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+      for (int n = 0; n < C::R0; ++n) {
+        const float2 sv = col.ok0(j) ? St::lds(sc, col.xrow(j, n)) : make_float2(0.f, 0.f);
+        xr[j][n] = cmul(sv, p[j][n]);
+      }
+    col.fwd(xr, kr, bufs, s.tw);
+#pragma unroll
+    for (int j = 0; j < C::JL; ++j)
+#pragma unroll
+      for (int m = 0; m < C::RL; ++m)
+        if (!((keep >> (j * C::RL + m)) & 1u)) kr[j][m] = make_float2(0.f, 0.f);
+    col.inv(kr, xr, bufs, s.tw);
+#pragma unroll
+    for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+      for (int n = 0; n < C::R0; ++n) {
+        const float2 sv = col.ok0(j) ? St::lds(sc, col.xrow(j, n)) : make_float2(0.f, 0.f);
+        q[j][n] = cfma_conj(q[j][n], sv, xr[j][n]);
+      }
+  }
+
+  // q staged as [column][row], then stored row-major
+  const float invN = 1.0f / (float)N;
+  float part = 0.f;
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+    for (int n = 0; n < C::R0; ++n) {
+      if (!col.ok0(j)) continue;
+      const float2 qv = cscale(q[j][n], invN);
+      s.buf0[col.c * CP + col.xrow(j, n)] = qv;
+      if (CG && xin) part = fmaf(p[j][n].x, qv.x, fmaf(p[j][n].y, qv.y, part));
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < N * W; i += C::THREADS) {
+    const int row = i / W, cc = i - row * W, xx = x0 + cc;
+    if (xx < a.nx) {
+      const size_t idx = (size_t)row * a.nx + xx;
+      if (CG)
+        __stcg(a.q + idx, s.buf0[cc * CP + row]);
+      else
+        a.out[idx] = s.buf0[cc * CP + row];
+    }
+  }
+  return part;
+}
+
+// S [C][N][nx] -> S^T [C][nx][N] (storage type kept), 32 x 32 tiles.
+template <class E>
+__global__ void __launch_bounds__(256) k_transpose_maps(const E* __restrict__ S, E* __restrict__ ST, int N, int nx) {
+  __shared__ E tile[32][33];
+  const int c = blockIdx.z;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  const E* src = S + (size_t)c * N * nx;
+  E* dst = ST + (size_t)c * N * nx;
+  for (int yy = threadIdx.y; yy < 32; yy += 8) {
+    const int y = y0 + yy, x = x0 + threadIdx.x;
+    if (y < N && x < nx) tile[yy][threadIdx.x] = src[(size_t)y * nx + x];
+  }
+  __syncthreads();
+  for (int xx = threadIdx.y; xx < 32; xx += 8) {
+    const int x = x0 + xx, y = y0 + threadIdx.x;
+    if (y < N && x < nx) dst[(size_t)x * N + y] = tile[threadIdx.x][xx];
+  }
+}
+
 // One bit per frequency row this thread holds: set if the row is sampled.
 template <class C>
-__device__ __forceinline__ unsigned sampled_bits(const ColSmem& s) {
+__device__ __forceinline__ unsigned sampled_bits(const short* map) {
   static_assert(C::JL * C::RL <= 32, "mask bits");
   const C col;
   unsigned keep = 0u;
@@ -566,8 +807,12 @@ __device__ __forceinline__ unsigned sampled_bits(const ColSmem& s) {
   for (int j = 0; j < C::JL; ++j)
 #pragma unroll
     for (int m = 0; m < C::RL; ++m)
-      if (col.okL(j) && s.map[col.krow(j, m)] >= 0) keep |= 1u << (j * C::RL + m);
+      if (col.okL(j) && map[col.krow(j, m)] >= 0) keep |= 1u << (j * C::RL + m);
   return keep;
+}
+template <class C>
+__device__ __forceinline__ unsigned sampled_bits(const ColSmem& s) {
+  return sampled_bits<C>(s.map);
 }
 
 template <class St>
@@ -586,15 +831,21 @@ struct NormalArgs {
   CgState cg;
 };
 
+// shared memory of k_normal for configuration C (either engine)
+template <class C, class St>
+__host__ __device__ constexpr size_t normal_smem_bytes() {
+  if constexpr (is_wcol<C>::value)
+    return wcol_smem_bytes<C, St>();
+  else
+    return col_smem_bytes_c<C>();
+}
+
 template <int N, int V, class St, bool CG, int TH = NormCfg<N, V>::C::THREADS, int MINB = NormCfg<N, V>::MINB>
 __global__ void __launch_bounds__(TH, MINB) k_normal(NormalArgs<St> a) {
   using C = typename NormCfg<N, V>::C;
   const int f = blockIdx.y;
   if (CG && a.cg.active[f] == 0) return;  // uniform per block
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const ColSmem s = col_smem_c<C>(smem_raw);
-  load_tw_and_linemap<N, C::THREADS>(s, a.tw, a.lines + (size_t)f * a.L, a.L, a.err);
-  const unsigned keep = sampled_bits<C>(s);
   const size_t img = (size_t)N * a.nx;
   NormalTile t;
   t.x = a.x + f * img;
@@ -609,9 +860,22 @@ __global__ void __launch_bounds__(TH, MINB) k_normal(NormalArgs<St> a) {
   t.tile = blockIdx.x;
   t.p_update = a.p_update;
   t.beta = (CG && a.p_update) ? (float)__ldg(a.cg.beta + f) : 0.f;
-  const float part = normal_tile<C, St, CG>(t, s, keep);
+  float part;
+  double* red;
+  if constexpr (is_wcol<C>::value) {  // a.S holds the transposed maps
+    const WSmem<C, St> s = wcol_smem<C, St>(smem_raw);
+    wcol_setup<C, St>(s, a.tw);
+    build_linemap<N, C::THREADS>(s.map, a.lines + (size_t)f * a.L, a.L, a.err);
+    part = normal_tile_warp<C, St, CG>(t, s, sampled_bits<C>(s.map), 0u, a.err);
+    red = s.red;
+  } else {
+    const ColSmem s = col_smem_c<C>(smem_raw);
+    load_tw_and_linemap<N, C::THREADS>(s, a.tw, a.lines + (size_t)f * a.L, a.L, a.err);
+    part = normal_tile<C, St, CG>(t, s, sampled_bits<C>(s));
+    red = s.red;
+  }
   if (CG) {
-    const double tot = block_sum<C::THREADS>((double)part, s.red);
+    const double tot = block_sum<C::THREADS>((double)part, red);
     const CgState& g = a.cg;
     double* slot = g.part + (size_t)f * g.part_stride + blockIdx.x;
     if (publish_and_arrive(tot, slot, g.counter + f, (unsigned)a.tiles)) {

@@ -25,6 +25,10 @@ cudaError_t launch_normal(int n, int variant, bool cg, const NormalArgs<St>& a, 
 // tile width / threads per block of a normal-operator variant, 0 if it does not exist
 int normal_variant_width(int n, int variant);
 int normal_variant_threads(int n, int variant);
+// 1 if the variant reads the transposed maps S^T [C][nx][ny] (lane-major tiles)
+int normal_variant_transposed(int n, int variant);
+// S [C][ny][nx] -> S^T [C][nx][ny] in storage type (bf16 pairs or complex64)
+cudaError_t launch_transpose_maps(bool bf16, const void* S, void* ST, int ny, int nx, int coils, cudaStream_t s);
 // persistent CG kernel (all iterations of all frames of `a` in one launch,
 // `sms` x resident blocks per SM)
 template <class St>

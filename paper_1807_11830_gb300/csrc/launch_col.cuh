@@ -33,7 +33,8 @@ cudaError_t normal_nv(const NormalArgs<St>& a, int frames, cudaStream_t s) {
   } else {
     using C = typename NormCfg<N, V>::C;
     static unsigned long long done = 0;
-    constexpr size_t sm = col_smem_bytes_c<C>();
+    constexpr size_t sm = normal_smem_bytes<C, St>();
+    static_assert(sm <= 227 * 1024, "normal kernel shared memory");
     cudaError_t e = ensure_smem(k_normal<N, V, St, CG>, sm, &done);
     const int tiles = (a.nx + C::W - 1) / C::W;
     if (e != cudaSuccess || frames == 0) return e;  // no frames: attribute set-up only
@@ -99,6 +100,15 @@ constexpr int norm_variant_width(int v) {
        : v == 1 ? (NormCfg<N, 1>::exists ? NormCfg<N, 1>::C::W : 0)
        : v == 2 ? (NormCfg<N, 2>::exists ? NormCfg<N, 2>::C::W : 0)
        : v == 3 ? (NormCfg<N, 3>::exists ? NormCfg<N, 3>::C::W : 0) : 0;
+}
+
+// 1 if the variant's normal-operator tiles read the transposed maps S^T
+template <int N>
+constexpr int norm_variant_transposed(int v) {
+  return v == 0 ? (int)is_wcol<typename NormCfg<N, 0>::C>::value
+       : v == 1 ? (NormCfg<N, 1>::exists ? (int)is_wcol<typename NormCfg<N, 1>::C>::value : 0)
+       : v == 2 ? (NormCfg<N, 2>::exists ? (int)is_wcol<typename NormCfg<N, 2>::C>::value : 0)
+       : v == 3 ? (NormCfg<N, 3>::exists ? (int)is_wcol<typename NormCfg<N, 3>::C>::value : 0) : 0;
 }
 
 template <int N, int DIR, class InSt, class OutSt>

@@ -82,33 +82,73 @@ __device__ __forceinline__ bool wait_at_least(const int* flag, int target, long 
   return true;
 }
 
-// shared memory of the persistent kernel: two map tiles, then the column
-// kernels' layout, then two mbarriers
+// Shared memory of the persistent kernel.  Block-tile configurations: two
+// TMA map tiles, the column kernels' layout, two mbarriers.  Lane-major
+// configurations: the layout of normal_tile_warp.
 template <class C, class St>
 __host__ __device__ constexpr size_t persistent_smem_bytes() {
-  return 2 * (size_t)C::N * C::W * sizeof(typename St::T) + ((col_smem_bytes_c<C>() + 7) & ~(size_t)7) + 16;
+  if constexpr (is_wcol<C>::value)
+    return wcol_smem_bytes<C, St>();
+  else
+    return 2 * (size_t)C::N * C::W * sizeof(typename St::T) + ((col_smem_bytes_c<C>() + 7) & ~(size_t)7) + 16;
 }
+
+// The normal-product piece of the persistent kernel for each engine: set-up
+// at block start, the line map of a frame, and one tile.
+template <class C, class St, bool WARP = is_wcol<C>::value>
+struct PTile;
+
+template <class C, class St>
+struct PTile<C, St, false> {  // block tiles, maps staged by TMA as [N][W] tiles
+  SStage<C, St> sg;
+  ColSmem s;
+  __device__ __forceinline__ PTile(unsigned char* smem, const float2* tw) {
+    constexpr size_t SB = (size_t)C::N * C::W * sizeof(typename St::T);
+    sg.buf[0] = reinterpret_cast<typename St::T*>(smem);
+    sg.buf[1] = reinterpret_cast<typename St::T*>(smem + SB);
+    s = col_smem_c<C>(smem + 2 * SB);
+    sg.bar = reinterpret_cast<uint64_t*>(smem + 2 * SB + ((col_smem_bytes_c<C>() + 7) & ~(size_t)7));
+    for (int i = threadIdx.x; i < C::N; i += C::THREADS) s.tw[i] = tw[i];
+    if (threadIdx.x == 0) {
+      mbar_init(sg.bar, 1);
+      mbar_init(sg.bar + 1, 1);
+      mbar_fence_init();
+    }
+  }
+  __device__ __forceinline__ double* red() const { return s.red; }
+  __device__ __forceinline__ short* map() const { return s.map; }
+  // called before the line map is built, so the first coil's copy overlaps it
+  __device__ __forceinline__ void prefetch(const PFrame& fr, int piece, unsigned nfill) {
+    sg.tmap = fr.tmap;
+    if (threadIdx.x == 0) sg.issue(nfill, piece, 0);
+  }
+  __device__ __forceinline__ float run(const NormalTile& nt, unsigned keep, unsigned nfill, int* err) const {
+    return normal_tile_tma<C, St>(nt, s, keep, sg, nfill, err);
+  }
+};
+
+template <class C, class St>
+struct PTile<C, St, true> {  // lane-major tiles, maps by per-warp bulk copies of S^T
+  WSmem<C, St> s;
+  __device__ __forceinline__ PTile(unsigned char* smem, const float2* tw) : s(wcol_smem<C, St>(smem)) {
+    wcol_setup<C, St>(s, tw);
+  }
+  __device__ __forceinline__ double* red() const { return s.red; }
+  __device__ __forceinline__ short* map() const { return s.map; }
+  __device__ __forceinline__ void prefetch(const PFrame&, int, unsigned) {}
+  __device__ __forceinline__ float run(const NormalTile& nt, unsigned keep, unsigned nfill, int* err) const {
+    return normal_tile_warp<C, St, true>(nt, s, keep, nfill, err);
+  }
+};
 
 template <int N, int V, class St, int TH = NormCfg<N, V>::C::THREADS, int MINB = NormCfg<N, V>::MINB>
 __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
   using C = typename NormCfg<N, V>::C;
-  using E = typename St::T;
   constexpr int T = C::THREADS;
-  constexpr size_t SB = (size_t)N * C::W * sizeof(E);
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  SStage<C, St> sg;
-  sg.buf[0] = reinterpret_cast<E*>(smem_raw);
-  sg.buf[1] = reinterpret_cast<E*>(smem_raw + SB);
-  const ColSmem s = col_smem_c<C>(smem_raw + 2 * SB);
-  sg.bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * SB + ((col_smem_bytes_c<C>() + 7) & ~(size_t)7));
+  PTile<C, St> tile(smem_raw, a.tw);
   __shared__ int s_ticket, s_ok, s_active;
-  for (int i = threadIdx.x; i < N; i += T) s.tw[i] = a.tw[i];
-  if (threadIdx.x == 0) {
-    mbar_init(sg.bar, 1);
-    mbar_init(sg.bar + 1, 1);
-    mbar_fence_init();
-  }
-  unsigned nfill = 0;  // map tiles requested so far by this block (same in every thread)
+  unsigned nfill = 0;  // map copies requested so far by this block (same in every thread)
 
   const int per_iter = a.nframes * (a.tiles + a.chunks);
   const long total = (long)per_iter * a.iters;
@@ -147,21 +187,9 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
 
     if (normal) {
       if (work) {
-        sg.tmap = fr.tmap;
-        if (threadIdx.x == 0) sg.issue(nfill, piece, 0);  // first coil's maps, overlapping the set-up below
-        // line map of this frame
-        for (int i = threadIdx.x; i < N; i += T) s.map[i] = -1;
-        __syncthreads();
-        for (int l = threadIdx.x; l < fr.L; l += T) {
-          const int v = __ldg(fr.lines + l);
-          const bool good = v >= 0 && v < N && (l == 0 || __ldg(fr.lines + l - 1) < v);
-          if (good)
-            s.map[v] = (short)l;
-          else
-            atomicOr(a.err, ERR_LINES);
-        }
-        __syncthreads();
-        const unsigned keep = sampled_bits<C>(s);
+        tile.prefetch(fr, piece, nfill);  // first coil's maps, overlapping the set-up below
+        build_linemap<N, T>(tile.map(), fr.lines, fr.L, a.err);
+        const unsigned keep = sampled_bits<C>(tile.map());
         const int kg = k + fr.k0;  // global iteration index of this frame
         NormalTile nt;
         nt.p_src = fr.p[kg > 0 ? ((kg - 1) & 1) : 0];
@@ -174,9 +202,9 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
         nt.tile = piece;
         nt.p_update = kg > 0 ? 1 : 0;
         nt.beta = kg > 0 ? (float)__ldcg(fr.beta) : 0.f;
-        const float part = normal_tile_tma<C, St>(nt, s, keep, sg, nfill, a.err);
+        const float part = tile.run(nt, keep, nfill, a.err);
         nfill += (unsigned)fr.coils;
-        const double tot = block_sum<T>((double)part, s.red);
+        const double tot = block_sum<T>((double)part, tile.red());
         if (threadIdx.x == 0) __stcg(g.part_nrm + (size_t)f * a.tiles + piece, tot);
       }
       __threadfence();
@@ -235,7 +263,7 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
             acc = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, acc))));
           }
         }
-        const double tot = block_sum<T>((double)acc, s.red);
+        const double tot = block_sum<T>((double)acc, tile.red());
         if (threadIdx.x == 0) __stcg(g.part_upd + (size_t)f * a.chunks + piece, tot);
       }
       __threadfence();

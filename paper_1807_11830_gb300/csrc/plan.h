@@ -46,6 +46,7 @@ struct sense_plan {
   float2* r = nullptr;
   float2* pp[2] = {nullptr, nullptr};  // search directions, ping-pong between iterations
   float2* q = nullptr;
+  void* maps_t = nullptr;  // S^T [C][nx][ny] for variants with lane-major tiles (allocated on first use)
 
   double* dbl = nullptr;  // rho, rho0, alpha, beta, resid  ([5][F])
   int* ints = nullptr;    // iters, outcome, active ([3][F]), live, err
@@ -115,6 +116,14 @@ std::vector<float2> plan_twiddles(int n);
 // Encode (when S or the kernel variant changed) the TMA descriptor of S and
 // queue its upload on `st`.  Must not run during stream capture.
 sense_status plan_prepare_tmap(sense_plan* pl, const void* S, cudaStream_t st);
+
+// Maps read by the normal-operator tiles of the plan's current variant:
+// plan_maps_buffer allocates S^T on first use if the variant reads it (not
+// during stream capture); plan_maps then returns S itself, or S^T refreshed
+// from S by a transpose queued on `st` (capturable once the buffer exists).
+sense_status plan_maps_buffer(sense_plan* pl);
+sense_status plan_maps(sense_plan* pl, const void* S, cudaStream_t st, const void** out);
+bool plan_maps_transposed(const sense_plan* pl);
 
 // Per-frame outputs of a finished CG solve of a plan (iterations, residual,
 // outcome; NULL outputs are skipped).

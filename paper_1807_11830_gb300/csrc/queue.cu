@@ -62,6 +62,7 @@ struct Request {
   sense_plan* plan = nullptr;
   void* y_d = nullptr;
   void* s_d = nullptr;
+  const void* maps = nullptr;  // what its normal-operator tiles read: s_d or the plan's S^T
   int* lines_d = nullptr;
   float2* x_d = nullptr;
   int* out_i_d = nullptr;  // iters [F], outcome [F]
@@ -189,13 +190,14 @@ void free_device(Request* r, cudaStream_t st) {
 }
 
 // Device bytes a request holds while live: its inputs, output and the plan's
-// workspace (CG vectors, the k-space intermediate, scalars), with slack.
+// workspace (CG vectors, the k-space intermediate, scalars, the transposed
+// maps that lane-major kernel variants read), with slack.
 size_t request_need(const sense_shape& sh) {
   const size_t F = sh.frames, img = (size_t)sh.ny * sh.nx;
   const size_t e = elem_bytes(sh.storage);
   const size_t inputs = F * sh.coils * sh.lines * sh.nx * e + (size_t)sh.coils * img * e + F * sh.lines * 4;
   const size_t outputs = F * img * 8 + F * 16;
-  const size_t plan = F * sh.coils * sh.lines * sh.nx * 8 + 4 * F * img * 8;
+  const size_t plan = F * sh.coils * sh.lines * sh.nx * 8 + 4 * F * img * 8 + (size_t)sh.coils * img * e;
   return inputs + outputs + plan + (size_t)(1 << 20);
 }
 
@@ -312,7 +314,11 @@ bool admit_device(sense_queue* q, Request* r, std::string* err) {
     *err = sense_last_error();
     return false;
   }
-  if (plan_prepare_tmap(r->plan, r->s_d, st) != SENSE_OK) {
+  if (!plan_maps_transposed(r->plan) && plan_prepare_tmap(r->plan, r->s_d, st) != SENSE_OK) {
+    *err = sense_last_error();
+    return false;
+  }
+  if (plan_maps(r->plan, r->s_d, st, &r->maps) != SENSE_OK) {
     *err = sense_last_error();
     return false;
   }
@@ -359,7 +365,7 @@ bool tick_device(sense_queue* q) {
     int off = 0;
     for (Request* r : kv.second) {
       r->status_off = off;
-      plan_frames(r->plan, r->s_d, r->lines_d, r->x_d, r->ticks, r->tol, c.table_h + off);
+      plan_frames(r->plan, r->maps, r->lines_d, r->x_d, r->ticks, r->tol, c.table_h + off);
       for (int f = 0; f < r->sh.frames; ++f) c.table_h[off + f].kmax = r->max_iter;
       off += r->sh.frames;
     }

@@ -130,6 +130,46 @@ sense_status dalloc(sense_plan* pl, T** out, size_t count) {
   return SENSE_OK;
 }
 
+}  // namespace
+
+namespace sense {
+
+bool plan_maps_transposed(const sense_plan* pl) {
+  return normal_variant_transposed(pl->sh.ny, pl->norm_variant) != 0;
+}
+
+sense_status plan_maps_buffer(sense_plan* pl) {
+  if (!plan_maps_transposed(pl) || pl->maps_t) return SENSE_OK;
+  const size_t count = (size_t)pl->sh.coils * pl->img;
+  sense_status rc;
+  if (pl->sh.storage == SENSE_STORE_BF16) {
+    __nv_bfloat162* ptr = nullptr;
+    rc = dalloc(pl, &ptr, count);
+    pl->maps_t = ptr;
+  } else {
+    float2* ptr = nullptr;
+    rc = dalloc(pl, &ptr, count);
+    pl->maps_t = ptr;
+  }
+  return rc;
+}
+
+sense_status plan_maps(sense_plan* pl, const void* S, cudaStream_t st, const void** out) {
+  *out = S;
+  if (!plan_maps_transposed(pl)) return SENSE_OK;
+  sense_status rc = plan_maps_buffer(pl);
+  if (rc != SENSE_OK) return rc;
+  const sense_shape& sh = pl->sh;
+  const cudaError_t e = launch_transpose_maps(sh.storage == SENSE_STORE_BF16, S, pl->maps_t, sh.ny, sh.nx, sh.coils, st);
+  if (e != cudaSuccess) return fail(SENSE_ECUDA, std::string("map transpose: ") + cudaGetErrorString(e));
+  *out = pl->maps_t;
+  return SENSE_OK;
+}
+
+}  // namespace sense
+
+namespace {
+
 void release(sense_plan* pl) {
   collect_spans(pl);
   for (auto& kv : pl->graphs) cudaGraphExecDestroy(kv.second);
@@ -255,10 +295,13 @@ template <class St>
 sense_status run_normal(sense_plan* pl, const float2* x, const void* S, const int* lines, float2* out,
                         cudaStream_t st) {
   const sense_shape& sh = pl->sh;
+  const void* maps = nullptr;
+  sense_status rc = plan_maps(pl, S, st, &maps);
+  if (rc != SENSE_OK) return rc;
   NormalArgs<St> a{};
   a.x = x;
   a.out = out;
-  a.S = static_cast<const typename St::T*>(S);
+  a.S = static_cast<const typename St::T*>(maps);
   a.lines = lines;
   a.tw = pl->tw_y;
   a.nx = sh.nx;
@@ -414,7 +457,7 @@ sense_status run_cg_persistent(sense_plan* pl, const void* S, const int* lines, 
                                cudaStream_t st) {
   const sense_shape& sh = pl->sh;
   const int F = sh.frames;
-  {
+  if (!plan_maps_transposed(pl)) {  // S here is what the tiles read: S, or S^T
     sense_status rc = plan_prepare_tmap(pl, S, st);
     if (rc != SENSE_OK) return rc;
   }
@@ -459,8 +502,11 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
   SENSE_CUDA_TRY(cudaMemsetAsync(pl->cg(tol).live, 0, sizeof(int), st));
   sense_status rc = run_adjoint<St>(pl, 1, y, S, lines, x, nullptr, tol, st);
   if (rc != SENSE_OK) return rc;
+  const void* maps = nullptr;  // what the normal-operator tiles read
+  rc = plan_maps(pl, S, st, &maps);
+  if (rc != SENSE_OK) return rc;
   if (pl->cg_mode == 1) {
-    if (max_iter > 0) rc = run_cg_persistent<St>(pl, S, lines, x, max_iter, tol, st);
+    if (max_iter > 0) rc = run_cg_persistent<St>(pl, maps, lines, x, max_iter, tol, st);
     if (rc != SENSE_OK) return rc;
     k_cg_finish<<<(sh.frames + 127) / 128, 128, 0, st>>>(pl->cg(tol), sh.frames, iters_out, resid_out, outcome_out);
     return launch_status(cudaGetLastError(), "CG finish");
@@ -471,13 +517,13 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
     if (rc != SENSE_OK) return rc;
   }
   if (tol <= 0.0) {
-    if (max_iter > 0) rc = cg_chunk_graph<St>(pl, S, lines, x, 0, max_iter, tol, st);
+    if (max_iter > 0) rc = cg_chunk_graph<St>(pl, maps, lines, x, 0, max_iter, tol, st);
     if (rc != SENSE_OK) return rc;
   } else {
     int done = 0;
     while (done < max_iter) {
       const int count = (max_iter - done) < kPollEvery ? (max_iter - done) : kPollEvery;
-      rc = cg_chunk_graph<St>(pl, S, lines, x, done, count, tol, st);
+      rc = cg_chunk_graph<St>(pl, maps, lines, x, done, count, tol, st);
       if (rc != SENSE_OK) return rc;
       done += count;
       if (done >= max_iter) break;

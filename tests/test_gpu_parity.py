@@ -218,7 +218,7 @@ def test_paper_workload_full_size():
 
 
 VARIANT_SHAPES = [(128, 128, 5, 40, 2), (192, 192, 6, 48, 1), (256, 256, 12, 64, 2), (320, 320, 6, 107, 1),
-                  (384, 384, 4, 96, 1), (256, 96, 3, 64, 1)]
+                  (384, 384, 4, 96, 1), (256, 96, 3, 64, 1), (256, 20, 2, 64, 2)]
 
 
 @pytest.mark.parametrize("shape", VARIANT_SHAPES, ids=lambda s: "%dx%d_c%d" % s[:3])
@@ -251,8 +251,11 @@ def test_cg_every_variant_and_autotune():
             sense.sense_plan_set_variant(plan, v)
         except sense.SenseError:
             continue
-        xg, ig, _, _ = gpu_cg(y, p.S, p.lines, 8, plan=plan)
-        assert rel(xg, xo) <= CG_TOL, v
+        for mode in (sense.CG_MODE_GRAPH, sense.CG_MODE_PERSISTENT):
+            sense.sense_plan_set_cg_mode(plan, mode)
+            xg, ig, _, _ = gpu_cg(y, p.S, p.lines, 8, plan=plan)
+            assert rel(xg, xo) <= CG_TOL, (v, mode)
+            np.testing.assert_array_equal(ig, io)
     # persistent mode (the default) times short CG solves on scratch buffers
     chosen, times = sense.sense_plan_autotune(plan, c64(p.S), i32(p.lines))
     assert chosen in times and len(times) >= 2
@@ -268,6 +271,28 @@ def test_cg_every_variant_and_autotune():
     print("autotune graph 256^2 C12 F3:", chosen_g, times_g)
     xg, ig, _, _ = gpu_cg(y, p.S, p.lines, 8, plan=plan)
     assert rel(xg, xo) <= CG_TOL
+
+
+@pytest.mark.parametrize("shape", [(256, 20, 3, 64, 2), (128, 12, 4, 40, 3), (192, 20, 5, 48, 2)],
+                         ids=lambda s: "%dx%d" % s[:2])
+def test_cg_every_variant_ragged_tiles(shape):
+    """Image widths that leave the last column tile (and, for lane-major
+    variants, whole warps) partly empty: every variant, both CG modes."""
+    ny, nx, C, L, F = shape
+    x, S, lines, _ = _problem(shape, 7000 + sum(shape))
+    S32 = _as32(S)
+    y = oracle.forward(_as32(x), S32, lines)
+    xo, io, _, _ = oracle.cg(_as32(y), S32, lines, 6)
+    plan = make_plan(S, lines)
+    for v in range(sense.NORM_VARIANTS):
+        try:
+            sense.sense_plan_set_variant(plan, v)
+        except sense.SenseError:
+            continue
+        for mode in (sense.CG_MODE_GRAPH, sense.CG_MODE_PERSISTENT):
+            sense.sense_plan_set_cg_mode(plan, mode)
+            xg, ig, _, _ = gpu_cg(y, S, lines, 6, plan=plan)
+            assert rel(xg, xo) <= CG_TOL, (v, mode)
 
 
 @pytest.mark.parametrize("which", ["slice64", "cine256", "slices320", "mix192"])
