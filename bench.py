@@ -39,11 +39,17 @@ WORKLOAD = "cine 256x256, 20 frames, 12 coils, R=4 (64 lines, 16 centre), 30 CG-
 METRIC = "E^H·E applications/s"
 UNIT = "applications/s"
 FLUSH_BYTES = 512 << 20
+# ncu DRAM traffic of k_cg_persistent on this workload, bytes per CG iteration,
+# keyed by (kernel variant, CG mode): the lane-major 256-point variant in the
+# persistent kernel (101.6 MB read + 553.0 MB written over 30 iterations)
+CINE_TRAFFIC_PER_ITER = {(1, "persistent"): (101.593856e6 + 552.989184e6) / 30}
 PAPER_WORKLOAD = ("paper reconstruction: 16 frames x 160x160, 8 coils, fully sampled; "
                   "2D inverse FFT + root-sum-of-squares (Sec. V)")
 PAPER_METRIC, PAPER_UNIT = "reconstructions/s", "reconstructions/s"
 # OpenCLIPER's own time for this workload on a GTX 970 (Table II: clFFT 1.361 ms + RSS 0.252 ms): context
 PAPER_GTX970_MS = 1.361 + 0.252
+# ncu DRAM traffic per launch of the paper workload's kernels (read + write)
+PAPER_TRAFFIC = {"rows_inv": 26.22464e6 + 24.064e6, "adj_col": 26.251008e6 + 0.0}
 
 
 def parse_args():
@@ -385,8 +391,9 @@ def run_ours(args):
     d2h = x.numel() * 8
 
     # ---- kernel roofline: the same step with the plan's event timers on ----
+    timed_steps = 5
     sense.sense_plan_set_timing(plan, True)
-    for _ in range(5):
+    for _ in range(timed_steps):
         flush.fill_(1)
         step()
     torch.cuda.synchronize(dev)
@@ -422,9 +429,13 @@ def run_ours(args):
         bytes_ = 8 * img * (COILS + 4 * FRAMES)
         alu_peak_tflops = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
         achieved_tflops = flops / dur_s / 1e12
+        # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu
+        # capture of this launch configuration, per CG iteration; null for any
+        # other configuration
+        traffic = CINE_TRAFFIC_PER_ITER.get((variant, cg_mode))
         roofline = {
             "kernel": kernel_name, "bound": "alu", "achieved": achieved_tflops, "peak": alu_peak_tflops,
-            "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak_tflops, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak_tflops, "traffic": traffic,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max)" % (sm_max_mhz, peak_src),
             "algorithmic_gflop_per_launch": flops / 1e9, "algorithmic_mb_per_launch": bytes_ / 1e6,
             "hbm_achieved_gbs": bytes_ / dur_s / 1e9, "hbm_peak_gbs": hbm_gbs,
@@ -438,7 +449,8 @@ def run_ours(args):
             cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "%d of %d frames x %d CG iterations (full 256x256, 12 coils, R=4), %.1f s"
                              % (frames, FRAMES, args.cpu_sample_iters, wall)}
-        launches_per_step = (2 + 1 + 1) if cg_mode == "persistent" else (2 + 2 * ITERS + 1)
+        # our kernels per step, counted by the plan's launch timers in the timing pass
+        launches_per_step = sum(v["launches"] for v in phase.values()) / timed_steps
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -446,7 +458,7 @@ def run_ours(args):
             "config": base_config(world),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_ms / args.steps},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": int(round(launches_per_step * args.steps)),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clocks.summary(t_wall0, t_wall1),
@@ -824,10 +836,12 @@ def run_paper(args):
         step()
     torch.cuda.synchronize(dev)
     phase = {}
+    launches_per_step = 0.0
     for name in sense.PHASES:
         ms, cnt = sense.sense_plan_phase_time(plan, name)
         if cnt:
             phase[name] = ms / cnt
+            launches_per_step += cnt / 5.0
     sense.sense_plan_set_timing(plan, False)
     sense.sense_plan_check(plan)
 
@@ -844,7 +858,7 @@ def run_paper(args):
             "kernel": {"rows_inv": "k_rows<160,+1> (inverse x-transforms of every k-space row)",
                        "adj_col": "k_adj_col<160,c64,rss> (inverse y-transforms, |.|^2 summed over coils, sqrt)"}[dom],
             "bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
-            "traffic": None, "peak_source": "%s hbm_gbs (copy)" % peak_src,
+            "traffic": PAPER_TRAFFIC.get(dom), "peak_source": "%s hbm_gbs (copy)" % peak_src,
             "algorithmic_mb_per_launch": kernel_bytes[dom] / 1e6, "duration_us": dur_s * 1e6,
             "whole_op_minimum_mb": (cimg + 4.0 * F * n * n) / 1e6,
         }
@@ -869,7 +883,7 @@ def run_paper(args):
             "eq1_combine": {"value": world * args.steps / (eq1_total / 1e3), "unit": PAPER_UNIT,
                             "ms_per_step": eq1_total / args.steps,
                             "kind": "sense_adjoint with every line sampled: sum_c conj(S_c) F^-1(Y_c)"},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": int(round(launches_per_step * args.steps)),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clocks.summary(t_wall0, t_wall1),

@@ -325,7 +325,9 @@ typedef enum {
   SENSE_PHASE_CG_NORMAL = 5,/* E^H E inside CG, with the p update and Re<p,q> */
   SENSE_PHASE_CG_UPDATE = 6,/* CG x/r update with <r,r> */
   SENSE_PHASE_CG_PERSISTENT = 7, /* all CG iterations in one persistent launch */
-  SENSE_PHASE_COUNT = 8
+  SENSE_PHASE_MAPS_TRANSPOSE = 8, /* S -> S^T for kernel variants with lane-major tiles */
+  SENSE_PHASE_CG_FINISH = 9,      /* per-frame CG outputs (iterations, residual, outcome) */
+  SENSE_PHASE_COUNT = 10
 } sense_phase;
 
 /* Turn the plan's kernel timers on (1) or off (0); either way the totals

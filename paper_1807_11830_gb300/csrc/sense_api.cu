@@ -160,6 +160,7 @@ sense_status plan_maps(sense_plan* pl, const void* S, cudaStream_t st, const voi
   sense_status rc = plan_maps_buffer(pl);
   if (rc != SENSE_OK) return rc;
   const sense_shape& sh = pl->sh;
+  PhaseScope ps(pl, SENSE_PHASE_MAPS_TRANSPOSE, st);
   const cudaError_t e = launch_transpose_maps(sh.storage == SENSE_STORE_BF16, S, pl->maps_t, sh.ny, sh.nx, sh.coils, st);
   if (e != cudaSuccess) return fail(SENSE_ECUDA, std::string("map transpose: ") + cudaGetErrorString(e));
   *out = pl->maps_t;
@@ -508,6 +509,7 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
   if (pl->cg_mode == 1) {
     if (max_iter > 0) rc = run_cg_persistent<St>(pl, maps, lines, x, max_iter, tol, st);
     if (rc != SENSE_OK) return rc;
+    PhaseScope ps(pl, SENSE_PHASE_CG_FINISH, st);
     k_cg_finish<<<(sh.frames + 127) / 128, 128, 0, st>>>(pl->cg(tol), sh.frames, iters_out, resid_out, outcome_out);
     return launch_status(cudaGetLastError(), "CG finish");
   }
@@ -532,6 +534,7 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
       if (*pl->live_host <= 0) break;
     }
   }
+  PhaseScope ps(pl, SENSE_PHASE_CG_FINISH, st);
   k_cg_finish<<<(sh.frames + 127) / 128, 128, 0, st>>>(pl->cg(tol), sh.frames, iters_out, resid_out, outcome_out);
   return launch_status(cudaGetLastError(), "CG finish");
 }

@@ -43,7 +43,8 @@ EXPORTED = (
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = 0, 1, 2, 3, 4
 NORM_VARIANTS = 4
 
-PHASES = ("rows_fwd", "rows_inv", "fwd_col", "adj_col", "normal", "cg_normal", "cg_update", "cg_persistent")
+PHASES = ("rows_fwd", "rows_inv", "fwd_col", "adj_col", "normal", "cg_normal", "cg_update", "cg_persistent",
+          "maps_transpose", "cg_finish")
 CG_MODE_GRAPH, CG_MODE_PERSISTENT, CG_MODE_DIRECT = 0, 1, 2
 
 
