@@ -44,6 +44,7 @@ struct Radices {
 
 template <int T_, int W_, class Rad>
 struct Col {
+  using Radix = Rad;
   static constexpr int N = Rad::N;
   static constexpr int S = Rad::S;
   static constexpr int T = T_, W = W_;
@@ -87,11 +88,11 @@ struct Col {
   // (the last stage, rows b*RL + n) are RL apart.  XOR-ing the low bits of
   // the row with (row / RL) mod G leaves the first kind a permutation of
   // the same G rows and spreads the second kind over all G residues, so
-  // both fill 16 distinct 8-byte bank pairs.  Needs RL a multiple of G.
+  // both fill 16 distinct 8-byte bank pairs.  Needs RL a multiple of G;
+  // otherwise rows are stored unswizzled (correct, with some conflicts).
   __device__ __forceinline__ int sidx(int row) const {
-    if constexpr (W < 16) {
-      constexpr int G = 16 / W;
-      static_assert(RL % G == 0, "the last radix must be a multiple of 16 / W");
+    constexpr int G = W < 16 ? 16 / W : 1;
+    if constexpr (W < 16 && RL % G == 0) {
       return (row ^ ((row / RL) & (G - 1))) * W + c;
     } else {
       return row * W + c;

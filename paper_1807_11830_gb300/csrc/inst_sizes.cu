@@ -16,7 +16,7 @@ bool size_supported(int n) {
 
 int col_width(int n) {
   switch (n) {
-#define SENSE_CASE(N) case N: return Cfg<N>::C::W;
+#define SENSE_CASE(N) case N: return ColPass<N>::C::W;
     SENSE_FOR_EACH_SIZE(SENSE_CASE)
 #undef SENSE_CASE
     default:
@@ -26,7 +26,7 @@ int col_width(int n) {
 
 int col_threads(int n) {
   switch (n) {
-#define SENSE_CASE(N) case N: return Cfg<N>::C::THREADS;
+#define SENSE_CASE(N) case N: return ColPass<N>::C::THREADS;
     SENSE_FOR_EACH_SIZE(SENSE_CASE)
 #undef SENSE_CASE
     default:
@@ -34,7 +34,15 @@ int col_threads(int n) {
   }
 }
 
-int row_width(int n) { return col_width(n); }
+int row_width(int n) {
+  switch (n) {
+#define SENSE_CASE(N) case N: return Cfg<N>::C::W;
+    SENSE_FOR_EACH_SIZE(SENSE_CASE)
+#undef SENSE_CASE
+    default:
+      return 0;
+  }
+}
 
 int normal_variant_threads(int n, int variant) {
   switch (n) {

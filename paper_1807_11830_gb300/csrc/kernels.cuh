@@ -25,9 +25,22 @@ __host__ __device__ constexpr size_t col_smem_bytes_c() {
          + sizeof(short) * (size_t)N;          // line map / sampled flags
 }
 
+// Column passes (E's first pass, E^H's second pass): the length's transform
+// configuration on 8-column tiles where that still fills whole warps, so a
+// frame spans twice as many blocks of half the threads and several blocks
+// share an SM (these passes loop over coils inside a block).
+template <int N>
+struct ColPass {
+  using Base = typename Cfg<N>::C;
+  // 384 keeps 16 columns: at 8 two 384-thread blocks would cap registers at 85
+  static constexpr int W = ((Base::T * 8) % 32 == 0 && N != 384) ? 8 : Base::W;
+  using C = Col<Base::T, W, typename Base::Radix>;
+  static constexpr int MINB = C::THREADS <= 384 ? 2 : 1;  // resident blocks the register cap allows
+};
+
 template <int N>
 __host__ __device__ constexpr size_t col_smem_bytes() {
-  return col_smem_bytes_c<typename Cfg<N>::C>();
+  return col_smem_bytes_c<typename ColPass<N>::C>();
 }
 
 template <int N>
@@ -72,7 +85,7 @@ __device__ __forceinline__ ColSmem col_smem_c(unsigned char* base) {
 
 template <int N>
 __device__ __forceinline__ ColSmem col_smem(unsigned char* base) {
-  return col_smem_c<typename Cfg<N>::C>(base);
+  return col_smem_c<typename ColPass<N>::C>(base);
 }
 
 // Copy the twiddles and build map[row] = index of `row` in this frame's line
@@ -111,9 +124,9 @@ struct FwdColArgs {
   int* err;
 };
 
-template <int N, class St, int TH = Cfg<N>::C::THREADS>
-__global__ void __launch_bounds__(TH) k_fwd_col(FwdColArgs<St> a) {
-  using C = typename Cfg<N>::C;
+template <int N, class St, int TH = ColPass<N>::C::THREADS>
+__global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_fwd_col(FwdColArgs<St> a) {
+  using C = typename ColPass<N>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ColSmem s = col_smem<N>(smem_raw);
   const int f = blockIdx.y;
@@ -183,10 +196,23 @@ __global__ void __launch_bounds__(TH)
   float2* bufs[2] = {tile, tile + C::W * P};  // the tile doubles as the first exchange buffer
   const C col;
   const long r0 = (long)blockIdx.x * C::W;
-  for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = a.tw[i];
-  for (int i = threadIdx.x; i < C::W * N; i += C::THREADS) {
-    const int rr = i / N, e = i - rr * N;
-    tile[rr * P + e] = (r0 + rr < a.rows) ? InSt::ld(a.in, (size_t)(r0 + rr) * N + e) : make_float2(0.f, 0.f);
+  // every load of the tile is issued before the first shared store
+  constexpr int PER = (C::W * N + C::THREADS - 1) / C::THREADS;
+  {
+    float2 v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = (int)threadIdx.x + k * C::THREADS;
+      const int rr = i / N, e = i - rr * N;
+      v[k] = (i < C::W * N && r0 + rr < a.rows) ? InSt::ld(a.in, (size_t)(r0 + rr) * N + e) : make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = a.tw[i];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = (int)threadIdx.x + k * C::THREADS;
+      const int rr = i / N, e = i - rr * N;
+      if (i < C::W * N) tile[rr * P + e] = v[k];
+    }
   }
   __syncthreads();
   const float scale = rsqrtf((float)N);
@@ -221,9 +247,20 @@ __global__ void __launch_bounds__(TH)
         if (col.ok0(j)) row[col.xrow(j, n)] = cscale(xr[j][n], scale);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < C::W * N; i += C::THREADS) {
-    const int rr = i / N, e = i - rr * N;
-    if (r0 + rr < a.rows) OutSt::st(a.out, (size_t)(r0 + rr) * N + e, tile[rr * P + e]);
+  {
+    float2 v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = (int)threadIdx.x + k * C::THREADS;
+      const int rr = i / N, e = i - rr * N;
+      v[k] = i < C::W * N ? tile[rr * P + e] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = (int)threadIdx.x + k * C::THREADS;
+      const int rr = i / N, e = i - rr * N;
+      if (i < C::W * N && r0 + rr < a.rows) OutSt::st(a.out, (size_t)(r0 + rr) * N + e, v[k]);
+    }
   }
 }
 
@@ -247,9 +284,9 @@ struct AdjColArgs {
   CgState cg;
 };
 
-template <int N, class St, int MODE, int TH = Cfg<N>::C::THREADS>
-__global__ void __launch_bounds__(TH) k_adj_col(AdjColArgs<St> a) {
-  using C = typename Cfg<N>::C;
+template <int N, class St, int MODE, int TH = ColPass<N>::C::THREADS>
+__global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St> a) {
+  using C = typename ColPass<N>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ColSmem s = col_smem<N>(smem_raw);
   const int f = blockIdx.y;
@@ -269,35 +306,66 @@ __global__ void __launch_bounds__(TH) k_adj_col(AdjColArgs<St> a) {
       accr[j][n] = 0.f;
     }
 
-#pragma unroll 1
-  for (int c = 0; c < a.coils; ++c) {
-    float2 xr[C::J0][C::R0];
-    float2 kr[C::JL][C::RL];
+  // With blocks of up to 256 threads (registers to spare at two blocks per
+  // SM), coil c + 1's k-space values and maps are loaded into registers
+  // before coil c is transformed, so their latency overlaps the transform.
+  constexpr bool PREFETCH = C::THREADS <= 256;
+  auto load_k = [&](int c, float2 (&kv)[C::JL][C::RL]) {
     const float2* src = a.tmp + ((size_t)f * a.coils + c) * a.L * a.nx;
 #pragma unroll
     for (int j = 0; j < C::JL; ++j)
 #pragma unroll
       for (int m = 0; m < C::RL; ++m) {
-        float2 v = make_float2(0.f, 0.f);
-        if (col.okL(j) && xin) {
-          const int l = s.map[col.krow(j, m)];
-          if (l >= 0) v = __ldg(src + (size_t)l * a.nx + x);
-        }
-        kr[j][m] = v;
+        const int l = (col.okL(j) && xin) ? (int)s.map[col.krow(j, m)] : -1;
+        kv[j][m] = l >= 0 ? __ldg(src + (size_t)l * a.nx + x) : make_float2(0.f, 0.f);
       }
+  };
+  auto load_s = [&](int c, float2 (&sv)[C::J0][C::R0]) {
+#pragma unroll
+    for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+      for (int n = 0; n < C::R0; ++n)
+        sv[j][n] = (MODE != 2 && col.ok0(j) && xin) ? St::ld(a.S, c * img + (size_t)col.xrow(j, n) * a.nx + x)
+                                                    : make_float2(0.f, 0.f);
+  };
+  float2 knext[C::JL][C::RL];
+  float2 snext[C::J0][C::R0];
+  if (PREFETCH && a.coils > 0) {
+    load_k(0, knext);
+    load_s(0, snext);
+  }
+#pragma unroll 1
+  for (int c = 0; c < a.coils; ++c) {
+    float2 xr[C::J0][C::R0];
+    float2 kr[C::JL][C::RL];
+    float2 sv[C::J0][C::R0];
+    if constexpr (PREFETCH) {
+#pragma unroll
+      for (int j = 0; j < C::JL; ++j)
+#pragma unroll
+        for (int m = 0; m < C::RL; ++m) kr[j][m] = knext[j][m];
+#pragma unroll
+      for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+        for (int n = 0; n < C::R0; ++n) sv[j][n] = snext[j][n];
+      if (c + 1 < a.coils) {
+        load_k(c + 1, knext);
+        load_s(c + 1, snext);
+      }
+    } else {
+      load_k(c, kr);
+      load_s(c, sv);
+    }
     const BufPair<C> bp(s.buf0, s.buf1, c);
     col.inv(kr, xr, bp.b, s.tw);
 #pragma unroll
     for (int j = 0; j < C::J0; ++j)
 #pragma unroll
       for (int n = 0; n < C::R0; ++n) {
-        if (MODE == 2) {
+        if (MODE == 2)
           accr[j][n] = fmaf(xr[j][n].x, xr[j][n].x, fmaf(xr[j][n].y, xr[j][n].y, accr[j][n]));
-        } else {
-          float2 sv = make_float2(0.f, 0.f);
-          if (col.ok0(j) && xin) sv = St::ld(a.S, c * img + (size_t)col.xrow(j, n) * a.nx + x);
-          acc[j][n] = cfma_conj(acc[j][n], sv, xr[j][n]);
-        }
+        else
+          acc[j][n] = cfma_conj(acc[j][n], sv[j][n], xr[j][n]);
       }
   }
 

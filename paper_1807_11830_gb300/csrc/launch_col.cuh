@@ -12,7 +12,7 @@ cudaError_t fwd_col_n(const FwdColArgs<St>& a, int tiles, int frames, cudaStream
   constexpr size_t sm = col_smem_bytes<N>();
   cudaError_t e = ensure_smem(k_fwd_col<N, St>, sm, &done);
   if (e != cudaSuccess || tiles == 0 || frames == 0) return e;
-  k_fwd_col<N, St><<<dim3(tiles, frames), Cfg<N>::C::THREADS, sm, s>>>(a);
+  k_fwd_col<N, St><<<dim3(tiles, frames), ColPass<N>::C::THREADS, sm, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -22,7 +22,7 @@ cudaError_t adj_col_n(const AdjColArgs<St>& a, int tiles, int frames, cudaStream
   constexpr size_t sm = col_smem_bytes<N>();
   cudaError_t e = ensure_smem(k_adj_col<N, St, MODE>, sm, &done);
   if (e != cudaSuccess || tiles == 0 || frames == 0) return e;
-  k_adj_col<N, St, MODE><<<dim3(tiles, frames), Cfg<N>::C::THREADS, sm, s>>>(a);
+  k_adj_col<N, St, MODE><<<dim3(tiles, frames), ColPass<N>::C::THREADS, sm, s>>>(a);
   return cudaGetLastError();
 }
 
