@@ -41,11 +41,12 @@ def _load(path):
     i = ctypes.c_int
     lib.orc_dft.argtypes = [i, i, dp, dp]
     lib.orc_fft.argtypes = [i, i, dp, dp]
-    lib.orc_fft2.argtypes = [i, i, i, i, dp, dp]
-    for name in ("orc_forward", "orc_adjoint", "orc_normal", "orc_normal_collapsed"):
-        getattr(lib, name).argtypes = [i, i, i, i, i, dp, dp, ip, dp]
-    lib.orc_cg.argtypes = [i, i, i, i, i, dp, dp, ip, i, ctypes.c_double, dp, ip, dp, ip]
-    lib.orc_rss.argtypes = [i, i, i, i, i, dp, ip, dp]
+    lib.orc_fft2.argtypes = [i, i, i, i, dp, dp, i]
+    for name in ("orc_forward", "orc_adjoint", "orc_normal"):
+        getattr(lib, name).argtypes = [i, i, i, i, i, dp, dp, ip, dp, i]
+    lib.orc_normal_collapsed.argtypes = [i, i, i, i, i, dp, dp, ip, dp]
+    lib.orc_cg.argtypes = [i, i, i, i, i, dp, dp, ip, i, ctypes.c_double, dp, ip, dp, ip, i]
+    lib.orc_rss.argtypes = [i, i, i, i, i, dp, ip, dp, i]
     lib.orc_bf16_rne.argtypes = [ctypes.c_long, ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(ctypes.c_uint16)]
     lib.orc_bf16_rne.restype = None
@@ -101,12 +102,12 @@ def fft(v, inverse=False):
     return out
 
 
-def fft2(img, inverse=False):
+def fft2(img, inverse=False, centred=False):
     img = _c128(img)
     ny, nx = img.shape[-2:]
     count = int(np.prod(img.shape[:-2])) if img.ndim > 2 else 1
     out = np.empty_like(img)
-    _check(_lib().orc_fft2(count, ny, nx, 1 if inverse else -1, _dptr(img), _dptr(out)), "fft2")
+    _check(_lib().orc_fft2(count, ny, nx, 1 if inverse else -1, _dptr(img), _dptr(out), int(centred)), "fft2")
     return out
 
 
@@ -118,27 +119,30 @@ def _shape(x_or_none, S, lines):
     return S, lines, F, C, ny, nx, L
 
 
-def forward(x, S, lines):
+def forward(x, S, lines, centred=False):
     S, lines, F, C, ny, nx, L = _shape(x, S, lines)
     x = _c128(x).reshape(F, ny, nx)
     y = np.empty((F, C, L, nx), np.complex128)
-    _check(_lib().orc_forward(F, C, ny, nx, L, _dptr(x), _dptr(S), _iptr(lines), _dptr(y)), "forward")
+    _check(_lib().orc_forward(F, C, ny, nx, L, _dptr(x), _dptr(S), _iptr(lines), _dptr(y), int(centred)),
+           "forward")
     return y
 
 
-def adjoint(y, S, lines):
+def adjoint(y, S, lines, centred=False):
     S, lines, F, C, ny, nx, L = _shape(None, S, lines)
     y = _c128(y).reshape(F, C, L, nx)
     x = np.empty((F, ny, nx), np.complex128)
-    _check(_lib().orc_adjoint(F, C, ny, nx, L, _dptr(y), _dptr(S), _iptr(lines), _dptr(x)), "adjoint")
+    _check(_lib().orc_adjoint(F, C, ny, nx, L, _dptr(y), _dptr(S), _iptr(lines), _dptr(x), int(centred)),
+           "adjoint")
     return x
 
 
-def normal(x, S, lines):
+def normal(x, S, lines, centred=False):
     S, lines, F, C, ny, nx, L = _shape(x, S, lines)
     x = _c128(x).reshape(F, ny, nx)
     out = np.empty_like(x)
-    _check(_lib().orc_normal(F, C, ny, nx, L, _dptr(x), _dptr(S), _iptr(lines), _dptr(out)), "normal")
+    _check(_lib().orc_normal(F, C, ny, nx, L, _dptr(x), _dptr(S), _iptr(lines), _dptr(out), int(centred)),
+           "normal")
     return out
 
 
@@ -151,7 +155,7 @@ def normal_collapsed(x, S, lines):
     return out
 
 
-def cg(y, S, lines, max_iter, tol=0.0):
+def cg(y, S, lines, max_iter, tol=0.0, centred=False):
     """Returns (x, iters[F], resid[F], status[F])."""
     S, lines, F, C, ny, nx, L = _shape(None, S, lines)
     y = _c128(y).reshape(F, C, L, nx)
@@ -160,16 +164,16 @@ def cg(y, S, lines, max_iter, tol=0.0):
     resid = np.zeros(F, np.float64)
     status = np.zeros(F, np.int32)
     _check(_lib().orc_cg(F, C, ny, nx, L, _dptr(y), _dptr(S), _iptr(lines), int(max_iter), float(tol),
-                         _dptr(x), _iptr(iters), _dptr(resid), _iptr(status)), "cg")
+                         _dptr(x), _iptr(iters), _dptr(resid), _iptr(status), int(centred)), "cg")
     return x, iters, resid, status
 
 
-def rss(y, lines, ny):
+def rss(y, lines, ny, centred=False):
     lines = np.ascontiguousarray(lines, dtype=np.int32)
     y = _c128(y)
     F, C, L, nx = y.shape
     out = np.empty((F, ny, nx), np.float64)
-    _check(_lib().orc_rss(F, C, ny, nx, L, _dptr(y), _iptr(lines), _dptr(out)), "rss")
+    _check(_lib().orc_rss(F, C, ny, nx, L, _dptr(y), _iptr(lines), _dptr(out), int(centred)), "rss")
     return out
 
 

@@ -22,7 +22,11 @@
 // Conventions (readings of the paper where it is silent):
 //   * F is unitary: forward kernel exp(-2 pi i jk/n)/sqrt(n), inverse the
 //     conjugate with the same scale (Eq. 1 writes F^{-1} without a scale).
-//   * DC sits at index 0 (no fftshift).  y (slow index, rows) is the masked
+//   * DC sits at index 0 (no fftshift) unless an entry point's `centred` is
+//     1: then every transform is the centred one, DC and the image centre at
+//     index floor(n/2) along each axis, defined as fftshift . F . ifftshift
+//     (fftshift rotates by floor(n/2), ifftshift back), and the line indices
+//     address that centred k-space.  y (slow index, rows) is the masked
 //     phase-encode direction; x (fast index) is the fully sampled readout.
 //   * lines[f][0..L) is strictly increasing inside [0, ny).
 //   * complex arrays are interleaved (re, im) doubles, row-major:
@@ -99,11 +103,26 @@ void fft1_strided(int n, int dir, cd* data, long stride, std::vector<cd>& tmp_in
   for (int j = 0; j < n; ++j) data[(long)j * stride] = tmp_out[j] * s;
 }
 
+// Rotate v[0], v[stride], ..., v[(n-1) stride] so that element i moves to
+// (i + shift) mod n.
+void rotate_strided(int n, cd* v, long stride, int shift) {
+  std::vector<cd> t((size_t)n);
+  for (int i = 0; i < n; ++i) t[((i + shift) % n + n) % n] = v[(long)i * stride];
+  for (int i = 0; i < n; ++i) v[(long)i * stride] = t[i];
+}
+
+// Unitary transform of one strided sequence; centred: fftshift . F . ifftshift.
+void fft1_conv(int n, int dir, cd* v, long stride, bool centred, std::vector<cd>& a, std::vector<cd>& b) {
+  if (centred) rotate_strided(n, v, stride, -(n / 2));  // ifftshift
+  fft1_strided(n, dir, v, stride, a, b);
+  if (centred) rotate_strided(n, v, stride, n / 2);  // fftshift
+}
+
 // Unitary 2D transform F2 = F_y F_x of one [ny][nx] image, in place.
-void fft2_inplace(int ny, int nx, int dir, cd* img) {
+void fft2_inplace(int ny, int nx, int dir, cd* img, bool centred = false) {
   std::vector<cd> a, b;
-  for (int r = 0; r < ny; ++r) fft1_strided(nx, dir, img + (long)r * nx, 1, a, b);
-  for (int c = 0; c < nx; ++c) fft1_strided(ny, dir, img + c, nx, a, b);
+  for (int r = 0; r < ny; ++r) fft1_conv(nx, dir, img + (long)r * nx, 1, centred, a, b);
+  for (int c = 0; c < nx; ++c) fft1_conv(ny, dir, img + c, nx, centred, a, b);
 }
 
 bool lines_ok(int ny, int L, const int* ln) {
@@ -121,20 +140,20 @@ bool all_lines_ok(int F, int ny, int L, const int* lines) {
 }
 
 // E for one frame: y_f[c][l][:] = F2(S_c . x_f)[ln[l]][:].
-void forward_frame(int C, int ny, int nx, int L, const cd* xf, const cd* S, const int* ln, cd* yf) {
+void forward_frame(int C, int ny, int nx, int L, const cd* xf, const cd* S, const int* ln, cd* yf, bool centred) {
   long npix = (long)ny * nx;
   std::vector<cd> t((size_t)npix);
   for (int c = 0; c < C; ++c) {
     const cd* Sc = S + c * npix;
     for (long i = 0; i < npix; ++i) t[i] = Sc[i] * xf[i];
-    fft2_inplace(ny, nx, -1, t.data());
+    fft2_inplace(ny, nx, -1, t.data(), centred);
     for (int l = 0; l < L; ++l)
       for (int k = 0; k < nx; ++k) yf[((long)c * L + l) * nx + k] = t[(long)ln[l] * nx + k];
   }
 }
 
 // E^H for one frame: x_f = sum_c conj(S_c) . F2^H(Z y_{f,c}), Z the zero-fill.
-void adjoint_frame(int C, int ny, int nx, int L, const cd* yf, const cd* S, const int* ln, cd* xf) {
+void adjoint_frame(int C, int ny, int nx, int L, const cd* yf, const cd* S, const int* ln, cd* xf, bool centred) {
   long npix = (long)ny * nx;
   std::vector<cd> z((size_t)npix);
   for (long i = 0; i < npix; ++i) xf[i] = 0.0;
@@ -142,17 +161,17 @@ void adjoint_frame(int C, int ny, int nx, int L, const cd* yf, const cd* S, cons
     for (long i = 0; i < npix; ++i) z[i] = 0.0;
     for (int l = 0; l < L; ++l)
       for (int k = 0; k < nx; ++k) z[(long)ln[l] * nx + k] = yf[((long)c * L + l) * nx + k];
-    fft2_inplace(ny, nx, +1, z.data());
+    fft2_inplace(ny, nx, +1, z.data(), centred);
     const cd* Sc = S + c * npix;
     for (long i = 0; i < npix; ++i) xf[i] += std::conj(Sc[i]) * z[i];
   }
 }
 
 // E^H E for one frame, literally adjoint(forward(.)).
-void normal_frame(int C, int ny, int nx, int L, const cd* xf, const cd* S, const int* ln, cd* of) {
+void normal_frame(int C, int ny, int nx, int L, const cd* xf, const cd* S, const int* ln, cd* of, bool centred) {
   std::vector<cd> y((size_t)C * L * nx);
-  forward_frame(C, ny, nx, L, xf, S, ln, y.data());
-  adjoint_frame(C, ny, nx, L, y.data(), S, ln, of);
+  forward_frame(C, ny, nx, L, xf, S, ln, y.data(), centred);
+  adjoint_frame(C, ny, nx, L, y.data(), S, ln, of, centred);
 }
 
 // Re <a, b> = Re sum conj(a) b, sequential sum.
@@ -210,18 +229,18 @@ int orc_fft(int n, int dir, const double* in, double* out) {
 }
 
 // Unitary 2D transform F2 = F_y F_x of `count` stacked [ny][nx] images.
-int orc_fft2(int count, int ny, int nx, int dir, const double* in, double* out) {
+int orc_fft2(int count, int ny, int nx, int dir, const double* in, double* out, int centred) {
   if (count < 0 || ny <= 0 || nx <= 0 || (dir != 1 && dir != -1)) return ORC_EINVAL;
   long npix = (long)ny * nx;
   if (out != in) std::memcpy(out, in, sizeof(double) * 2 * npix * count);
   cd* b = reinterpret_cast<cd*>(out);
 #pragma omp parallel for schedule(dynamic)
-  for (int i = 0; i < count; ++i) fft2_inplace(ny, nx, dir, b + i * npix);
+  for (int i = 0; i < count; ++i) fft2_inplace(ny, nx, dir, b + i * npix, centred != 0);
   return ORC_OK;
 }
 
 int orc_forward(int F, int C, int ny, int nx, int L, const double* x, const double* S, const int* lines,
-                double* y) {
+                double* y, int centred) {
   if (F < 0 || C <= 0 || ny <= 0 || nx <= 0 || L < 0 || L > ny) return ORC_EINVAL;
   if (!all_lines_ok(F, ny, L, lines)) return ORC_EINVAL;
   long npix = (long)ny * nx;
@@ -230,12 +249,12 @@ int orc_forward(int F, int C, int ny, int nx, int L, const double* x, const doub
   cd* yc = reinterpret_cast<cd*>(y);
 #pragma omp parallel for schedule(dynamic)
   for (int f = 0; f < F; ++f)
-    forward_frame(C, ny, nx, L, xc + f * npix, Sc, lines + (long)f * L, yc + (long)f * C * L * nx);
+    forward_frame(C, ny, nx, L, xc + f * npix, Sc, lines + (long)f * L, yc + (long)f * C * L * nx, centred != 0);
   return ORC_OK;
 }
 
 int orc_adjoint(int F, int C, int ny, int nx, int L, const double* y, const double* S, const int* lines,
-                double* x) {
+                double* x, int centred) {
   if (F < 0 || C <= 0 || ny <= 0 || nx <= 0 || L < 0 || L > ny) return ORC_EINVAL;
   if (!all_lines_ok(F, ny, L, lines)) return ORC_EINVAL;
   long npix = (long)ny * nx;
@@ -244,13 +263,13 @@ int orc_adjoint(int F, int C, int ny, int nx, int L, const double* y, const doub
   cd* xc = reinterpret_cast<cd*>(x);
 #pragma omp parallel for schedule(dynamic)
   for (int f = 0; f < F; ++f)
-    adjoint_frame(C, ny, nx, L, yc + (long)f * C * L * nx, Sc, lines + (long)f * L, xc + f * npix);
+    adjoint_frame(C, ny, nx, L, yc + (long)f * C * L * nx, Sc, lines + (long)f * L, xc + f * npix, centred != 0);
   return ORC_OK;
 }
 
 // Literal E^H(E x).
 int orc_normal(int F, int C, int ny, int nx, int L, const double* x, const double* S, const int* lines,
-               double* out) {
+               double* out, int centred) {
   if (F < 0 || C <= 0 || ny <= 0 || nx <= 0 || L < 0 || L > ny) return ORC_EINVAL;
   if (!all_lines_ok(F, ny, L, lines)) return ORC_EINVAL;
   long npix = (long)ny * nx;
@@ -258,7 +277,8 @@ int orc_normal(int F, int C, int ny, int nx, int L, const double* x, const doubl
   const cd* Sc = reinterpret_cast<const cd*>(S);
   cd* oc = reinterpret_cast<cd*>(out);
 #pragma omp parallel for schedule(dynamic)
-  for (int f = 0; f < F; ++f) normal_frame(C, ny, nx, L, xc + f * npix, Sc, lines + (long)f * L, oc + f * npix);
+  for (int f = 0; f < F; ++f)
+    normal_frame(C, ny, nx, L, xc + f * npix, Sc, lines + (long)f * L, oc + f * npix, centred != 0);
   return ORC_OK;
 }
 
@@ -315,7 +335,7 @@ enum { ORC_CG_RUNNING = 0, ORC_CG_CONVERGED = 1, ORC_CG_MAXITER = 2, ORC_CG_BREA
 // Outputs: x [F][ny][nx]; iters[f] = iterations applied; resid[f] =
 // sqrt(rho/rho0) at exit (0 when rho0 == 0); status[f] as above.
 int orc_cg(int F, int C, int ny, int nx, int L, const double* y, const double* S, const int* lines, int max_iter,
-           double tol, double* x, int* iters, double* resid, int* status) {
+           double tol, double* x, int* iters, double* resid, int* status, int centred) {
   if (F < 0 || C <= 0 || ny <= 0 || nx <= 0 || L < 0 || L > ny || max_iter < 0 || !(tol >= 0.0))
     return ORC_EINVAL;
   if (!all_lines_ok(F, ny, L, lines)) return ORC_EINVAL;
@@ -328,7 +348,7 @@ int orc_cg(int F, int C, int ny, int nx, int L, const double* y, const double* S
     const int* ln = lines + (long)f * L;
     cd* xf = xc + f * npix;
     std::vector<cd> r((size_t)npix), p((size_t)npix), q((size_t)npix);
-    adjoint_frame(C, ny, nx, L, yc + (long)f * C * L * nx, Sc, ln, r.data());
+    adjoint_frame(C, ny, nx, L, yc + (long)f * C * L * nx, Sc, ln, r.data(), centred != 0);
     for (long i = 0; i < npix; ++i) { xf[i] = 0.0; p[i] = r[i]; }
     double rho = re_dot(npix, r.data(), r.data());
     double rho0 = rho;
@@ -336,7 +356,7 @@ int orc_cg(int F, int C, int ny, int nx, int L, const double* y, const double* S
     int st = ORC_CG_RUNNING;
     if (rho0 == 0.0) st = ORC_CG_CONVERGED;
     while (st == ORC_CG_RUNNING && it < max_iter) {
-      normal_frame(C, ny, nx, L, p.data(), Sc, ln, q.data());
+      normal_frame(C, ny, nx, L, p.data(), Sc, ln, q.data(), centred != 0);
       double pq = re_dot(npix, p.data(), q.data());
       if (!(pq > 0.0)) { st = ORC_CG_BREAKDOWN; break; }
       double alpha = rho / pq;
@@ -366,7 +386,7 @@ int orc_cg(int F, int C, int ny, int nx, int L, const double* y, const double* S
 // Root sum of squares (Sec. IV-B): per frame and pixel,
 //   out[f][i] = sqrt(sum_c |F2^H(Z y_{f,c})[i]|^2)
 // with y [F][C][L][nx] and the same line convention as orc_adjoint.
-int orc_rss(int F, int C, int ny, int nx, int L, const double* y, const int* lines, double* out) {
+int orc_rss(int F, int C, int ny, int nx, int L, const double* y, const int* lines, double* out, int centred) {
   if (F < 0 || C <= 0 || ny <= 0 || nx <= 0 || L < 0 || L > ny) return ORC_EINVAL;
   if (!all_lines_ok(F, ny, L, lines)) return ORC_EINVAL;
   long npix = (long)ny * nx;
@@ -381,7 +401,7 @@ int orc_rss(int F, int C, int ny, int nx, int L, const double* y, const int* lin
       const cd* yfc = yc + ((long)f * C + c) * L * nx;
       for (int l = 0; l < L; ++l)
         for (int k = 0; k < nx; ++k) z[(long)ln[l] * nx + k] = yfc[(long)l * nx + k];
-      fft2_inplace(ny, nx, +1, z.data());
+      fft2_inplace(ny, nx, +1, z.data(), centred != 0);
       for (long i = 0; i < npix; ++i) acc[i] += std::norm(z[i]);
     }
     for (long i = 0; i < npix; ++i) out[f * npix + i] = std::sqrt(acc[i]);

@@ -12,6 +12,7 @@ import subprocess
 import pytest
 
 import oracle
+import tests.test_oracle_centred as centred
 import tests.test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "sense_oracle.cpp")
@@ -41,6 +42,11 @@ MUTANTS = {
     # direct DFT index slip
     "dft_index": ("in[(long)j * stride] * unit_root((long long)j * k, n, dir)",
                   "in[(long)j * stride] * unit_root((long long)j * (k + 1), n, dir)"),
+    # centred transform forgets the output fftshift
+    "centred_no_fftshift": ("  if (centred) rotate_strided(n, v, stride, n / 2);  // fftshift\n", "\n"),
+    # centred transform shifts the input the wrong way (differs for odd n)
+    "centred_shift_direction": ("rotate_strided(n, v, stride, -(n / 2));  // ifftshift",
+                                "rotate_strided(n, v, stride, n / 2);  // ifftshift"),
 }
 
 QUICK_PINS = [
@@ -54,6 +60,8 @@ QUICK_PINS = [
     lambda: pins.test_full_sampling_is_identity(64, 4),
     pins.test_cg_against_dense_krylov_solves,
     pins.test_bf16_rne_hand_cases,
+    lambda: [centred.test_centred_fft2_brute_force(*sh) for sh in [(3, 5), (4, 6), (7, 7)]],
+    lambda: centred.test_centred_adjoint_identity_and_full_sampling((16, 12, 3, 7, 2)),
 ]
 
 
