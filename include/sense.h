@@ -64,10 +64,24 @@ typedef enum {
 typedef enum { SENSE_STORE_C64 = 0, SENSE_STORE_BF16 = 1 } sense_storage;
 
 /* Problem shape of one plan: ny x nx images, `coils` maps, `frames` images
- * sharing them, `lines` sampled phase-encode rows per frame. */
+ * sharing them, `lines` sampled phase-encode rows per frame.
+ *
+ * `centred` selects the k-space convention (the paper fixes none):
+ *   0  DC at index 0 along both axes, image origin at pixel (0, 0): every
+ *      transform is the unitary DFT exp(-2 pi i jk/n) / sqrt(n);
+ *   1  DC at index n/2 and the image centre at pixel n/2 along both axes:
+ *      every transform is the centred unitary DFT
+ *      exp(-2 pi i (k - n/2)(j - n/2)/n) / sqrt(n) (fftshift . F . ifftshift),
+ *      and `lines` index that centred k-space.
+ * Every supported length is even, where the centred DFT equals
+ * (-1)^(n/2) D F D with D = diag((-1)^i); the library applies those signs at
+ * the kernels' loads and stores, and CG iterates in the sign-modulated image
+ * space (the same scalars, residuals and iteration counts), mapping x back at
+ * the end. */
 typedef struct {
   int ny, nx, coils, frames, lines;
   int storage; /* sense_storage of S and y */
+  int centred; /* 0 or 1, see above */
 } sense_shape;
 
 /* Per-frame CG outcome written by sense_cg_solve. */

@@ -138,7 +138,9 @@ sense_status run_batch(sense_batch* b, const sense_batch_io* io, const std::vect
       if (e != cudaSuccess) return bfail(SENSE_ECUDA, std::string("persistent CG (batch): ") + cudaGetErrorString(e));
     }
     for (int i : c.members) {
-      sense_status rc = plan_cg_finish(b->plans[i], io[i].iters_out, io[i].rel_resid_out, io[i].outcome_out, st);
+      sense_status rc = plan_centred_output(b->plans[i], reinterpret_cast<float2*>(io[i].x_out), st);
+      if (rc == SENSE_OK)
+        rc = plan_cg_finish(b->plans[i], io[i].iters_out, io[i].rel_resid_out, io[i].outcome_out, st);
       if (rc != SENSE_OK) return rc;
     }
   }

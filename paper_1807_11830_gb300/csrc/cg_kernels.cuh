@@ -93,6 +93,19 @@ __global__ void k_cg_finish(CgState g, int frames, int* iters_out, double* resid
   if (outcome_out) outcome_out[f] = oc;
 }
 
+// CG iterates of a centred-k-space problem live in the modulated space
+// x' = D x (D = diag((-1)^(y+x))): map the solution back, in place.
+__global__ void k_checkerboard(float2* x, int ny, int nx, long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long pix = i % ((long)ny * nx);
+  const int yy = (int)(pix / nx), xx = (int)(pix - (long)yy * nx);
+  if ((yy + xx) & 1) {
+    const float2 v = x[i];
+    x[i] = make_float2(-v.x, -v.y);
+  }
+}
+
 // Self-test of the bounded wait: waits for a flag that nothing sets and
 // records whether the wait gave up (1) or saw the flag (0).
 __global__ void k_wait_selftest(const int* flag, long max_spins, int* timed_out) {

@@ -88,6 +88,14 @@ __device__ __forceinline__ ColSmem col_smem(unsigned char* base) {
   return col_smem_c<typename ColPass<N>::C>(base);
 }
 
+// Centred k-space (DC at n/2): F_c = (-1)^(n/2) D F D with D = diag((-1)^i),
+// so the kernels keep the uncentred transforms and flip signs at their loads
+// and stores: image pixels by (-1)^(y+x), k-space rows by (-1)^ky, row
+// elements by (-1)^kx times the constant (-1)^(ny/2 + nx/2).
+__device__ __forceinline__ float2 negate_if(float2 v, bool neg) {
+  return neg ? make_float2(-v.x, -v.y) : v;
+}
+
 // Copy the twiddles and build map[row] = index of `row` in this frame's line
 // list, or -1 if the row is not sampled.  Out-of-range or unordered lines are
 // skipped and flagged.
@@ -121,6 +129,7 @@ struct FwdColArgs {
   float2* tmp;                  // [F][C][L][nx]
   const float2* tw;
   int nx, coils, L;
+  int centred;                  // 1: centred k-space (image and k-space row signs)
   int* err;
 };
 
@@ -142,7 +151,8 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_fwd_col(FwdColArgs<St>
   for (int j = 0; j < C::J0; ++j)
 #pragma unroll
     for (int n = 0; n < C::R0; ++n)
-      xv[j][n] = (col.ok0(j) && xin) ? __ldg(a.x + f * img + (size_t)col.xrow(j, n) * a.nx + x)
+      xv[j][n] = (col.ok0(j) && xin) ? negate_if(__ldg(a.x + f * img + (size_t)col.xrow(j, n) * a.nx + x),
+                                                 a.centred && ((col.xrow(j, n) + x) & 1))
                                       : make_float2(0.f, 0.f);
 
 #pragma unroll 1
@@ -166,7 +176,8 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_fwd_col(FwdColArgs<St>
       for (int m = 0; m < C::RL; ++m) {
         if (col.okL(j) && xin) {
           const int l = s.map[col.krow(j, m)];
-          if (l >= 0) dst[(size_t)l * a.nx + x] = cscale(kr[j][m], scale);
+          if (l >= 0)
+            dst[(size_t)l * a.nx + x] = negate_if(cscale(kr[j][m], scale), a.centred && (col.krow(j, m) & 1));
         }
       }
   }
@@ -183,6 +194,8 @@ struct RowArgs {
   OutT* out;
   const float2* tw;
   long rows;
+  int centred;  // 1: k-space elements times cs (-1)^kx (inverse: on input; forward: on output)
+  float cs;     // (-1)^(ny/2 + nx/2)
 };
 
 template <int N, int DIR, class InSt, class OutSt, int TH = Cfg<N>::C::THREADS>
@@ -205,6 +218,7 @@ __global__ void __launch_bounds__(TH)
       const int i = (int)threadIdx.x + k * C::THREADS;
       const int rr = i / N, e = i - rr * N;
       v[k] = (i < C::W * N && r0 + rr < a.rows) ? InSt::ld(a.in, (size_t)(r0 + rr) * N + e) : make_float2(0.f, 0.f);
+      if (DIR > 0 && a.centred) v[k] = cscale(v[k], (e & 1) ? -a.cs : a.cs);
     }
     for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = a.tw[i];
 #pragma unroll
@@ -259,6 +273,7 @@ __global__ void __launch_bounds__(TH)
     for (int k = 0; k < PER; ++k) {
       const int i = (int)threadIdx.x + k * C::THREADS;
       const int rr = i / N, e = i - rr * N;
+      if (DIR < 0 && a.centred) v[k] = cscale(v[k], (e & 1) ? -a.cs : a.cs);
       if (i < C::W * N && r0 + rr < a.rows) OutSt::st(a.out, (size_t)(r0 + rr) * N + e, v[k]);
     }
   }
@@ -280,6 +295,7 @@ struct AdjColArgs {
   float2* p;                  // MODE 1
   float* rss;                 // MODE 2
   int nx, coils, L, tiles;
+  int centred;                // 1: k-space rows by (-1)^ky; MODE 0 output by (-1)^(y+x)
   int* err;
   CgState cg;
 };
@@ -317,7 +333,8 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St>
 #pragma unroll
       for (int m = 0; m < C::RL; ++m) {
         const int l = (col.okL(j) && xin) ? (int)s.map[col.krow(j, m)] : -1;
-        kv[j][m] = l >= 0 ? __ldg(src + (size_t)l * a.nx + x) : make_float2(0.f, 0.f);
+        kv[j][m] = l >= 0 ? negate_if(__ldg(src + (size_t)l * a.nx + x), a.centred && (col.krow(j, m) & 1))
+                          : make_float2(0.f, 0.f);
       }
   };
   auto load_s = [&](int c, float2 (&sv)[C::J0][C::R0]) {
@@ -382,7 +399,7 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St>
       } else {
         const float2 v = cscale(acc[j][n], scale);
         if (MODE == 0) {
-          a.x[idx] = v;
+          a.x[idx] = negate_if(v, a.centred && ((col.xrow(j, n) + x) & 1));
         } else {
           a.r[idx] = v;
           a.p[idx] = v;
@@ -437,6 +454,7 @@ struct NormalTile {
   float2* q;            // CG=true, frame base
   const void* S;        // maps [C][N][nx], storage type
   int nx, coils, tile, p_update;
+  int centred;          // CG=false: x and out signed by (-1)^(y+x)
   float beta;
 };
 
@@ -463,7 +481,7 @@ __device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem&
             __stcg(a.p_dst + idx, v);
           }
         } else {
-          v = __ldg(a.x + idx);
+          v = negate_if(__ldg(a.x + idx), a.centred && ((col.xrow(j, n) + x) & 1));
         }
       }
       p[j][n] = v;
@@ -514,7 +532,7 @@ __device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem&
         __stcg(a.q + idx, qv);
         part = fmaf(p[j][n].x, qv.x, fmaf(p[j][n].y, qv.y, part));
       } else {
-        a.out[idx] = qv;
+        a.out[idx] = negate_if(qv, a.centred && ((col.xrow(j, n) + x) & 1));
       }
     }
   return part;
@@ -770,7 +788,7 @@ __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSm
           __stcg(a.p_dst + idx, v);
         }
       } else {
-        v = __ldg(a.x + idx);
+        v = negate_if(__ldg(a.x + idx), a.centred && ((row + xx) & 1));
       }
     }
     s.buf0[cc * CP + row] = v;
@@ -840,7 +858,7 @@ __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSm
       if (CG)
         __stcg(a.q + idx, s.buf0[cc * CP + row]);
       else
-        a.out[idx] = s.buf0[cc * CP + row];
+        a.out[idx] = negate_if(s.buf0[cc * CP + row], a.centred && ((row + xx) & 1));
     }
   }
   return part;
@@ -895,6 +913,7 @@ struct NormalArgs {
   const int* lines;
   const float2* tw;
   int nx, coils, L, tiles, p_update;
+  int centred;                 // CG=false: centred k-space (see NormalTile)
   int* err;
   CgState cg;
 };
@@ -927,6 +946,7 @@ __global__ void __launch_bounds__(TH, MINB) k_normal(NormalArgs<St> a) {
   t.coils = a.coils;
   t.tile = blockIdx.x;
   t.p_update = a.p_update;
+  t.centred = CG ? 0 : a.centred;
   t.beta = (CG && a.p_update) ? (float)__ldg(a.cg.beta + f) : 0.f;
   float part;
   double* red;

@@ -120,6 +120,8 @@ sense_status noalloc_adjoint(const sense_shape& sh, const DeviceTables& t, const
   ra.out = t.scratch;
   ra.tw = t.twiddles + twiddle_offset(sh.nx);
   ra.rows = (long)sh.frames * sh.coils * sh.lines;
+  ra.centred = sh.centred;
+  ra.cs = ((sh.ny / 2 + sh.nx / 2) & 1) ? -1.0f : 1.0f;
   cudaError_t e = launch_rows_inv<St>(sh.nx, ra, st);
   if (e != cudaSuccess) {
     *msg = std::string("adjoint row pass: ") + cudaGetErrorString(e);
@@ -137,6 +139,7 @@ sense_status noalloc_adjoint(const sense_shape& sh, const DeviceTables& t, const
   a.coils = sh.coils;
   a.L = sh.lines;
   a.tiles = tiles;
+  a.centred = sh.centred;
   a.err = t.err;
   e = launch_adj_col<St>(sh.ny, 0, a, tiles, sh.frames, st);
   if (e != cudaSuccess) {
@@ -162,6 +165,7 @@ extern "C" sense_status sense_adjoint_noalloc(const sense_shape* shape, const vo
     return done(SENSE_EINVAL, "need frames in [1, 65535], coils >= 1, lines in [1, ny]");
   if (sh.storage != SENSE_STORE_C64 && sh.storage != SENSE_STORE_BF16)
     return done(SENSE_EINVAL, "storage must be SENSE_STORE_C64 or SENSE_STORE_BF16");
+  if (sh.centred != 0 && sh.centred != 1) return done(SENSE_EINVAL, "centred must be 0 or 1");
   if (!size_supported(sh.ny) || !size_supported(sh.nx))
     return done(SENSE_EUNSUPPORTED_SIZE, "no compiled transform for this ny / nx");
   const size_t need = (size_t)sh.frames * sh.coils * sh.lines * sh.nx;

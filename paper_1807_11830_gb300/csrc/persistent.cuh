@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
         nt.coils = fr.coils;
         nt.tile = piece;
         nt.p_update = kg > 0 ? 1 : 0;
+        nt.centred = 0;
         nt.beta = kg > 0 ? (float)__ldcg(fr.beta) : 0.f;
         const float part = tile.run(nt, keep, nfill, a.err);
         nfill += (unsigned)fr.coils;

@@ -125,6 +125,10 @@ sense_status plan_maps_buffer(sense_plan* pl);
 sense_status plan_maps(sense_plan* pl, const void* S, cudaStream_t st, const void** out);
 bool plan_maps_transposed(const sense_plan* pl);
 
+// Centred plans: map a finished CG solution x (all frames) from the
+// modulated space the iterations run in back to the image, on `st`.
+sense_status plan_centred_output(sense_plan* pl, float2* x, cudaStream_t st);
+
 // Per-frame outputs of a finished CG solve of a plan (iterations, residual,
 // outcome; NULL outputs are skipped).
 sense_status plan_cg_finish(sense_plan* pl, int* iters_out, double* resid_out, int* outcome_out, cudaStream_t st);

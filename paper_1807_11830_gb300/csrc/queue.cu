@@ -334,6 +334,7 @@ bool retire_enqueue(sense_queue* q, Request* r) {
   const size_t F = r->sh.frames;
   cudaStream_t st = q->stream;
   bool ok = plan_cg_finish(r->plan, r->out_i_d, r->resid_d, r->out_i_d + F, st) == SENSE_OK;
+  ok = ok && plan_centred_output(r->plan, r->x_d, st) == SENSE_OK;
   ok = ok && cudaMemcpyAsync(r->x_h, r->x_d, r->x_bytes, cudaMemcpyDeviceToHost, st) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(r->iters_h, r->out_i_d, sizeof(int) * F, cudaMemcpyDeviceToHost, st) == cudaSuccess;
   ok = ok && cudaMemcpyAsync(r->outcome_h, r->out_i_d + F, sizeof(int) * F, cudaMemcpyDeviceToHost, st) ==
@@ -599,6 +600,7 @@ sense_status sense_queue_submit(sense_queue* q, const sense_shape* shape, const 
   if (sh.frames < 1 || sh.coils < 1 || sh.lines < 1 || sh.lines > sh.ny || max_iter < 1 || !(rel_tol >= 0.0))
     return qfail(SENSE_EINVAL, "bad shape, max_iter or rel_tol");
   if (sh.storage != SENSE_STORE_C64 && sh.storage != SENSE_STORE_BF16) return qfail(SENSE_EINVAL, "bad storage");
+  if (sh.centred != 0 && sh.centred != 1) return qfail(SENSE_EINVAL, "centred must be 0 or 1");
   if (!sense_size_supported(sh.ny) || !sense_size_supported(sh.nx))
     return qfail(SENSE_EUNSUPPORTED_SIZE, "no compiled transform for this ny / nx");
   Request* r = new Request();

@@ -167,6 +167,16 @@ sense_status plan_maps(sense_plan* pl, const void* S, cudaStream_t st, const voi
   return SENSE_OK;
 }
 
+sense_status plan_centred_output(sense_plan* pl, float2* x, cudaStream_t st) {
+  const sense_shape& sh = pl->sh;
+  if (!sh.centred) return SENSE_OK;
+  const long n = (long)sh.frames * (long)pl->img;
+  k_checkerboard<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, sh.ny, sh.nx, n);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(SENSE_ECUDA, std::string("centred output: ") + cudaGetErrorString(e));
+  return SENSE_OK;
+}
+
 }  // namespace sense
 
 namespace {
@@ -201,8 +211,12 @@ sense_status check_shape(const sense_shape* sh) {
   if (!size_supported(sh->ny) || !size_supported(sh->nx))
     return fail(SENSE_EUNSUPPORTED_SIZE, "no compiled transform for ny=" + std::to_string(sh->ny) +
                                              " / nx=" + std::to_string(sh->nx));
+  if (sh->centred != 0 && sh->centred != 1) return fail(SENSE_EINVAL, "centred must be 0 or 1");
   return SENSE_OK;
 }
+
+// (-1)^(ny/2 + nx/2): the constant of the centred 2D transform
+float centred_sign(const sense_shape& sh) { return ((sh.ny / 2 + sh.nx / 2) & 1) ? -1.0f : 1.0f; }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
@@ -226,6 +240,7 @@ sense_status run_forward(sense_plan* pl, const float2* x, const void* S, const i
   a.nx = sh.nx;
   a.coils = sh.coils;
   a.L = sh.lines;
+  a.centred = sh.centred;
   a.err = pl->err();
   sense_status rc;
   {
@@ -238,6 +253,8 @@ sense_status run_forward(sense_plan* pl, const float2* x, const void* S, const i
   ra.out = static_cast<typename St::T*>(y);
   ra.tw = pl->tw_x;
   ra.rows = (long)sh.frames * sh.coils * sh.lines;
+  ra.centred = sh.centred;
+  ra.cs = centred_sign(sh);
   PhaseScope ps(pl, SENSE_PHASE_ROWS_FWD, st);
   return launch_status(launch_rows_fwd<St>(sh.nx, ra, st), "forward row pass");
 }
@@ -250,6 +267,8 @@ sense_status run_rows_inv(sense_plan* pl, const void* y, cudaStream_t st) {
   ra.out = pl->tmp;
   ra.tw = pl->tw_x;
   ra.rows = (long)sh.frames * sh.coils * sh.lines;
+  ra.centred = sh.centred;
+  ra.cs = centred_sign(sh);
   PhaseScope ps(pl, SENSE_PHASE_ROWS_INV, st);
   return launch_status(launch_rows_inv<St>(sh.nx, ra, st), "adjoint row pass");
 }
@@ -270,6 +289,7 @@ sense_status run_adjoint(sense_plan* pl, int mode, const void* y, const void* S,
     a.coils = sh.coils;
     a.L = sh.lines;
     a.tiles = pl->tiles;
+    a.centred = sh.centred;
     a.err = pl->err();
     PhaseScope ps(pl, SENSE_PHASE_ADJ_COL, st);
     return launch_status(launch_adj_col<StC64>(sh.ny, 2, a, pl->tiles, sh.frames, st), "rss column pass");
@@ -286,6 +306,7 @@ sense_status run_adjoint(sense_plan* pl, int mode, const void* y, const void* S,
   a.coils = sh.coils;
   a.L = sh.lines;
   a.tiles = pl->tiles;
+  a.centred = sh.centred;  // mode 1 (CG start) works in the modulated space: no image signs there
   a.err = pl->err();
   a.cg = pl->cg(tol);
   PhaseScope ps(pl, SENSE_PHASE_ADJ_COL, st);
@@ -309,6 +330,7 @@ sense_status run_normal(sense_plan* pl, const float2* x, const void* S, const in
   a.coils = sh.coils;
   a.L = sh.lines;
   a.tiles = pl->norm_tiles;
+  a.centred = sh.centred;
   a.err = pl->err();
   PhaseScope ps(pl, SENSE_PHASE_NORMAL, st);
   return launch_status(launch_normal<St>(sh.ny, pl->norm_variant, false, a, sh.frames, st), "normal operator");
@@ -509,6 +531,8 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
   if (pl->cg_mode == 1) {
     if (max_iter > 0) rc = run_cg_persistent<St>(pl, maps, lines, x, max_iter, tol, st);
     if (rc != SENSE_OK) return rc;
+    rc = plan_centred_output(pl, x, st);
+    if (rc != SENSE_OK) return rc;
     PhaseScope ps(pl, SENSE_PHASE_CG_FINISH, st);
     k_cg_finish<<<(sh.frames + 127) / 128, 128, 0, st>>>(pl->cg(tol), sh.frames, iters_out, resid_out, outcome_out);
     return launch_status(cudaGetLastError(), "CG finish");
@@ -534,6 +558,8 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
       if (*pl->live_host <= 0) break;
     }
   }
+  rc = plan_centred_output(pl, x, st);
+  if (rc != SENSE_OK) return rc;
   PhaseScope ps(pl, SENSE_PHASE_CG_FINISH, st);
   k_cg_finish<<<(sh.frames + 127) / 128, 128, 0, st>>>(pl->cg(tol), sh.frames, iters_out, resid_out, outcome_out);
   return launch_status(cudaGetLastError(), "CG finish");

@@ -56,7 +56,15 @@ class SenseError(RuntimeError):
 
 class _Shape(ctypes.Structure):
     _fields_ = [("ny", ctypes.c_int), ("nx", ctypes.c_int), ("coils", ctypes.c_int),
-                ("frames", ctypes.c_int), ("lines", ctypes.c_int), ("storage", ctypes.c_int)]
+                ("frames", ctypes.c_int), ("lines", ctypes.c_int), ("storage", ctypes.c_int),
+                ("centred", ctypes.c_int)]
+
+
+def _shape_struct(d):
+    """sense_shape from a dict with ny, nx, coils, frames, lines and
+    optionally storage (default complex64) and centred (default 0)."""
+    return _Shape(d["ny"], d["nx"], d["coils"], d["frames"], d["lines"], d.get("storage", STORE_C64),
+                  int(d.get("centred", 0)))
 
 
 class _BatchIO(ctypes.Structure):
@@ -192,12 +200,13 @@ def sense_size_supported(n):
 class Plan:
     """Owns a ``sense_plan*`` (twiddles + workspace) for one problem shape."""
 
-    def __init__(self, ny, nx, coils, frames, lines, storage=STORE_C64, device=0):
+    def __init__(self, ny, nx, coils, frames, lines, storage=STORE_C64, device=0, centred=False):
         lib = load_library()
-        self.shape = dict(ny=ny, nx=nx, coils=coils, frames=frames, lines=lines, storage=storage)
+        self.shape = dict(ny=ny, nx=nx, coils=coils, frames=frames, lines=lines, storage=storage,
+                          centred=int(centred))
         self.device = device
         h = ctypes.c_void_p()
-        sh = _Shape(ny, nx, coils, frames, lines, storage)
+        sh = _Shape(ny, nx, coils, frames, lines, storage, int(centred))
         _check(lib.sense_plan_create(ctypes.byref(sh), device, ctypes.byref(h)))
         self.handle = h
 
@@ -238,9 +247,8 @@ def sense_adjoint(plan, y, S, lines, x, stream=None):
 def sense_adjoint_noalloc(shape, y, S, lines, x, stream=None):
     """Adjoint without a plan and without device allocation (fixed-size
     library scratch; see include/sense.h).  `shape` is a dict with ny, nx,
-    coils, frames, lines and optionally storage."""
-    sh = _Shape(shape["ny"], shape["nx"], shape["coils"], shape["frames"], shape["lines"],
-                shape.get("storage", STORE_C64))
+    coils, frames, lines and optionally storage and centred."""
+    sh = _shape_struct(shape)
     _check(load_library().sense_adjoint_noalloc(ctypes.byref(sh), _ptr(y), _ptr(S), _ptr(lines), _ptr(x),
                                                 _stream(stream)))
     return x
@@ -324,8 +332,7 @@ class Batch:
 
     def __init__(self, shapes, device=0):
         lib = load_library()
-        arr = (_Shape * len(shapes))(*[_Shape(d["ny"], d["nx"], d["coils"], d["frames"], d["lines"],
-                                               d.get("storage", STORE_C64)) for d in shapes])
+        arr = (_Shape * len(shapes))(*[_shape_struct(d) for d in shapes])
         h = ctypes.c_void_p()
         _check(lib.sense_batch_create(arr, len(shapes), device, ctypes.byref(h)))
         self.handle = h
@@ -416,8 +423,7 @@ class Queue:
         self.handle = h
 
     def submit(self, shape, y, S, lines, max_iter, rel_tol=0.0):
-        sh = _Shape(shape["ny"], shape["nx"], shape["coils"], shape["frames"], shape["lines"],
-                    shape.get("storage", STORE_C64))
+        sh = _shape_struct(shape)
         rid = ctypes.c_uint64()
         _check(load_library().sense_queue_submit(self.handle, ctypes.byref(sh), _np_ptr(y), _np_ptr(S),
                                                  _np_ptr(lines), int(max_iter), float(rel_tol), ctypes.byref(rid)))

@@ -127,6 +127,12 @@ def full_lines(ny, frames):
     return np.tile(np.arange(ny, dtype=np.int32), (frames, 1))
 
 
+def centred_lines(lines, ny):
+    """The same sampled frequencies in centred k-space indexing (DC at ny/2):
+    row k becomes (k + ny/2) mod ny, sorted per frame."""
+    return np.sort((np.asarray(lines, np.int64) + ny // 2) % ny, axis=1).astype(np.int32)
+
+
 def complex_noise(shape, sigma, rng):
     s = sigma / np.sqrt(2.0)
     return rng.normal(0.0, s, size=shape) + 1j * rng.normal(0.0, s, size=shape)
