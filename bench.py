@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--serve-requests", type=int, default=160)
     ap.add_argument("--cg-mode", default="auto", choices=("auto", "graph", "persistent"),
                     help="CG iteration scheme; 'auto' times both briefly and keeps the faster")
+    ap.add_argument("--centred", action="store_true",
+                    help="centred k-space convention (DC at n/2) for the cine and paper workloads")
     ap.add_argument("--normal-variant", default="auto",
                     help="normal-operator kernel variant, or 'auto' for the library's autotuner")
     return ap.parse_args()
@@ -110,10 +112,11 @@ def shard_instances(specs, world, rank):
     return [i for i in range(len(specs)) if owner[i] == rank]
 
 
-def base_config(world):
+def base_config(world, centred=False):
     return {
-        "workload": WORKLOAD, "ny": N, "nx": N, "frames": FRAMES, "coils": COILS, "lines": N // ACCEL,
-        "centre_lines": CENTRE, "cg_iterations": ITERS, "storage": "complex64",
+        "workload": WORKLOAD + (", centred k-space" if centred else ""), "ny": N, "nx": N, "frames": FRAMES,
+        "coils": COILS, "lines": N // ACCEL, "centre_lines": CENTRE, "cg_iterations": ITERS, "storage": "complex64",
+        "kspace": "centred (DC at n/2)" if centred else "uncentred (DC at 0)",
         "l2": "flushed before every timed step (512 MiB device write)",
         "parallelism": "replicas x%d (independent problems, no collective)" % world,
     }
@@ -125,29 +128,30 @@ def base_config(world):
 _ORACLE_INPUTS = {}
 
 
-def oracle_inputs():
+def oracle_inputs(centred=False):
     """k-space of the whole workload made once by the oracle's E (untimed)."""
     if not _ORACLE_INPUTS:
         import oracle
         from paper_1807_11830_gb300 import synth
 
         p = synth.cine_256(frames=FRAMES)
+        lines = synth.centred_lines(p.lines, N) if centred else p.lines
         S = p.S.astype(np.complex64).astype(np.complex128)
-        y = oracle.forward(p.x_true.astype(np.complex64), S, p.lines) + p.noise
-        _ORACLE_INPUTS.update(y=y, S=S, lines=p.lines)
+        y = oracle.forward(p.x_true.astype(np.complex64), S, lines, centred=centred) + p.noise
+        _ORACLE_INPUTS.update(y=y, S=S, lines=lines, centred=centred)
     return _ORACLE_INPUTS
 
 
-def oracle_sample(frames, iters, seed_offset=0):
+def oracle_sample(frames, iters, seed_offset=0, centred=False):
     """Time oracle CG-SENSE on `frames` frames of the workload for `iters`
     iterations.  Returns (applications/s, wall seconds, threads)."""
     import oracle
 
-    d = oracle_inputs()
+    d = oracle_inputs(centred)
     sel = [(i + seed_offset) % FRAMES for i in range(frames)]
     y, S, lines = d["y"][sel], d["S"], d["lines"][sel]
     t0 = time.perf_counter()
-    oracle.cg(y, S, lines, iters)
+    oracle.cg(y, S, lines, iters, centred=d["centred"])
     wall = time.perf_counter() - t0
     return frames * iters / wall, wall, min(oracle.threads(), frames)
 
@@ -164,11 +168,11 @@ def run_reference(args):
     frames = max(1, min(FRAMES, threads))
     iters = 2
     for _ in range(args.warmup):
-        oracle_sample(frames, 1)
+        oracle_sample(frames, 1, centred=args.centred)
     walls = []
     apps = 0
     for k in range(args.steps):
-        _, wall, _ = oracle_sample(frames, iters, seed_offset=k)
+        _, wall, _ = oracle_sample(frames, iters, seed_offset=k, centred=args.centred)
         walls.append(wall)
         apps += frames * iters
     total = sum(walls)
@@ -178,7 +182,7 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": base_config(1),
+        "config": base_config(1, args.centred),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(threads, frames), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -284,8 +288,9 @@ def run_ours(args):
     L = p.lines.shape[1]
     x_true = torch.from_numpy(p.x_true.astype(np.complex64)).to(dev)
     S = torch.from_numpy(p.S.astype(np.complex64)).to(dev)
-    lines = torch.from_numpy(p.lines).to(dev)
-    plan = sense.Plan(N, N, COILS, FRAMES, L, device=local_rank)
+    lines_np = synth.centred_lines(p.lines, N) if args.centred else p.lines
+    lines = torch.from_numpy(lines_np).to(dev)
+    plan = sense.Plan(N, N, COILS, FRAMES, L, device=local_rank, centred=args.centred)
     y = torch.empty((FRAMES, COILS, L, N), dtype=torch.complex64, device=dev)
     sense.sense_forward(plan, x_true, S, lines, y)
     y += torch.from_numpy(p.noise.astype(np.complex64)).to(dev)
@@ -445,7 +450,7 @@ def run_ours(args):
         if world == 1 and not args.no_cpu_baseline:
             import oracle
             frames = max(1, min(FRAMES, oracle.threads()))
-            v, wall, cores = oracle_sample(frames, args.cpu_sample_iters)
+            v, wall, cores = oracle_sample(frames, args.cpu_sample_iters, centred=args.centred)
             cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "%d of %d frames x %d CG iterations (full 256x256, 12 coils, R=4), %.1f s"
                              % (frames, FRAMES, args.cpu_sample_iters, wall)}
@@ -455,7 +460,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": base_config(world),
+            "config": base_config(world, args.centred),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_ms / args.steps},
             "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -689,7 +694,7 @@ def run_serve(args):
 _PAPER_ORACLE = {}
 
 
-def paper_oracle_inputs():
+def paper_oracle_inputs(centred=False):
     """k-space of the paper workload made once by the oracle's E (untimed)."""
     if not _PAPER_ORACLE:
         import oracle
@@ -697,20 +702,20 @@ def paper_oracle_inputs():
 
         p = synth.paper_160()
         S = p.S.astype(np.complex64).astype(np.complex128)
-        y = oracle.forward(p.x_true.astype(np.complex64), S, p.lines) + p.noise
-        _PAPER_ORACLE.update(y=y, lines=p.lines, n=p.x_true.shape[1])
+        y = oracle.forward(p.x_true.astype(np.complex64), S, p.lines, centred=centred) + p.noise
+        _PAPER_ORACLE.update(y=y, lines=p.lines, n=p.x_true.shape[1], centred=centred)
     return _PAPER_ORACLE
 
 
-def paper_oracle_sample(min_seconds):
+def paper_oracle_sample(min_seconds, centred=False):
     """Oracle FFT + RSS reconstructions of the whole workload, repeated for at
     least `min_seconds`.  Returns (reconstructions/s, wall, count, threads)."""
     import oracle
 
-    d = paper_oracle_inputs()
+    d = paper_oracle_inputs(centred)
     count, t0 = 0, time.perf_counter()
     while True:
-        oracle.rss(d["y"], d["lines"], d["n"])
+        oracle.rss(d["y"], d["lines"], d["n"], centred=d["centred"])
         count += 1
         wall = time.perf_counter() - t0
         if wall >= min_seconds:
@@ -719,10 +724,10 @@ def paper_oracle_sample(min_seconds):
 
 def run_reference_paper(args):
     for _ in range(args.warmup):
-        paper_oracle_sample(0.0)
+        paper_oracle_sample(0.0, args.centred)
     walls, count = [], 0
     for _ in range(args.steps):
-        _, wall, c, threads = paper_oracle_sample(0.0)
+        _, wall, c, threads = paper_oracle_sample(0.0, args.centred)
         walls.append(wall)
         count += c
     value = count / sum(walls)
@@ -730,7 +735,8 @@ def run_reference_paper(args):
         "metric": PAPER_METRIC, "value": value, "unit": PAPER_UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": PAPER_WORKLOAD, "ny": 160, "nx": 160, "frames": 16, "coils": 8},
+        "config": {"workload": PAPER_WORKLOAD + (", centred k-space" if args.centred else ""), "ny": 160, "nx": 160,
+                   "frames": 16, "coils": 8},
         "cpu_baseline": {"value": value, "unit": PAPER_UNIT, "cores": threads, "kind": "oracle",
                          "sample": "one whole reconstruction (16 frames x 8 coils) per step"},
         "e2e": {"value": value, "unit": PAPER_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -756,7 +762,7 @@ def run_paper(args):
 
     p = synth.paper_160()
     F, C, n = p.x_true.shape[0], p.S.shape[0], p.x_true.shape[1]
-    plan = sense.Plan(n, n, C, F, n, device=local_rank)
+    plan = sense.Plan(n, n, C, F, n, device=local_rank, centred=args.centred)
     x_true = torch.from_numpy(p.x_true.astype(np.complex64)).to(dev)
     S = torch.from_numpy(p.S.astype(np.complex64)).to(dev)
     lines = torch.from_numpy(p.lines).to(dev)
@@ -864,7 +870,7 @@ def run_paper(args):
         }
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            v, wall, cnt, threads = paper_oracle_sample(10.0)
+            v, wall, cnt, threads = paper_oracle_sample(10.0, args.centred)
             cpu = {"value": v, "unit": PAPER_UNIT, "cores": threads, "kind": "oracle",
                    "sample": "%d whole reconstructions (16 frames x 8 coils, FP64), %.1f s" % (cnt, wall)}
         paper_value = 1e3 / PAPER_GTX970_MS
@@ -872,7 +878,8 @@ def run_paper(args):
             "metric": PAPER_METRIC, "value": value, "unit": PAPER_UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": value / paper_value, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": PAPER_WORKLOAD, "ny": n, "nx": n, "frames": F, "coils": C,
+            "config": {"workload": PAPER_WORKLOAD + (", centred k-space" if args.centred else ""), "ny": n, "nx": n,
+                       "frames": F, "coils": C, "kspace": "centred (DC at n/2)" if args.centred else "uncentred (DC at 0)",
                        "l2": "flushed before every timed step (512 MiB device write)",
                        "parallelism": "replicas x%d (independent problems, no collective)" % world},
             "baseline_context": "OpenCLIPER on a GTX 970, clFFT 1.361 ms + RSS 0.252 ms (Table II): "

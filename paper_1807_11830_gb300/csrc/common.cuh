@@ -49,13 +49,21 @@ template <> struct Cfg<8> { using C = Col<2, 16, Radices<4, 2>>; };
 template <> struct Cfg<12> { using C = Col<4, 16, Radices<4, 3>>; };
 template <> struct Cfg<16> { using C = Col<4, 16, Radices<4, 4>>; };
 template <> struct Cfg<20> { using C = Col<4, 16, Radices<5, 4>>; };
+template <> struct Cfg<24> { using C = Col<4, 16, Radices<4, 6>>; };
 template <> struct Cfg<32> { using C = Col<4, 32, Radices<8, 4>>; };
+template <> struct Cfg<40> { using C = Col<8, 16, Radices<5, 8>>; };
+template <> struct Cfg<48> { using C = Col<8, 16, Radices<6, 8>>; };
 template <> struct Cfg<64> { using C = Col<8, 32, Radices<8, 8>>; };
+template <> struct Cfg<80> { using C = Col<10, 16, Radices<8, 10>>; };
 template <> struct Cfg<96> { using C = Col<24, 16, Radices<4, 4, 6>>; };
+template <> struct Cfg<120> { using C = Col<12, 16, Radices<10, 12>>; };
 template <> struct Cfg<128> { using C = Col<16, 16, Radices<8, 4, 4>>; };
+template <> struct Cfg<144> { using C = Col<12, 16, Radices<12, 12>>; };
 template <> struct Cfg<160> { using C = Col<20, 16, Radices<8, 4, 5>>; };
 template <> struct Cfg<192> { using C = Col<24, 16, Radices<8, 3, 8>>; };
+template <> struct Cfg<240> { using C = Col<16, 16, Radices<15, 16>>; };
 template <> struct Cfg<256> { using C = Col<32, 16, Radices<8, 4, 8>>; };
+template <> struct Cfg<288> { using C = Col<24, 16, Radices<6, 6, 8>>; };
 template <> struct Cfg<320> { using C = Col<40, 16, Radices<8, 4, 10>>; };
 template <> struct Cfg<384> { using C = Col<48, 16, Radices<8, 4, 12>>; };
 
@@ -90,8 +98,9 @@ SENSE_NORM_VARIANT(384, 2, 2, Col<48, 8, Radices<8, 4, 12>>)
 #undef SENSE_NORM_VARIANT
 constexpr int kNormVariants = 4;
 
-#define SENSE_FOR_EACH_SIZE(X) \
-  X(8) X(12) X(16) X(20) X(32) X(64) X(96) X(128) X(160) X(192) X(256) X(320) X(384)
+#define SENSE_FOR_EACH_SIZE(X)                                                                     \
+  X(8) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64) X(80) X(96) X(120) X(128) X(144) X(160) X(192) \
+  X(240) X(256) X(288) X(320) X(384)
 
 // ---------------------------------------------------------------------------
 // FP64 block sum; the result is valid in thread 0.  Fixed shuffle tree and a

@@ -322,10 +322,11 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St>
       accr[j][n] = 0.f;
     }
 
-  // With blocks of up to 256 threads (registers to spare at two blocks per
-  // SM), coil c + 1's k-space values and maps are loaded into registers
-  // before coil c is transformed, so their latency overlaps the transform.
-  constexpr bool PREFETCH = C::THREADS <= 256;
+  // With blocks of up to 256 threads and at most 24 values per thread per
+  // side (registers to spare at two blocks per SM), coil c + 1's k-space
+  // values and maps are loaded into registers before coil c is transformed,
+  // so their latency overlaps the transform.
+  constexpr bool PREFETCH = C::THREADS <= 256 && C::J0 * C::R0 + C::JL * C::RL <= 24;
   auto load_k = [&](int c, float2 (&kv)[C::JL][C::RL]) {
     const float2* src = a.tmp + ((size_t)f * a.coils + c) * a.L * a.nx;
 #pragma unroll
@@ -333,8 +334,7 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St>
 #pragma unroll
       for (int m = 0; m < C::RL; ++m) {
         const int l = (col.okL(j) && xin) ? (int)s.map[col.krow(j, m)] : -1;
-        kv[j][m] = l >= 0 ? negate_if(__ldg(src + (size_t)l * a.nx + x), a.centred && (col.krow(j, m) & 1))
-                          : make_float2(0.f, 0.f);
+        kv[j][m] = l >= 0 ? __ldg(src + (size_t)l * a.nx + x) : make_float2(0.f, 0.f);
       }
   };
   auto load_s = [&](int c, float2 (&sv)[C::J0][C::R0]) {
@@ -372,6 +372,12 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St>
     } else {
       load_k(c, kr);
       load_s(c, sv);
+    }
+    if (a.centred) {  // k-space rows by (-1)^ky, once the values are in registers
+#pragma unroll
+      for (int j = 0; j < C::JL; ++j)
+#pragma unroll
+        for (int m = 0; m < C::RL; ++m) kr[j][m] = negate_if(kr[j][m], col.krow(j, m) & 1);
     }
     const BufPair<C> bp(s.buf0, s.buf1, c);
     col.inv(kr, xr, bp.b, s.tw);

@@ -42,6 +42,8 @@ EXPORTED = (
 )
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = 0, 1, 2, 3, 4
 NORM_VARIANTS = 4
+# transform lengths compiled into the library (ny and nx each; sense_size_supported)
+SIZES = (8, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192, 240, 256, 288, 320, 384)
 
 PHASES = ("rows_fwd", "rows_inv", "fwd_col", "adj_col", "normal", "cg_normal", "cg_update", "cg_persistent",
           "maps_transpose", "cg_finish")

@@ -48,10 +48,10 @@ def test_binding_covers_every_declared_symbol():
 
 def test_size_table_is_host_only(lib):
     lib.sense_size_supported.restype = ctypes.c_int
-    for n in (8, 12, 16, 20, 32, 64, 96, 128, 160, 192, 256, 320, 384):
+    for n in sense.SIZES:
         assert lib.sense_size_supported(n) == 1
-    for n in (0, 7, 100, 512, 1000):
-        assert lib.sense_size_supported(n) == 0
+    for n in range(0, 1025):
+        assert lib.sense_size_supported(n) == (1 if n in sense.SIZES else 0), n
 
 
 def test_null_arguments_rejected_without_device(lib):

@@ -40,6 +40,12 @@ OP_SHAPES = [
     (384, 384, 3, 64, 1),
     (256, 320, 3, 50, 1),
     (384, 8, 2, 96, 1),
+    (24, 40, 2, 9, 2),
+    (48, 80, 3, 17, 1),
+    (120, 144, 4, 41, 1),
+    (144, 120, 3, 48, 2),
+    (240, 288, 2, 80, 1),
+    (288, 240, 3, 96, 1),
 ]
 
 
@@ -343,7 +349,7 @@ def test_bounded_wait_gives_up_and_device_stays_usable():
     assert list(ig) == [3]
 
 
-@pytest.mark.parametrize("n", [8, 12, 16, 20, 32, 64, 96, 128, 160, 192, 256, 320, 384])
+@pytest.mark.parametrize("n", sense.SIZES)
 def test_cg_persistent_every_length(n):
     """Persistent CG (maps staged into shared memory by TMA) at every
     compiled length, including tiles wider than the image (nx < 16)."""

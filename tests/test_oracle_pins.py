@@ -19,7 +19,7 @@ import oracle
 from paper_1807_11830_gb300 import synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-SIZES = [1, 2, 3, 4, 5, 6, 8, 12, 15, 16, 20, 64, 128, 160, 192, 256, 320, 384]
+SIZES = [1, 2, 3, 4, 5, 6, 8, 12, 15, 16, 20, 24, 40, 48, 64, 80, 120, 128, 144, 160, 192, 240, 256, 288, 320, 384]
 
 
 def rel(a, b):
