@@ -322,10 +322,11 @@ int orc_normal_collapsed(int F, int C, int ny, int nx, int L, const double* x, c
 // Per-frame CG status values written to status[f].
 enum { ORC_CG_RUNNING = 0, ORC_CG_CONVERGED = 1, ORC_CG_MAXITER = 2, ORC_CG_BREAKDOWN = 3 };
 
-// Hestenes-Stiefel CG on (E^H E) x = E^H y, independently for every frame:
+// Hestenes-Stiefel CG on (E^H E + lambda I) x = E^H y, independently for
+// every frame (lambda >= 0 is Tikhonov regularisation; 0 gives CG-SENSE):
 //   b = E^H y; x0 = 0; r0 = b; p0 = r0; rho0 = <r0, r0>
 //   for k = 0 .. max_iter-1:
-//     q = E^H E p;  alpha = rho_k / Re<p, q>
+//     q = E^H E p + lambda p;  alpha = rho_k / Re<p, q>
 //     x += alpha p;  r -= alpha q;  rho_{k+1} = <r, r>
 //     stop if rho_{k+1} == 0, or tol > 0 and sqrt(rho_{k+1}/rho0) <= tol
 //     beta = rho_{k+1} / rho_k;  p = r + beta p
@@ -335,8 +336,9 @@ enum { ORC_CG_RUNNING = 0, ORC_CG_CONVERGED = 1, ORC_CG_MAXITER = 2, ORC_CG_BREA
 // Outputs: x [F][ny][nx]; iters[f] = iterations applied; resid[f] =
 // sqrt(rho/rho0) at exit (0 when rho0 == 0); status[f] as above.
 int orc_cg(int F, int C, int ny, int nx, int L, const double* y, const double* S, const int* lines, int max_iter,
-           double tol, double* x, int* iters, double* resid, int* status, int centred) {
-  if (F < 0 || C <= 0 || ny <= 0 || nx <= 0 || L < 0 || L > ny || max_iter < 0 || !(tol >= 0.0))
+           double tol, double* x, int* iters, double* resid, int* status, int centred, double lambda) {
+  if (F < 0 || C <= 0 || ny <= 0 || nx <= 0 || L < 0 || L > ny || max_iter < 0 || !(tol >= 0.0) ||
+      !(lambda >= 0.0))
     return ORC_EINVAL;
   if (!all_lines_ok(F, ny, L, lines)) return ORC_EINVAL;
   long npix = (long)ny * nx;
@@ -357,6 +359,7 @@ int orc_cg(int F, int C, int ny, int nx, int L, const double* y, const double* S
     if (rho0 == 0.0) st = ORC_CG_CONVERGED;
     while (st == ORC_CG_RUNNING && it < max_iter) {
       normal_frame(C, ny, nx, L, p.data(), Sc, ln, q.data(), centred != 0);
+      for (long i = 0; i < npix; ++i) q[i] += lambda * p[i];
       double pq = re_dot(npix, p.data(), q.data());
       if (!(pq > 0.0)) { st = ORC_CG_BREAKDOWN; break; }
       double alpha = rho / pq;

@@ -42,6 +42,8 @@ MUTANTS = {
     # direct DFT index slip
     "dft_index": ("in[(long)j * stride] * unit_root((long long)j * k, n, dir)",
                   "in[(long)j * stride] * unit_root((long long)j * (k + 1), n, dir)"),
+    # Tikhonov term with the wrong sign
+    "cg_lambda_sign": ("q[i] += lambda * p[i];", "q[i] -= lambda * p[i];"),
     # centred transform forgets the output fftshift
     "centred_no_fftshift": ("  if (centred) rotate_strided(n, v, stride, n / 2);  // fftshift\n", "\n"),
     # centred transform shifts the input the wrong way (differs for odd n)
@@ -62,6 +64,7 @@ QUICK_PINS = [
     pins.test_bf16_rne_hand_cases,
     lambda: [centred.test_centred_fft2_brute_force(*sh) for sh in [(3, 5), (4, 6), (7, 7)]],
     lambda: centred.test_centred_adjoint_identity_and_full_sampling((16, 12, 3, 7, 2)),
+    lambda: pins.test_regularised_cg_against_dense_solves(0.0625),
 ]
 
 

@@ -264,6 +264,43 @@ def test_cg_against_dense_krylov_solves():
     assert rel(A @ xc.ravel(), b) <= 1e-10
 
 
+@pytest.mark.parametrize("lam", [0.0625, 1.5])
+def test_regularised_cg_against_dense_solves(lam):
+    """Tikhonov-regularised CG solves (A + lam I) x = b with A = E^H E built
+    densely: each iterate is the (A + lam I)-norm minimiser over the Krylov
+    space of A + lam I, and the converged iterate is the dense solve (the
+    shifted matrix is positive definite, so the solution is unique)."""
+    ny = nx = 8
+    rng = synth.rng_for(62)
+    S = synth.random_complex((3, ny, nx), rng)
+    lines = synth.mask_lines(ny, 4, 2, 1, rng)
+    y = synth.random_complex((1, 3, 4, nx), rng)
+    A = _dense_normal(S, lines, ny, nx) + lam * np.eye(ny * nx)
+    b = oracle.adjoint(y, S, lines).ravel()
+    for k in (1, 3, 6):
+        K = np.stack([np.linalg.matrix_power(A, i) @ b for i in range(k)], axis=1)
+        Q, _ = np.linalg.qr(K)
+        xk_dense = Q @ np.linalg.solve(Q.conj().T @ A @ Q, Q.conj().T @ b)
+        xk, iters, _, _ = oracle.cg(y, S, lines, max_iter=k, lam=lam)
+        assert iters[0] == k
+        assert rel(xk.ravel(), xk_dense) <= 1e-8, k
+    xc, _, _, status = oracle.cg(y, S, lines, max_iter=300, tol=1e-13, lam=lam)
+    assert rel(xc.ravel(), np.linalg.solve(A, b)) <= 1e-9
+
+
+def test_regularised_cg_limits():
+    x, S, lines, y = _small_problem(16, 16, 3, 6, 2, 73)
+    # lam = 0 is plain CG-SENSE
+    a = oracle.cg(y, S, lines, 5)
+    b = oracle.cg(y, S, lines, 5, lam=0.0)
+    assert rel(a[0], b[0]) == 0.0
+    # a dominant lam: one step gives x = (rho0 / (rho0 lam + <b, A b>)) b -> b / lam
+    lam = 1e8
+    xb = oracle.adjoint(y, S, lines)
+    x1, _, _, _ = oracle.cg(y, S, lines, 1, lam=lam)
+    assert rel(x1 * lam, xb) <= 1e-7
+
+
 def test_cg_frames_independent_and_zero_rhs():
     x, S, lines, y = _small_problem(32, 32, 3, 12, 3, 71)
     y[1] = 0.0
