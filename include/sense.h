@@ -166,6 +166,7 @@ sense_status sense_normal(sense_plan* plan, const sense_c32* x, const void* S, c
  * The iteration loop runs on the device without host synchronisation; with
  * rel_tol > 0 the host polls a device counter of live frames every few
  * iterations to stop early.  x_out must not alias y or S. */
+/* (With sense_plan_set_lambda the system solved is (E^H E + lambda I) x = E^H y.) */
 sense_status sense_cg_solve(sense_plan* plan, const void* y, const void* S, const int32_t* lines, int max_iter,
                             double rel_tol, sense_c32* x_out, int32_t* iters_out, double* rel_resid_out,
                             int32_t* outcome_out, void* stream);
@@ -205,6 +206,8 @@ int sense_batch_classes(const sense_batch* batch);
 /* Pick each class's normal-operator kernel variant by timing it on the
  * class member with the most frames (see sense_plan_autotune). */
 sense_status sense_batch_autotune(sense_batch* batch, const sense_batch_io* io, void* stream);
+/* Tikhonov weight of instance `instance`'s CG (see sense_plan_set_lambda). */
+sense_status sense_batch_set_lambda(sense_batch* batch, int instance, double lambda);
 /* Use kernel variant `variant` for every class of row count `ny`. */
 sense_status sense_batch_set_variant(sense_batch* batch, int ny, int variant);
 /* CG-SENSE on every instance (io[i] for instance i), same stopping rules as
@@ -307,6 +310,15 @@ sense_status sense_plan_set_cg_mode(sense_plan* plan, int mode);
  * the plan's ny); sense_plan_variant reports the current one. */
 sense_status sense_plan_set_variant(sense_plan* plan, int variant);
 int sense_plan_variant(const sense_plan* plan);
+
+/* Tikhonov regularisation of this plan's CG solves: sense_cg_solve then
+ * solves (E^H E + lambda I) x = E^H y per frame, the same Hestenes-Stiefel
+ * iteration with q = E^H E p + lambda p (the paper's method is lambda = 0,
+ * the default).  lambda must be finite, >= 0 and representable in FP32
+ * (the kernels use it in FP32), else SENSE_EINVAL.  sense_normal is not
+ * affected.  Synchronises the device when lambda changes (captured CG
+ * graphs are rebuilt). */
+sense_status sense_plan_set_lambda(sense_plan* plan, double lambda);
 
 /* Autotuner: time every variant of the normal-operator kernel on this plan's
  * shape with the caller's S and lines (device pointers), keep the fastest and

@@ -258,6 +258,15 @@ sense_status sense_batch_autotune(sense_batch* b, const sense_batch_io* io, void
   return SENSE_OK;
 }
 
+sense_status sense_batch_set_lambda(sense_batch* b, int instance, double lambda) {
+  if (!b) return bfail(SENSE_EINVAL, "batch is NULL");
+  if (instance < 0 || instance >= (int)b->plans.size()) return bfail(SENSE_EINVAL, "instance index out of range");
+  sense_status rc = sense_plan_set_lambda(b->plans[instance], lambda);
+  if (rc != SENSE_OK) return rc;
+  drop_graphs(b);  // frame tables bake lambda in
+  return SENSE_OK;
+}
+
 sense_status sense_batch_set_variant(sense_batch* b, int ny, int variant) {
   if (!b) return bfail(SENSE_EINVAL, "batch is NULL");
   for (auto& c : b->classes) {

@@ -462,6 +462,7 @@ struct NormalTile {
   int nx, coils, tile, p_update;
   int centred;          // CG=false: x and out signed by (-1)^(y+x)
   float beta;
+  float lambda;         // CG=true: Tikhonov weight, q = E^H E p + lambda p
 };
 
 template <class C, class St, bool CG>
@@ -533,8 +534,9 @@ __device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem&
     for (int n = 0; n < C::R0; ++n) {
       if (!(col.ok0(j) && xin)) continue;
       const size_t idx = (size_t)col.xrow(j, n) * a.nx + x;
-      const float2 qv = cscale(q[j][n], invN);
+      float2 qv = cscale(q[j][n], invN);
       if (CG) {
+        qv = make_float2(fmaf(a.lambda, p[j][n].x, qv.x), fmaf(a.lambda, p[j][n].y, qv.y));
         __stcg(a.q + idx, qv);
         part = fmaf(p[j][n].x, qv.x, fmaf(p[j][n].y, qv.y, part));
       } else {
@@ -641,7 +643,8 @@ __device__ __forceinline__ float normal_tile_tma(const NormalTile& a, const ColS
     for (int n = 0; n < C::R0; ++n) {
       if (!(col.ok0(j) && xin)) continue;
       const size_t idx = (size_t)col.xrow(j, n) * a.nx + x;
-      const float2 qv = cscale(q[j][n], invN);
+      float2 qv = cscale(q[j][n], invN);
+      qv = make_float2(fmaf(a.lambda, p[j][n].x, qv.x), fmaf(a.lambda, p[j][n].y, qv.y));
       __stcg(a.q + idx, qv);
       part = fmaf(p[j][n].x, qv.x, fmaf(p[j][n].y, qv.y, part));
     }
@@ -852,7 +855,8 @@ __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSm
 #pragma unroll
     for (int n = 0; n < C::R0; ++n) {
       if (!col.ok0(j)) continue;
-      const float2 qv = cscale(q[j][n], invN);
+      float2 qv = cscale(q[j][n], invN);
+      if (CG) qv = make_float2(fmaf(a.lambda, p[j][n].x, qv.x), fmaf(a.lambda, p[j][n].y, qv.y));
       s.buf0[col.c * CP + col.xrow(j, n)] = qv;
       if (CG && xin) part = fmaf(p[j][n].x, qv.x, fmaf(p[j][n].y, qv.y, part));
     }
@@ -920,6 +924,7 @@ struct NormalArgs {
   const float2* tw;
   int nx, coils, L, tiles, p_update;
   int centred;                 // CG=false: centred k-space (see NormalTile)
+  float lambda;                // CG=true: Tikhonov weight
   int* err;
   CgState cg;
 };
@@ -953,6 +958,7 @@ __global__ void __launch_bounds__(TH, MINB) k_normal(NormalArgs<St> a) {
   t.tile = blockIdx.x;
   t.p_update = a.p_update;
   t.centred = CG ? 0 : a.centred;
+  t.lambda = CG ? a.lambda : 0.f;
   t.beta = (CG && a.p_update) ? (float)__ldg(a.cg.beta + f) : 0.f;
   float part;
   double* red;

@@ -43,6 +43,7 @@ struct PFrame {
   int k0;              // CG iterations this frame has already done before the launch
   int kmax;            // the frame does no work at global iterations >= kmax
   double tol;          // relative-residual stopping tolerance (0: none)
+  float lambda;        // Tikhonov weight: the frame solves (E^H E + lambda I) x = E^H y
 };
 
 struct PState {
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
         nt.tile = piece;
         nt.p_update = kg > 0 ? 1 : 0;
         nt.centred = 0;
+        nt.lambda = fr.lambda;
         nt.beta = kg > 0 ? (float)__ldcg(fr.beta) : 0.f;
         const float part = tile.run(nt, keep, nfill, a.err);
         nfill += (unsigned)fr.coils;

@@ -23,6 +23,7 @@ struct sense_plan {
   int norm_variant = 0;  // kernel variant of the normal operator (autotuned)
   int norm_tiles = 0;    // column tiles per frame of that variant
   int cg_mode = 1;       // 0: per-phase kernels replayed as CUDA graphs; 1: one persistent launch
+  double lambda = 0.0;   // Tikhonov weight of CG: (E^H E + lambda I) x = E^H y
   cudaStream_t pool = nullptr;  // non-null: workspace is stream-ordered (cudaMallocAsync) on this stream
   CUtensorMap tmap_host;        // TMA descriptor of the maps S for the persistent kernel
   CUtensorMap* tmap_d = nullptr;

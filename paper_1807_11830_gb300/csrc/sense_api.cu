@@ -358,6 +358,7 @@ sense_status run_cg_iteration(sense_plan* pl, const void* S, const int* lines, f
   a.L = sh.lines;
   a.tiles = pl->norm_tiles;
   a.p_update = p_update;
+  a.lambda = (float)pl->lambda;
   a.err = pl->err();
   a.cg = pl->cg(tol);
   sense_status rc;
@@ -639,6 +640,7 @@ void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* 
     fr.k0 = k0;
     fr.kmax = 1 << 30;
     fr.tol = tol;
+    fr.lambda = (float)pl->lambda;
   }
 }
 
@@ -924,6 +926,20 @@ sense_status sense_plan_set_variant(sense_plan* pl, int variant) {
 }
 
 int sense_plan_variant(const sense_plan* pl) { return pl ? pl->norm_variant : -1; }
+
+sense_status sense_plan_set_lambda(sense_plan* pl, double lambda) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (!(lambda >= 0.0) || !std::isfinite(lambda) || lambda > 3.0e38)
+    return fail(SENSE_EINVAL, "lambda must be finite, >= 0 and representable in FP32");
+  if (lambda == pl->lambda) return SENSE_OK;
+  DeviceGuard guard(pl->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : pl->graphs) cudaGraphExecDestroy(kv.second);  // graphs bake lambda in
+  pl->graphs.clear();
+  pl->ptable_key[0] = nullptr;  // and so does the persistent frame table
+  pl->lambda = lambda;
+  return SENSE_OK;
+}
 
 sense_status sense_plan_autotune(sense_plan* pl, const void* S, const int32_t* lines, int* variant_out,
                                  double* ms_out, void* stream) {

@@ -34,7 +34,7 @@ EXPORTED = (
     "sense_forward", "sense_adjoint", "sense_normal", "sense_cg_solve", "sense_rss", "sense_c32_to_bf16",
     "sense_plan_check", "sense_last_error", "sense_plan_set_timing", "sense_plan_phase_time",
     "sense_adjoint_noalloc", "sense_plan_set_variant", "sense_plan_variant", "sense_plan_autotune",
-    "sense_plan_set_cg_mode", "sense_selftest_wait",
+    "sense_plan_set_cg_mode", "sense_selftest_wait", "sense_plan_set_lambda", "sense_batch_set_lambda",
     "sense_batch_create", "sense_batch_destroy", "sense_batch_workspace_bytes", "sense_batch_classes",
     "sense_batch_autotune", "sense_batch_set_variant", "sense_batch_cg_solve", "sense_batch_check",
     "sense_queue_create", "sense_queue_submit", "sense_queue_poll", "sense_queue_wait", "sense_queue_cancel",
@@ -130,6 +130,10 @@ def load_library(path=LIB_PATH):
     lib.sense_plan_set_variant.restype = st
     lib.sense_plan_variant.argtypes = [vp]
     lib.sense_plan_variant.restype = i
+    lib.sense_plan_set_lambda.argtypes = [vp, ctypes.c_double]
+    lib.sense_plan_set_lambda.restype = st
+    lib.sense_batch_set_lambda.argtypes = [vp, i, ctypes.c_double]
+    lib.sense_batch_set_lambda.restype = st
     lib.sense_plan_autotune.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), vp]
     lib.sense_plan_autotune.restype = st
     lib.sense_plan_set_cg_mode.argtypes = [vp, i]
@@ -295,6 +299,15 @@ def sense_plan_phase_time(plan, phase):
     n = ctypes.c_long()
     _check(load_library().sense_plan_phase_time(plan.handle, idx, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def sense_plan_set_lambda(plan, lam):
+    """Tikhonov weight of the plan's CG: solves (E^H E + lam I) x = E^H y."""
+    _check(load_library().sense_plan_set_lambda(plan.handle, float(lam)))
+
+
+def sense_batch_set_lambda(batch, instance, lam):
+    _check(load_library().sense_batch_set_lambda(batch.handle, int(instance), float(lam)))
 
 
 def sense_plan_set_cg_mode(plan, mode):
