@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--serve-requests", type=int, default=160)
     ap.add_argument("--cg-mode", default="auto", choices=("auto", "graph", "persistent"),
                     help="CG iteration scheme; 'auto' times both briefly and keeps the faster")
+    ap.add_argument("--lam", type=float, default=0.0,
+                    help="Tikhonov weight of the cine workload's CG, (E^H E + lam I) x = E^H y")
     ap.add_argument("--centred", action="store_true",
                     help="centred k-space convention (DC at n/2) for the cine and paper workloads")
     ap.add_argument("--normal-variant", default="auto",
@@ -142,7 +144,7 @@ def oracle_inputs(centred=False):
     return _ORACLE_INPUTS
 
 
-def oracle_sample(frames, iters, seed_offset=0, centred=False):
+def oracle_sample(frames, iters, seed_offset=0, centred=False, lam=0.0):
     """Time oracle CG-SENSE on `frames` frames of the workload for `iters`
     iterations.  Returns (applications/s, wall seconds, threads)."""
     import oracle
@@ -151,7 +153,7 @@ def oracle_sample(frames, iters, seed_offset=0, centred=False):
     sel = [(i + seed_offset) % FRAMES for i in range(frames)]
     y, S, lines = d["y"][sel], d["S"], d["lines"][sel]
     t0 = time.perf_counter()
-    oracle.cg(y, S, lines, iters, centred=d["centred"])
+    oracle.cg(y, S, lines, iters, centred=d["centred"], lam=lam)
     wall = time.perf_counter() - t0
     return frames * iters / wall, wall, min(oracle.threads(), frames)
 
@@ -291,6 +293,8 @@ def run_ours(args):
     lines_np = synth.centred_lines(p.lines, N) if args.centred else p.lines
     lines = torch.from_numpy(lines_np).to(dev)
     plan = sense.Plan(N, N, COILS, FRAMES, L, device=local_rank, centred=args.centred)
+    if args.lam:
+        sense.sense_plan_set_lambda(plan, args.lam)
     y = torch.empty((FRAMES, COILS, L, N), dtype=torch.complex64, device=dev)
     sense.sense_forward(plan, x_true, S, lines, y)
     y += torch.from_numpy(p.noise.astype(np.complex64)).to(dev)
@@ -450,7 +454,7 @@ def run_ours(args):
         if world == 1 and not args.no_cpu_baseline:
             import oracle
             frames = max(1, min(FRAMES, oracle.threads()))
-            v, wall, cores = oracle_sample(frames, args.cpu_sample_iters, centred=args.centred)
+            v, wall, cores = oracle_sample(frames, args.cpu_sample_iters, centred=args.centred, lam=args.lam)
             cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "%d of %d frames x %d CG iterations (full 256x256, 12 coils, R=4), %.1f s"
                              % (frames, FRAMES, args.cpu_sample_iters, wall)}
@@ -460,7 +464,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": base_config(world, args.centred),
+            "config": dict(base_config(world, args.centred), **({"tikhonov_lambda": args.lam} if args.lam else {})),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_ms / args.steps},
             "gpu_launches": int(round(launches_per_step * args.steps)),
