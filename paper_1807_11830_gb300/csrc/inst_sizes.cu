@@ -36,7 +36,7 @@ int col_threads(int n) {
 
 int row_width(int n) {
   switch (n) {
-#define SENSE_CASE(N) case N: return Cfg<N>::C::W;
+#define SENSE_CASE(N) case N: return RowPass<N>::C::W;
     SENSE_FOR_EACH_SIZE(SENSE_CASE)
 #undef SENSE_CASE
     default:

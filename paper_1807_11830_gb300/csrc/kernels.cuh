@@ -43,10 +43,23 @@ __host__ __device__ constexpr size_t col_smem_bytes() {
   return col_smem_bytes_c<typename ColPass<N>::C>();
 }
 
+// Row pass (E's second pass, E^H's first): the length's transform on 8-row
+// tiles where that fills whole warps (more, smaller blocks in flight for a
+// pass bound by memory latency).  The staged tile has row pitch N + 1 for
+// 16-row tiles and N + 2 for 8-row tiles: a half-warp then reads 16 rows (or
+// 8 rows x 2 adjacent elements) on 16 distinct 8-byte bank pairs.
+template <int N>
+struct RowPass {
+  using Base = typename Cfg<N>::C;
+  static constexpr int W = (Base::T * 8) % 32 == 0 ? 8 : Base::W;
+  using C = Col<Base::T, W, typename Base::Radix>;
+  static constexpr int P = W == 8 ? N + 2 : N + 1;
+};
+
 template <int N>
 constexpr size_t row_smem_bytes() {
-  using C = typename Cfg<N>::C;
-  return sizeof(float2) * (size_t)N + sizeof(float2) * (size_t)C::W * (N + 1) + sizeof(float2) * (size_t)C::W * N;
+  using R = RowPass<N>;
+  return sizeof(float2) * (size_t)N + sizeof(float2) * (size_t)R::C::W * R::P + sizeof(float2) * (size_t)R::C::W * N;
 }
 
 struct ColSmem {
@@ -198,11 +211,11 @@ struct RowArgs {
   float cs;     // (-1)^(ny/2 + nx/2)
 };
 
-template <int N, int DIR, class InSt, class OutSt, int TH = Cfg<N>::C::THREADS>
+template <int N, int DIR, class InSt, class OutSt, int TH = RowPass<N>::C::THREADS>
 __global__ void __launch_bounds__(TH)
     k_rows(RowArgs<typename InSt::T, typename OutSt::T> a) {
-  using C = typename Cfg<N>::C;
-  constexpr int P = N + 1;  // padded row pitch (conflict-free column access)
+  using C = typename RowPass<N>::C;
+  constexpr int P = RowPass<N>::P;  // padded row pitch (conflict-free column access)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* tile = tw + N;

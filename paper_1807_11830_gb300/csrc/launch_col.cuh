@@ -117,9 +117,9 @@ cudaError_t rows_n(const RowArgs<typename InSt::T, typename OutSt::T>& a, cudaSt
   constexpr size_t sm = row_smem_bytes<N>();
   cudaError_t e = ensure_smem(k_rows<N, DIR, InSt, OutSt>, sm, &done);
   if (e != cudaSuccess) return e;
-  const long blocks = (a.rows + Cfg<N>::C::W - 1) / Cfg<N>::C::W;
+  const long blocks = (a.rows + RowPass<N>::C::W - 1) / RowPass<N>::C::W;
   if (blocks <= 0) return cudaSuccess;
-  k_rows<N, DIR, InSt, OutSt><<<(unsigned)blocks, Cfg<N>::C::THREADS, sm, s>>>(a);
+  k_rows<N, DIR, InSt, OutSt><<<(unsigned)blocks, RowPass<N>::C::THREADS, sm, s>>>(a);
   return cudaGetLastError();
 }
 
