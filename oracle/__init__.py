@@ -45,7 +45,8 @@ def _load(path):
     for name in ("orc_forward", "orc_adjoint", "orc_normal"):
         getattr(lib, name).argtypes = [i, i, i, i, i, dp, dp, ip, dp, i]
     lib.orc_normal_collapsed.argtypes = [i, i, i, i, i, dp, dp, ip, dp]
-    lib.orc_cg.argtypes = [i, i, i, i, i, dp, dp, ip, i, ctypes.c_double, dp, ip, dp, ip, i, ctypes.c_double]
+    lib.orc_cg.argtypes = [i, i, i, i, i, dp, dp, ip, i, ctypes.c_double, dp, ip, dp, ip, i, ctypes.c_double,
+                           ctypes.c_double]
     lib.orc_rss.argtypes = [i, i, i, i, i, dp, ip, dp, i]
     lib.orc_bf16_rne.argtypes = [ctypes.c_long, ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(ctypes.c_uint16)]
@@ -155,9 +156,10 @@ def normal_collapsed(x, S, lines):
     return out
 
 
-def cg(y, S, lines, max_iter, tol=0.0, centred=False, lam=0.0):
-    """CG on (E^H E + lam I) x = E^H y per frame.  Returns (x, iters[F],
-    resid[F], status[F])."""
+def cg(y, S, lines, max_iter, tol=0.0, centred=False, lam=0.0, lam_t=0.0):
+    """CG on (E^H E + lam I) x = E^H y per frame; with lam_t > 0 one CG over
+    all frames on (E^H E + lam I + lam_t L) x = E^H y, L the cyclic second
+    difference across frames.  Returns (x, iters[F], resid[F], status[F])."""
     S, lines, F, C, ny, nx, L = _shape(None, S, lines)
     y = _c128(y).reshape(F, C, L, nx)
     x = np.empty((F, ny, nx), np.complex128)
@@ -165,7 +167,8 @@ def cg(y, S, lines, max_iter, tol=0.0, centred=False, lam=0.0):
     resid = np.zeros(F, np.float64)
     status = np.zeros(F, np.int32)
     _check(_lib().orc_cg(F, C, ny, nx, L, _dptr(y), _dptr(S), _iptr(lines), int(max_iter), float(tol),
-                         _dptr(x), _iptr(iters), _dptr(resid), _iptr(status), int(centred), float(lam)), "cg")
+                         _dptr(x), _iptr(iters), _dptr(resid), _iptr(status), int(centred), float(lam),
+                         float(lam_t)), "cg")
     return x, iters, resid, status
 
 

@@ -181,6 +181,60 @@ double re_dot(long n, const cd* a, const cd* b) {
   return s;
 }
 
+// CG over all frames at once on
+//   (E^H E + lambda I + lambda_t L) x = E^H y,
+// L the cyclic second difference across frames, (L x)_f = 2 x_f - x_{f-1} -
+// x_{f+1} with frame indices modulo F: the normal equations of
+// ||E x - y||^2 + lambda ||x||^2 + lambda_t sum_f ||x_f - x_{f-1}||^2 for a
+// cyclic (cine) series.  One set of scalars for the stacked vector; every
+// frame reports the same iterations, residual and status.
+void cg_coupled(int F, int C, int ny, int nx, int L, const cd* yc, const cd* Sc, const int* lines, int max_iter,
+                double tol, bool centred, double lambda, double lambda_t, cd* x, int* iters, double* resid,
+                int* status) {
+  const long npix = (long)ny * nx, n = (long)F * npix;
+  std::vector<cd> r((size_t)n), p((size_t)n), q((size_t)n);
+  for (int f = 0; f < F; ++f)
+    adjoint_frame(C, ny, nx, L, yc + (long)f * C * L * nx, Sc, lines + (long)f * L, r.data() + f * npix, centred);
+  for (long i = 0; i < n; ++i) { x[i] = 0.0; p[i] = r[i]; }
+  double rho = re_dot(n, r.data(), r.data());
+  const double rho0 = rho;
+  int it = 0;
+  int st = rho0 == 0.0 ? 1 : 0;  // converged / running
+  while (st == 0 && it < max_iter) {
+    for (int f = 0; f < F; ++f) {
+      cd* qf = q.data() + f * npix;
+      const cd* pf = p.data() + f * npix;
+      const cd* pm = p.data() + (long)((f + F - 1) % F) * npix;
+      const cd* pn = p.data() + (long)((f + 1) % F) * npix;
+      normal_frame(C, ny, nx, L, pf, Sc, lines + (long)f * L, qf, centred);
+      for (long i = 0; i < npix; ++i) qf[i] += lambda * pf[i] + lambda_t * (2.0 * pf[i] - pm[i] - pn[i]);
+    }
+    const double pq = re_dot(n, p.data(), q.data());
+    if (!(pq > 0.0)) { st = 3; break; }
+    const double alpha = rho / pq;
+    for (long i = 0; i < n; ++i) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * q[i];
+    }
+    const double rho_new = re_dot(n, r.data(), r.data());
+    ++it;
+    if (rho_new == 0.0 || (tol > 0.0 && std::sqrt(rho_new / rho0) <= tol)) {
+      rho = rho_new;
+      st = 1;
+      break;
+    }
+    const double beta = rho_new / rho;
+    for (long i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+    rho = rho_new;
+  }
+  if (st == 0) st = 2;
+  for (int f = 0; f < F; ++f) {
+    iters[f] = it;
+    resid[f] = rho0 > 0.0 ? std::sqrt(rho / rho0) : 0.0;
+    status[f] = st;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -323,7 +377,8 @@ int orc_normal_collapsed(int F, int C, int ny, int nx, int L, const double* x, c
 enum { ORC_CG_RUNNING = 0, ORC_CG_CONVERGED = 1, ORC_CG_MAXITER = 2, ORC_CG_BREAKDOWN = 3 };
 
 // Hestenes-Stiefel CG on (E^H E + lambda I) x = E^H y, independently for
-// every frame (lambda >= 0 is Tikhonov regularisation; 0 gives CG-SENSE):
+// every frame (lambda >= 0 is Tikhonov regularisation; 0 gives CG-SENSE);
+// lambda_t > 0 adds the temporal term and couples the frames (cg_coupled):
 //   b = E^H y; x0 = 0; r0 = b; p0 = r0; rho0 = <r0, r0>
 //   for k = 0 .. max_iter-1:
 //     q = E^H E p + lambda p;  alpha = rho_k / Re<p, q>
@@ -336,15 +391,21 @@ enum { ORC_CG_RUNNING = 0, ORC_CG_CONVERGED = 1, ORC_CG_MAXITER = 2, ORC_CG_BREA
 // Outputs: x [F][ny][nx]; iters[f] = iterations applied; resid[f] =
 // sqrt(rho/rho0) at exit (0 when rho0 == 0); status[f] as above.
 int orc_cg(int F, int C, int ny, int nx, int L, const double* y, const double* S, const int* lines, int max_iter,
-           double tol, double* x, int* iters, double* resid, int* status, int centred, double lambda) {
+           double tol, double* x, int* iters, double* resid, int* status, int centred, double lambda,
+           double lambda_t) {
   if (F < 0 || C <= 0 || ny <= 0 || nx <= 0 || L < 0 || L > ny || max_iter < 0 || !(tol >= 0.0) ||
-      !(lambda >= 0.0))
+      !(lambda >= 0.0) || !(lambda_t >= 0.0))
     return ORC_EINVAL;
   if (!all_lines_ok(F, ny, L, lines)) return ORC_EINVAL;
   long npix = (long)ny * nx;
   const cd* yc = reinterpret_cast<const cd*>(y);
   const cd* Sc = reinterpret_cast<const cd*>(S);
   cd* xc = reinterpret_cast<cd*>(x);
+  if (lambda_t > 0.0) {  // frames coupled: one CG over the series
+    cg_coupled(F, C, ny, nx, L, yc, Sc, lines, max_iter, tol, centred != 0, lambda, lambda_t, xc, iters, resid,
+               status);
+    return ORC_OK;
+  }
 #pragma omp parallel for schedule(dynamic)
   for (int f = 0; f < F; ++f) {
     const int* ln = lines + (long)f * L;

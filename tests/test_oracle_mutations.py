@@ -42,6 +42,8 @@ MUTANTS = {
     # direct DFT index slip
     "dft_index": ("in[(long)j * stride] * unit_root((long long)j * k, n, dir)",
                   "in[(long)j * stride] * unit_root((long long)j * (k + 1), n, dir)"),
+    # temporal difference adds a neighbour instead of subtracting it
+    "temporal_neighbour_sign": ("(2.0 * pf[i] - pm[i] - pn[i])", "(2.0 * pf[i] - pm[i] + pn[i])"),
     # Tikhonov term with the wrong sign
     "cg_lambda_sign": ("q[i] += lambda * p[i];", "q[i] -= lambda * p[i];"),
     # centred transform forgets the output fftshift
@@ -65,6 +67,7 @@ QUICK_PINS = [
     lambda: [centred.test_centred_fft2_brute_force(*sh) for sh in [(3, 5), (4, 6), (7, 7)]],
     lambda: centred.test_centred_adjoint_identity_and_full_sampling((16, 12, 3, 7, 2)),
     lambda: pins.test_regularised_cg_against_dense_solves(0.0625),
+    lambda: pins.test_temporal_cg_against_dense_solves(3, 0.0, 0.5),
 ]
 
 

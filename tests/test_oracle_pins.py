@@ -301,6 +301,60 @@ def test_regularised_cg_limits():
     assert rel(x1 * lam, xb) <= 1e-7
 
 
+def _dense_coupled(S, lines, ny, nx, lam, lam_t):
+    """Stacked dense matrix of E^H E + lam I + lam_t (L (x) I) over F frames,
+    L the cyclic second difference 2 I - shift - shift^T."""
+    F = lines.shape[0]
+    n = ny * nx
+    A = np.zeros((F * n, F * n), complex)
+    for f in range(F):
+        A[f * n:(f + 1) * n, f * n:(f + 1) * n] = _dense_normal(S, lines[f:f + 1], ny, nx) + lam * np.eye(n)
+    Lt = 2 * np.eye(F) - np.roll(np.eye(F), 1, axis=1) - np.roll(np.eye(F), -1, axis=1)
+    return A + lam_t * np.kron(Lt, np.eye(n))
+
+
+@pytest.mark.parametrize("F,lam,lam_t", [(3, 0.0, 0.5), (4, 0.125, 2.0), (2, 0.0, 0.25)])
+def test_temporal_cg_against_dense_solves(F, lam, lam_t):
+    """Temporally regularised CG couples the frames: one CG on the stacked
+    system.  Each iterate is the minimiser over the stacked Krylov space and
+    the converged iterate is the dense solve."""
+    ny = nx = 6
+    rng = synth.rng_for(64 + F)
+    S = synth.random_complex((2, ny, nx), rng)
+    lines = synth.mask_lines(ny, 3, 2, F, rng)
+    y = synth.random_complex((F, 2, 3, nx), rng)
+    A = _dense_coupled(S, lines, ny, nx, lam, lam_t)
+    assert np.allclose(A, A.conj().T, atol=1e-12)
+    b = oracle.adjoint(y, S, lines).ravel()
+    for k in (1, 2, 5):
+        K = np.stack([np.linalg.matrix_power(A, i) @ b for i in range(k)], axis=1)
+        Q, _ = np.linalg.qr(K)
+        xk_dense = Q @ np.linalg.solve(Q.conj().T @ A @ Q, Q.conj().T @ b)
+        xk, iters, _, _ = oracle.cg(y, S, lines, max_iter=k, lam=lam, lam_t=lam_t)
+        assert list(iters) == [k] * F
+        assert rel(xk.ravel(), xk_dense) <= 1e-8, k
+    xc, iters, resid, status = oracle.cg(y, S, lines, max_iter=400, tol=1e-13, lam=lam, lam_t=lam_t)
+    assert len(set(iters)) == 1 and len(set(status)) == 1 and len(set(resid)) == 1
+    x_ls = np.linalg.lstsq(A, b, rcond=1e-12)[0]
+    assert rel(xc.ravel(), x_ls) <= 1e-8
+
+
+def test_temporal_cg_special_cases():
+    x, S, lines, y = _small_problem(12, 12, 3, 5, 1, 75)
+    # one frame: the cyclic difference vanishes, the plain per-frame CG results
+    a = oracle.cg(y, S, lines, 6, lam=0.25)
+    b = oracle.cg(y, S, lines, 6, lam=0.25, lam_t=3.0)
+    assert rel(b[0], a[0]) <= 1e-12
+    # frames with identical data and masks: the solution is constant in time,
+    # so the temporal term does not change it
+    F = 3
+    yy = np.repeat(y, F, axis=0)
+    ll = np.repeat(lines, F, axis=0)
+    c = oracle.cg(yy, S, ll, 8, lam_t=5.0)
+    d = oracle.cg(yy, S, ll, 8)
+    assert rel(c[0], d[0]) <= 1e-10
+
+
 def test_cg_frames_independent_and_zero_rhs():
     x, S, lines, y = _small_problem(32, 32, 3, 12, 3, 71)
     y[1] = 0.0
