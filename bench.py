@@ -71,6 +71,9 @@ def parse_args():
                     help="CG iteration scheme; 'auto' times both briefly and keeps the faster")
     ap.add_argument("--lam", type=float, default=0.0,
                     help="Tikhonov weight of the cine workload's CG, (E^H E + lam I) x = E^H y")
+    ap.add_argument("--lam-t", type=float, default=0.0,
+                    help="temporal weight of the cine workload: one CG over the 20 frames, "
+                         "(E^H E + lam I + lam_t L) x = E^H y with L the cyclic second difference")
     ap.add_argument("--centred", action="store_true",
                     help="centred k-space convention (DC at n/2) for the cine and paper workloads")
     ap.add_argument("--normal-variant", default="auto",
@@ -144,7 +147,7 @@ def oracle_inputs(centred=False):
     return _ORACLE_INPUTS
 
 
-def oracle_sample(frames, iters, seed_offset=0, centred=False, lam=0.0):
+def oracle_sample(frames, iters, seed_offset=0, centred=False, lam=0.0, lam_t=0.0):
     """Time oracle CG-SENSE on `frames` frames of the workload for `iters`
     iterations.  Returns (applications/s, wall seconds, threads)."""
     import oracle
@@ -153,7 +156,7 @@ def oracle_sample(frames, iters, seed_offset=0, centred=False, lam=0.0):
     sel = [(i + seed_offset) % FRAMES for i in range(frames)]
     y, S, lines = d["y"][sel], d["S"], d["lines"][sel]
     t0 = time.perf_counter()
-    oracle.cg(y, S, lines, iters, centred=d["centred"], lam=lam)
+    oracle.cg(y, S, lines, iters, centred=d["centred"], lam=lam, lam_t=lam_t)
     wall = time.perf_counter() - t0
     return frames * iters / wall, wall, min(oracle.threads(), frames)
 
@@ -295,6 +298,8 @@ def run_ours(args):
     plan = sense.Plan(N, N, COILS, FRAMES, L, device=local_rank, centred=args.centred)
     if args.lam:
         sense.sense_plan_set_lambda(plan, args.lam)
+    if args.lam_t:
+        sense.sense_plan_set_temporal(plan, args.lam_t)
     y = torch.empty((FRAMES, COILS, L, N), dtype=torch.complex64, device=dev)
     sense.sense_forward(plan, x_true, S, lines, y)
     y += torch.from_numpy(p.noise.astype(np.complex64)).to(dev)
@@ -454,7 +459,8 @@ def run_ours(args):
         if world == 1 and not args.no_cpu_baseline:
             import oracle
             frames = max(1, min(FRAMES, oracle.threads()))
-            v, wall, cores = oracle_sample(frames, args.cpu_sample_iters, centred=args.centred, lam=args.lam)
+            v, wall, cores = oracle_sample(frames, args.cpu_sample_iters, centred=args.centred, lam=args.lam,
+                                           lam_t=args.lam_t)
             cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "%d of %d frames x %d CG iterations (full 256x256, 12 coils, R=4), %.1f s"
                              % (frames, FRAMES, args.cpu_sample_iters, wall)}
@@ -464,7 +470,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(base_config(world, args.centred), **({"tikhonov_lambda": args.lam} if args.lam else {})),
+            "config": dict(base_config(world, args.centred), **({"tikhonov_lambda": args.lam} if args.lam else {}),
+                           **({"temporal_lambda": args.lam_t} if args.lam_t else {})),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_ms / args.steps},
             "gpu_launches": int(round(launches_per_step * args.steps)),

@@ -208,6 +208,8 @@ int sense_batch_classes(const sense_batch* batch);
 sense_status sense_batch_autotune(sense_batch* batch, const sense_batch_io* io, void* stream);
 /* Tikhonov weight of instance `instance`'s CG (see sense_plan_set_lambda). */
 sense_status sense_batch_set_lambda(sense_batch* batch, int instance, double lambda);
+/* Temporal weight of instance `instance` (see sense_plan_set_temporal). */
+sense_status sense_batch_set_temporal(sense_batch* batch, int instance, double lambda_t);
 /* Use kernel variant `variant` for every class of row count `ny`. */
 sense_status sense_batch_set_variant(sense_batch* batch, int ny, int variant);
 /* CG-SENSE on every instance (io[i] for instance i), same stopping rules as
@@ -319,6 +321,19 @@ int sense_plan_variant(const sense_plan* plan);
  * affected.  Synchronises the device when lambda changes (captured CG
  * graphs are rebuilt). */
 sense_status sense_plan_set_lambda(sense_plan* plan, double lambda);
+
+/* Temporal regularisation of this plan's CG over its frames, treated as a
+ * cyclic (cine) series: with lambda_t > 0, sense_cg_solve runs ONE CG over
+ * all frames on (E^H E + lambda I + lambda_t L) x = E^H y, L the cyclic
+ * second difference across frames ((L x)_f = 2 x_f - x_{f-1} - x_{f+1},
+ * frame indices modulo F): the normal equations of ||E x - y||^2 +
+ * lambda ||x||^2 + lambda_t sum_f ||x_f - x_{f-1}||^2.  The scalars, the
+ * stopping test (on the residual of the whole series) and the per-frame
+ * outputs (iterations, residual, outcome: equal for every frame) are the
+ * series'.  It runs in the persistent CG kernel whatever the CG mode.
+ * lambda_t = 0 (the default) keeps the frames independent.  lambda_t must be
+ * finite, >= 0 and FP32-representable, else SENSE_EINVAL. */
+sense_status sense_plan_set_temporal(sense_plan* plan, double lambda_t);
 
 /* Autotuner: time every variant of the normal-operator kernel on this plan's
  * shape with the caller's S and lines (device pointers), keep the fastest and

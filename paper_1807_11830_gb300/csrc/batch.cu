@@ -267,6 +267,15 @@ sense_status sense_batch_set_lambda(sense_batch* b, int instance, double lambda)
   return SENSE_OK;
 }
 
+sense_status sense_batch_set_temporal(sense_batch* b, int instance, double lambda_t) {
+  if (!b) return bfail(SENSE_EINVAL, "batch is NULL");
+  if (instance < 0 || instance >= (int)b->plans.size()) return bfail(SENSE_EINVAL, "instance index out of range");
+  sense_status rc = sense_plan_set_temporal(b->plans[instance], lambda_t);
+  if (rc != SENSE_OK) return rc;
+  drop_graphs(b);  // frame tables bake the coupling in
+  return SENSE_OK;
+}
+
 sense_status sense_batch_set_variant(sense_batch* b, int ny, int variant) {
   if (!b) return bfail(SENSE_EINVAL, "batch is NULL");
   for (auto& c : b->classes) {
@@ -327,7 +336,7 @@ sense_status sense_batch_cg_solve(sense_batch* b, const sense_batch_io* io, int 
           return trc;
         }
         plan_frames(p, transposed ? p->maps_t : io[i].S, io[i].lines, reinterpret_cast<float2*>(io[i].x_out), 0,
-                    rel_tol, host.data() + off);
+                    rel_tol, host.data() + off, (int)off);
         off += p->sh.frames;
       }
       PFrame* dev = nullptr;

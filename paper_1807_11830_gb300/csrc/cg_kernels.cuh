@@ -82,15 +82,34 @@ __global__ void __launch_bounds__(UPD_THREADS) k_cg_update(UpdateArgs a) {
 }
 
 // Final per-frame outputs of a CG solve.
-__global__ void k_cg_finish(CgState g, int frames, int* iters_out, double* resid_out, int* outcome_out) {
+// Per-frame CG outputs; `coupled`: all frames report the group's (slot 0).
+__global__ void k_cg_finish(CgState g, int frames, int* iters_out, double* resid_out, int* outcome_out,
+                            int coupled) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= frames) return;
-  int oc = g.outcome[f];
+  const int s = coupled ? 0 : f;
+  int oc = g.outcome[s];
   if (oc == CG_RUNNING) oc = CG_MAXITER;
-  g.outcome[f] = oc;
-  if (iters_out) iters_out[f] = g.iters[f];
-  if (resid_out) resid_out[f] = g.resid[f];
+  if (!coupled) g.outcome[f] = oc;
+  if (iters_out) iters_out[f] = g.iters[s];
+  if (resid_out) resid_out[f] = g.resid[s];
   if (outcome_out) outcome_out[f] = oc;
+}
+
+// Frames coupled into one CG: after the per-frame CG start, slot 0 takes the
+// group's start state, rho0 = sum over frames (in frame order).
+__global__ void k_cg_couple_start(CgState g, int frames) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double rho = 0.0;
+  for (int f = 0; f < frames; ++f) rho += g.rho[f];
+  g.rho[0] = rho;
+  g.rho0[0] = rho;
+  g.iters[0] = 0;
+  g.alpha[0] = 0.0;
+  g.beta[0] = 0.0;
+  g.active[0] = rho > 0.0 ? 1 : 0;
+  g.outcome[0] = rho > 0.0 ? CG_RUNNING : CG_CONVERGED;
+  g.resid[0] = rho > 0.0 ? 1.0 : 0.0;
 }
 
 // CG iterates of a centred-k-space problem live in the modulated space

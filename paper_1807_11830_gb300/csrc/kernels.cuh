@@ -476,7 +476,28 @@ struct NormalTile {
   int centred;          // CG=false: x and out signed by (-1)^(y+x)
   float beta;
   float lambda;         // CG=true: Tikhonov weight, q = E^H E p + lambda p
+  // CG=true, frames coupled in time (lambda_t > 0): q += lambda_t (2 p - p_prev - p_next)
+  // with the neighbouring frames' current directions formed on the fly,
+  // p_nb = r_nb + beta ps_nb (or ps_nb itself when !p_update)
+  float lambda_t;
+  const float2 *r_prev, *r_next, *ps_prev, *ps_next;
 };
+
+// The temporal term lambda_t (2 p - p_prev - p_next) at image index idx.
+__device__ __forceinline__ float2 neighbour_direction(const NormalTile& a, const float2* ps, const float2* r,
+                                                      size_t idx) {
+  float2 v = __ldcg(ps + idx);
+  if (a.p_update) {
+    const float2 rv = __ldcg(r + idx);
+    v = make_float2(fmaf(a.beta, v.x, rv.x), fmaf(a.beta, v.y, rv.y));
+  }
+  return v;
+}
+__device__ __forceinline__ float2 temporal_term(const NormalTile& a, size_t idx, float2 p) {
+  const float2 pp = neighbour_direction(a, a.ps_prev, a.r_prev, idx);
+  const float2 pn = neighbour_direction(a, a.ps_next, a.r_next, idx);
+  return make_float2(a.lambda_t * (2.f * p.x - pp.x - pn.x), a.lambda_t * (2.f * p.y - pp.y - pn.y));
+}
 
 template <class C, class St, bool CG>
 __device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem& s, unsigned keep) {
@@ -550,6 +571,7 @@ __device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem&
       float2 qv = cscale(q[j][n], invN);
       if (CG) {
         qv = make_float2(fmaf(a.lambda, p[j][n].x, qv.x), fmaf(a.lambda, p[j][n].y, qv.y));
+        if (a.lambda_t != 0.f) qv = cadd(qv, temporal_term(a, idx, p[j][n]));
         __stcg(a.q + idx, qv);
         part = fmaf(p[j][n].x, qv.x, fmaf(p[j][n].y, qv.y, part));
       } else {
@@ -576,7 +598,7 @@ struct SStage {
   static constexpr unsigned BYTES = (unsigned)(C::N * C::W * sizeof(typename St::T));
   // thread 0: copy the [N][W] map tile of coil c, columns tile*W.., into fill slot i
   __device__ __forceinline__ void issue(unsigned i, int tile, int c) const {
-    typename St::T* dst = buf[i & 1];
+    typename St::T* dst = (i & 1) ? buf[1] : buf[0];  // constant indices keep the struct in registers
     uint64_t* b = bar + (i & 1);
     tmap_acquire(tmap);
     fence_proxy_async_smem();
@@ -621,7 +643,7 @@ __device__ __forceinline__ float normal_tile_tma(const NormalTile& a, const ColS
   for (int c = 0; c < a.coils; ++c) {
     const unsigned i = nfill + (unsigned)c;
     if (!mbar_wait(sg.bar + (i & 1), (i >> 1) & 1u)) atomicOr(err, ERR_TIMEOUT);
-    const typename St::T* sb = sg.buf[i & 1];
+    const typename St::T* sb = (i & 1) ? sg.buf[1] : sg.buf[0];
     float2 xr[C::J0][C::R0];
     float2 kr[C::JL][C::RL];
 #pragma unroll
@@ -658,6 +680,7 @@ __device__ __forceinline__ float normal_tile_tma(const NormalTile& a, const ColS
       const size_t idx = (size_t)col.xrow(j, n) * a.nx + x;
       float2 qv = cscale(q[j][n], invN);
       qv = make_float2(fmaf(a.lambda, p[j][n].x, qv.x), fmaf(a.lambda, p[j][n].y, qv.y));
+      if (a.lambda_t != 0.f) qv = cadd(qv, temporal_term(a, idx, p[j][n]));
       __stcg(a.q + idx, qv);
       part = fmaf(p[j][n].x, qv.x, fmaf(p[j][n].y, qv.y, part));
     }
@@ -869,7 +892,10 @@ __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSm
     for (int n = 0; n < C::R0; ++n) {
       if (!col.ok0(j)) continue;
       float2 qv = cscale(q[j][n], invN);
-      if (CG) qv = make_float2(fmaf(a.lambda, p[j][n].x, qv.x), fmaf(a.lambda, p[j][n].y, qv.y));
+      if (CG) {
+        qv = make_float2(fmaf(a.lambda, p[j][n].x, qv.x), fmaf(a.lambda, p[j][n].y, qv.y));
+        if (a.lambda_t != 0.f && xin) qv = cadd(qv, temporal_term(a, (size_t)col.xrow(j, n) * a.nx + x0 + col.c, p[j][n]));
+      }
       s.buf0[col.c * CP + col.xrow(j, n)] = qv;
       if (CG && xin) part = fmaf(p[j][n].x, qv.x, fmaf(p[j][n].y, qv.y, part));
     }
@@ -972,6 +998,7 @@ __global__ void __launch_bounds__(TH, MINB) k_normal(NormalArgs<St> a) {
   t.p_update = a.p_update;
   t.centred = CG ? 0 : a.centred;
   t.lambda = CG ? a.lambda : 0.f;
+  t.lambda_t = 0.f;  // frames are coupled only in the persistent kernel
   t.beta = (CG && a.p_update) ? (float)__ldg(a.cg.beta + f) : 0.f;
   float part;
   double* red;

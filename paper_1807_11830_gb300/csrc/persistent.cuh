@@ -44,8 +44,19 @@ struct PFrame {
   int kmax;            // the frame does no work at global iterations >= kmax
   double tol;          // relative-residual stopping tolerance (0: none)
   float lambda;        // Tikhonov weight: the frame solves (E^H E + lambda I) x = E^H y
+  // Frames coupled in time share one CG: the group is the table range
+  // [g0, g0 + gsize) (g0 = own index, gsize = 1 for an independent frame),
+  // whose scalars live at the first frame's slots; arrivals, ready flags and
+  // partial sums are counted over the whole group.  lambda_t weighs the
+  // cyclic temporal second difference with the table entries nb_prev, nb_next.
+  int g0, gsize;
+  float lambda_t;
+  int nb_prev, nb_next;
 };
 
+// (Members of a frame entry are picked with constant indices throughout: a
+// runtime index into the kernel's copy of the entry would put the copy in
+// local memory.)
 struct PState {
   unsigned *nrm_arrive, *upd_arrive;          // [frames] arrivals of the current phase
   int *nrm_ready, *upd_ready;                 // [frames] launch iterations whose phase is complete
@@ -170,14 +181,15 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
     const int f = w / per;
     const int piece = w - f * per;
     const PFrame fr = a.frames[f];
+    const int gi = fr.g0;  // this frame's group: state index and first table entry
 
-    // ---- wait for the previous phase of this frame ----
+    // ---- wait for the previous phase of this frame's group ----
     if (threadIdx.x == 0) {
       bool ok = true;
       if (normal) {
-        if (k > 0) ok = wait_at_least(g.upd_ready + f, k);
+        if (k > 0) ok = wait_at_least(g.upd_ready + gi, k);
       } else {
-        ok = wait_at_least(g.nrm_ready + f, k + 1);
+        ok = wait_at_least(g.nrm_ready + gi, k + 1);
       }
       if (!ok) atomicOr(a.err, ERR_TIMEOUT);
       s_ok = ok ? 1 : 0;
@@ -193,8 +205,8 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
         const unsigned keep = sampled_bits<C>(tile.map());
         const int kg = k + fr.k0;  // global iteration index of this frame
         NormalTile nt;
-        nt.p_src = fr.p[kg > 0 ? ((kg - 1) & 1) : 0];
-        nt.p_dst = fr.p[kg & 1];
+        nt.p_src = (kg > 0 && ((kg - 1) & 1) ? fr.p[1] : fr.p[0]);
+        nt.p_dst = ((kg & 1) ? fr.p[1] : fr.p[0]);
         nt.r = fr.r;
         nt.q = fr.q;
         nt.S = fr.S;
@@ -204,6 +216,16 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
         nt.p_update = kg > 0 ? 1 : 0;
         nt.centred = 0;
         nt.lambda = fr.lambda;
+        nt.lambda_t = fr.lambda_t;
+        if (fr.lambda_t != 0.f) {  // neighbours' table entries only for frames coupled in time
+          const int ip = kg > 0 ? ((kg - 1) & 1) : 0;
+          const PFrame* fp = a.frames + fr.nb_prev;
+          const PFrame* fn = a.frames + fr.nb_next;
+          nt.r_prev = fp->r;
+          nt.ps_prev = ip ? fp->p[1] : fp->p[0];
+          nt.r_next = fn->r;
+          nt.ps_next = ip ? fn->p[1] : fn->p[0];
+        }
         nt.beta = kg > 0 ? (float)__ldcg(fr.beta) : 0.f;
         const float part = tile.run(nt, keep, nfill, a.err);
         nfill += (unsigned)fr.coils;
@@ -213,13 +235,13 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(g.nrm_arrive + f, 1u);
-        if (prev == (unsigned)a.tiles - 1u) {  // last tile of the frame: alpha
-          g.nrm_arrive[f] = 0u;
+        const unsigned prev = atomicAdd(g.nrm_arrive + gi, 1u);
+        if (prev == (unsigned)(a.tiles * fr.gsize) - 1u) {  // last tile of the group: alpha
+          g.nrm_arrive[gi] = 0u;
           __threadfence();
           if (s_active) {
             double pq = 0.0;
-            for (int i = 0; i < a.tiles; ++i) pq += __ldcg(g.part_nrm + (size_t)f * a.tiles + i);
+            for (int i = 0; i < a.tiles * fr.gsize; ++i) pq += __ldcg(g.part_nrm + (size_t)gi * a.tiles + i);
             if (pq > 0.0) {
               __stcg(fr.alpha, __ldcg(fr.rho) / pq);
             } else {  // breakdown (zero, negative or NaN curvature): freeze the frame
@@ -228,14 +250,14 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
             }
           }
           __threadfence();
-          st_release(g.nrm_ready + f, k + 1);
+          st_release(g.nrm_ready + gi, k + 1);
         }
       }
     } else {
       float acc = 0.f;
       if (work) {
         const float al = (float)__ldcg(fr.alpha);
-        const float4* pp = reinterpret_cast<const float4*>(fr.p[(k + fr.k0) & 1]);
+        const float4* pp = reinterpret_cast<const float4*>((((k + fr.k0) & 1) ? fr.p[1] : fr.p[0]));
         const float4* qp = reinterpret_cast<const float4*>(fr.q);
         float4* xp = reinterpret_cast<float4*>(fr.x);
         float4* rp = reinterpret_cast<float4*>(fr.r);
@@ -272,13 +294,13 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(g.upd_arrive + f, 1u);
-        if (prev == (unsigned)a.chunks - 1u) {  // last chunk of the frame: beta, stopping test
-          g.upd_arrive[f] = 0u;
+        const unsigned prev = atomicAdd(g.upd_arrive + gi, 1u);
+        if (prev == (unsigned)(a.chunks * fr.gsize) - 1u) {  // last chunk of the group: beta, stopping test
+          g.upd_arrive[gi] = 0u;
           __threadfence();
           if (s_active) {
             double rho_new = 0.0;
-            for (int i = 0; i < a.chunks; ++i) rho_new += __ldcg(g.part_upd + (size_t)f * a.chunks + i);
+            for (int i = 0; i < a.chunks * fr.gsize; ++i) rho_new += __ldcg(g.part_upd + (size_t)gi * a.chunks + i);
             const double rho0 = __ldcg(fr.rho0);
             __stcg(fr.iters, __ldcg(fr.iters) + 1);
             __stcg(fr.resid, sqrt(rho_new / rho0));
@@ -292,7 +314,7 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
             __stcg(fr.rho, rho_new);
           }
           __threadfence();
-          st_release(g.upd_ready + f, k + 1);
+          st_release(g.upd_ready + gi, k + 1);
         }
       }
     }

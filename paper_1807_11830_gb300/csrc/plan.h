@@ -24,6 +24,7 @@ struct sense_plan {
   int norm_tiles = 0;    // column tiles per frame of that variant
   int cg_mode = 1;       // 0: per-phase kernels replayed as CUDA graphs; 1: one persistent launch
   double lambda = 0.0;   // Tikhonov weight of CG: (E^H E + lambda I) x = E^H y
+  double lambda_t = 0.0; // temporal weight: > 0 couples the frames into one CG (persistent mode)
   cudaStream_t pool = nullptr;  // non-null: workspace is stream-ordered (cudaMallocAsync) on this stream
   CUtensorMap tmap_host;        // TMA descriptor of the maps S for the persistent kernel
   CUtensorMap* tmap_d = nullptr;
@@ -98,9 +99,10 @@ void record_error(const std::string& msg);
 sense_status plan_cg_start(sense_plan* pl, const void* y, const void* S, const int* lines, float2* x, double tol,
                            cudaStream_t st);
 
-// Frame-table entries of a plan's frames for the persistent CG kernel.
+// Frame-table entries of a plan's frames for the persistent CG kernel;
+// `base` is the table index of the plan's first frame.
 void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* x, int k0, double tol,
-                 PFrame* out);
+                 PFrame* out, int base);
 
 // A plan whose workspace comes from the device's stream-ordered pool on `st`
 // and whose twiddle tables are the caller's (shared per size): no device-wide

@@ -366,7 +366,7 @@ bool tick_device(sense_queue* q) {
     int off = 0;
     for (Request* r : kv.second) {
       r->status_off = off;
-      plan_frames(r->plan, r->maps, r->lines_d, r->x_d, r->ticks, r->tol, c.table_h + off);
+      plan_frames(r->plan, r->maps, r->lines_d, r->x_d, r->ticks, r->tol, c.table_h + off, off);
       for (int f = 0; f < r->sh.frames; ++f) c.table_h[off + f].kmax = r->max_iter;
       off += r->sh.frames;
     }

@@ -488,7 +488,7 @@ sense_status run_cg_persistent(sense_plan* pl, const void* S, const int* lines, 
   if (pl->ptable_key[0] != S || pl->ptable_key[1] != (const void*)lines || pl->ptable_key[2] != (const void*)x ||
       pl->ptable_tol != tol) {
     SENSE_CUDA_TRY(cudaStreamSynchronize(st));  // the staging copy may still be read by an earlier call
-    plan_frames(pl, S, lines, x, 0, tol, pl->ptable_host);
+    plan_frames(pl, S, lines, x, 0, tol, pl->ptable_host, 0);
     SENSE_CUDA_TRY(cudaMemcpyAsync(pl->ptable, pl->ptable_host, sizeof(PFrame) * F, cudaMemcpyHostToDevice, st));
     pl->ptable_key[0] = S;
     pl->ptable_key[1] = lines;
@@ -529,13 +529,20 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
   const void* maps = nullptr;  // what the normal-operator tiles read
   rc = plan_maps(pl, S, st, &maps);
   if (rc != SENSE_OK) return rc;
-  if (pl->cg_mode == 1) {
+  const int coupled = pl->lambda_t > 0.0 ? 1 : 0;
+  if (coupled) {  // one CG over all frames: the group's start scalars from the frames'
+    k_cg_couple_start<<<1, 32, 0, st>>>(pl->cg(tol), sh.frames);
+    rc = launch_status(cudaGetLastError(), "coupled CG start");
+    if (rc != SENSE_OK) return rc;
+  }
+  if (pl->cg_mode == 1 || coupled) {  // frames coupled in time run in the persistent kernel only
     if (max_iter > 0) rc = run_cg_persistent<St>(pl, maps, lines, x, max_iter, tol, st);
     if (rc != SENSE_OK) return rc;
     rc = plan_centred_output(pl, x, st);
     if (rc != SENSE_OK) return rc;
     PhaseScope ps(pl, SENSE_PHASE_CG_FINISH, st);
-    k_cg_finish<<<(sh.frames + 127) / 128, 128, 0, st>>>(pl->cg(tol), sh.frames, iters_out, resid_out, outcome_out);
+    k_cg_finish<<<(sh.frames + 127) / 128, 128, 0, st>>>(pl->cg(tol), sh.frames, iters_out, resid_out, outcome_out,
+                                                          coupled);
     return launch_status(cudaGetLastError(), "CG finish");
   }
   {  // kernel attributes are set outside stream capture
@@ -562,7 +569,7 @@ sense_status run_cg_solve(sense_plan* pl, const void* y, const void* S, const in
   rc = plan_centred_output(pl, x, st);
   if (rc != SENSE_OK) return rc;
   PhaseScope ps(pl, SENSE_PHASE_CG_FINISH, st);
-  k_cg_finish<<<(sh.frames + 127) / 128, 128, 0, st>>>(pl->cg(tol), sh.frames, iters_out, resid_out, outcome_out);
+  k_cg_finish<<<(sh.frames + 127) / 128, 128, 0, st>>>(pl->cg(tol), sh.frames, iters_out, resid_out, outcome_out, 0);
   return launch_status(cudaGetLastError(), "CG finish");
 }
 
@@ -614,11 +621,14 @@ sense_status plan_allocate(sense_plan* pl) {
 namespace sense {
 
 void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* x, int k0, double tol,
-                 PFrame* out) {
+                 PFrame* out, int base) {
   const sense_shape& sh = pl->sh;
+  const int F = sh.frames;
   const CgState g = pl->cg(0.0);
+  const bool coupled = pl->lambda_t > 0.0;
   for (int f = 0; f < sh.frames; ++f) {
     PFrame& fr = out[f];
+    const int sl = coupled ? 0 : f;  // scalar slot: coupled frames share the first frame's
     fr.S = S;
     fr.lines = lines + (size_t)f * sh.lines;
     fr.x = x + (size_t)f * pl->img;
@@ -626,14 +636,14 @@ void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* 
     fr.p[0] = pl->pp[0] + (size_t)f * pl->img;
     fr.p[1] = pl->pp[1] + (size_t)f * pl->img;
     fr.q = pl->q + (size_t)f * pl->img;
-    fr.rho = g.rho + f;
-    fr.rho0 = g.rho0 + f;
-    fr.alpha = g.alpha + f;
-    fr.beta = g.beta + f;
-    fr.resid = g.resid + f;
-    fr.iters = g.iters + f;
-    fr.outcome = g.outcome + f;
-    fr.active = g.active + f;
+    fr.rho = g.rho + sl;
+    fr.rho0 = g.rho0 + sl;
+    fr.alpha = g.alpha + sl;
+    fr.beta = g.beta + sl;
+    fr.resid = g.resid + sl;
+    fr.iters = g.iters + sl;
+    fr.outcome = g.outcome + sl;
+    fr.active = g.active + sl;
     fr.coils = sh.coils;
     fr.L = sh.lines;
     fr.tmap = pl->tmap_d;
@@ -641,6 +651,11 @@ void plan_frames(const sense_plan* pl, const void* S, const int* lines, float2* 
     fr.kmax = 1 << 30;
     fr.tol = tol;
     fr.lambda = (float)pl->lambda;
+    fr.g0 = coupled ? base : base + f;
+    fr.gsize = coupled ? F : 1;
+    fr.lambda_t = (float)pl->lambda_t;
+    fr.nb_prev = base + (f + F - 1) % F;
+    fr.nb_next = base + (f + 1) % F;
   }
 }
 
@@ -649,8 +664,11 @@ sense_status plan_cg_start(sense_plan* pl, const void* y, const void* S, const i
   const sense_shape& sh = pl->sh;
   SENSE_CUDA_TRY(cudaMemsetAsync(pl->counter, 0, sizeof(unsigned) * sh.frames, st));
   SENSE_CUDA_TRY(cudaMemsetAsync(pl->cg(tol).live, 0, sizeof(int), st));
-  if (sh.storage == SENSE_STORE_BF16) return run_adjoint<StBF16>(pl, 1, y, S, lines, x, nullptr, tol, st);
-  return run_adjoint<StC64>(pl, 1, y, S, lines, x, nullptr, tol, st);
+  sense_status rc = sh.storage == SENSE_STORE_BF16 ? run_adjoint<StBF16>(pl, 1, y, S, lines, x, nullptr, tol, st)
+                                                   : run_adjoint<StC64>(pl, 1, y, S, lines, x, nullptr, tol, st);
+  if (rc != SENSE_OK || pl->lambda_t <= 0.0) return rc;
+  k_cg_couple_start<<<1, 32, 0, st>>>(pl->cg(tol), sh.frames);
+  return launch_status(cudaGetLastError(), "coupled CG start");
 }
 
 std::vector<float2> plan_twiddles(int n) { return twiddles(n); }
@@ -748,7 +766,8 @@ sense_status plan_set_variant_nosync(sense_plan* pl, int variant) {
 
 sense_status plan_cg_finish(sense_plan* pl, int* iters_out, double* resid_out, int* outcome_out, cudaStream_t st) {
   const int F = pl->sh.frames;
-  k_cg_finish<<<(F + 127) / 128, 128, 0, st>>>(pl->cg(0.0), F, iters_out, resid_out, outcome_out);
+  k_cg_finish<<<(F + 127) / 128, 128, 0, st>>>(pl->cg(0.0), F, iters_out, resid_out, outcome_out,
+                                                pl->lambda_t > 0.0 ? 1 : 0);
   return launch_status(cudaGetLastError(), "CG finish");
 }
 
@@ -926,6 +945,18 @@ sense_status sense_plan_set_variant(sense_plan* pl, int variant) {
 }
 
 int sense_plan_variant(const sense_plan* pl) { return pl ? pl->norm_variant : -1; }
+
+sense_status sense_plan_set_temporal(sense_plan* pl, double lambda_t) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (!(lambda_t >= 0.0) || !std::isfinite(lambda_t) || lambda_t > 3.0e38)
+    return fail(SENSE_EINVAL, "lambda_t must be finite, >= 0 and representable in FP32");
+  if (lambda_t == pl->lambda_t) return SENSE_OK;
+  DeviceGuard guard(pl->device);
+  cudaDeviceSynchronize();
+  pl->ptable_key[0] = nullptr;  // the persistent frame table bakes the coupling in
+  pl->lambda_t = lambda_t;
+  return SENSE_OK;
+}
 
 sense_status sense_plan_set_lambda(sense_plan* pl, double lambda) {
   if (!pl) return fail(SENSE_EINVAL, "plan is NULL");

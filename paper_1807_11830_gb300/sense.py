@@ -35,6 +35,7 @@ EXPORTED = (
     "sense_plan_check", "sense_last_error", "sense_plan_set_timing", "sense_plan_phase_time",
     "sense_adjoint_noalloc", "sense_plan_set_variant", "sense_plan_variant", "sense_plan_autotune",
     "sense_plan_set_cg_mode", "sense_selftest_wait", "sense_plan_set_lambda", "sense_batch_set_lambda",
+    "sense_plan_set_temporal", "sense_batch_set_temporal",
     "sense_batch_create", "sense_batch_destroy", "sense_batch_workspace_bytes", "sense_batch_classes",
     "sense_batch_autotune", "sense_batch_set_variant", "sense_batch_cg_solve", "sense_batch_check",
     "sense_queue_create", "sense_queue_submit", "sense_queue_poll", "sense_queue_wait", "sense_queue_cancel",
@@ -134,6 +135,10 @@ def load_library(path=LIB_PATH):
     lib.sense_plan_set_lambda.restype = st
     lib.sense_batch_set_lambda.argtypes = [vp, i, ctypes.c_double]
     lib.sense_batch_set_lambda.restype = st
+    lib.sense_plan_set_temporal.argtypes = [vp, ctypes.c_double]
+    lib.sense_plan_set_temporal.restype = st
+    lib.sense_batch_set_temporal.argtypes = [vp, i, ctypes.c_double]
+    lib.sense_batch_set_temporal.restype = st
     lib.sense_plan_autotune.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), vp]
     lib.sense_plan_autotune.restype = st
     lib.sense_plan_set_cg_mode.argtypes = [vp, i]
@@ -308,6 +313,15 @@ def sense_plan_set_lambda(plan, lam):
 
 def sense_batch_set_lambda(batch, instance, lam):
     _check(load_library().sense_batch_set_lambda(batch.handle, int(instance), float(lam)))
+
+
+def sense_plan_set_temporal(plan, lam_t):
+    """Couple the plan's frames in time: one CG on (E^H E + lam I + lam_t L) x = E^H y."""
+    _check(load_library().sense_plan_set_temporal(plan.handle, float(lam_t)))
+
+
+def sense_batch_set_temporal(batch, instance, lam_t):
+    _check(load_library().sense_batch_set_temporal(batch.handle, int(instance), float(lam_t)))
 
 
 def sense_plan_set_cg_mode(plan, mode):
