@@ -92,9 +92,9 @@ SENSE_NORM_VARIANT(256, 1, 2, WCol<32, 8, Radices<8, 4, 8>, Pads<Pad<8, 5>, Pad<
 SENSE_NORM_VARIANT(256, 2, 1, WCol<16, 8, Radices<16, 16>, Pads<Pad<1, 4>>>)
 SENSE_NORM_VARIANT(256, 3, 2, Col<32, 8, Radices<8, 4, 8>>)
 SENSE_NORM_VARIANT(320, 1, 1, Col<20, 16, Radices<16, 20>>)
-SENSE_NORM_VARIANT(320, 2, 2, Col<40, 8, Radices<8, 4, 10>>)
+SENSE_NORM_VARIANT(320, 2, 1, Col<40, 8, Radices<8, 4, 10>>)
 SENSE_NORM_VARIANT(384, 1, 1, Col<24, 16, Radices<16, 24>>)
-SENSE_NORM_VARIANT(384, 2, 2, Col<48, 8, Radices<8, 4, 12>>)
+SENSE_NORM_VARIANT(384, 2, 1, Col<48, 8, Radices<8, 4, 12>>)
 #undef SENSE_NORM_VARIANT
 constexpr int kNormVariants = 4;
 
