@@ -242,8 +242,10 @@ typedef struct {
   int fake_tick_us;
   int fake_iters;
   int autotune;            /* 1: autotune each size class on its first request; 0: variant 0 */
-  int iters_per_tick;      /* CG iterations per tick (0 = 10); each frame still stops at its own
-                              max_iter / tolerance inside the tick, new requests join between ticks */
+  int iters_per_tick;      /* CG iterations per tick; each frame still stops at its own max_iter /
+                              tolerance inside the tick, new requests join between ticks.  0: 10,
+                              stretched up to 80 (the largest remaining budget of the live requests)
+                              while no request waits for admission */
 } sense_queue_cfg;
 
 typedef enum {

@@ -351,7 +351,23 @@ bool retire_enqueue(sense_queue* q, Request* r) {
 // synchronisation completes those, and their memory is released in stream
 // order.
 bool tick_device(sense_queue* q) {
-  const int m = q->cfg.iters_per_tick > 0 ? q->cfg.iters_per_tick : 10;
+  // Iterations per tick: the configured number, or by default 10, stretched
+  // while nothing waits for admission (up to the largest remaining budget of
+  // the live requests, at most 80) so a lone request is not cut into many
+  // host round trips.
+  int m = q->cfg.iters_per_tick > 0 ? q->cfg.iters_per_tick : 10;
+  if (q->cfg.iters_per_tick <= 0) {
+    bool waiting;
+    {
+      std::lock_guard<std::mutex> lock(q->mu);
+      waiting = !q->pending.empty();
+    }
+    if (!waiting) {
+      int remaining = 0;
+      for (Request* r : q->live) remaining = std::max(remaining, r->max_iter - r->ticks);
+      m = std::max(m, std::min(remaining, 8 * m));
+    }
+  }
   std::map<std::tuple<int, int, int>, std::vector<Request*>> by_class;
   for (Request* r : q->live) by_class[std::make_tuple(r->sh.ny, r->sh.nx, r->sh.storage)].push_back(r);
   std::vector<std::pair<SizeClass*, int>> launched;
