@@ -494,6 +494,59 @@ struct WCol {
     sync();
     inv_last(buf[(2 * S - 3) & 1], x, tw);
   }
+
+  // Stage-0 twiddles of this lane held in registers: w[j][k-1] = table
+  // entry (k - 1) P_0 + b for butterfly b = t + T j (the same for every
+  // transform the lane runs), with fwd / inv overloads that use them.
+  struct Tw0 {
+    float2 w[J0][R0 - 1];
+  };
+  __device__ __forceinline__ Tw0 load_tw0(const float2* tw) const {
+    Tw0 r;
+#pragma unroll
+    for (int j = 0; j < J0; ++j)
+#pragma unroll
+      for (int k = 1; k < R0; ++k)
+        r.w[j][k - 1] = ok<0>(j) ? tw[twoff(0) + (k - 1) * P0 + t + T * j] : make_float2(1.f, 0.f);
+    return r;
+  }
+  __device__ __forceinline__ void fwd(float2 (&x)[J0][R0], float2 (&kr)[JL][RL], float2* const* buf,
+                                      const float2* tw, const Tw0& w0) const {
+#pragma unroll
+    for (int j = 0; j < J0; ++j) {
+      if (!ok<0>(j)) continue;
+      const int b = t + T * j;
+      Dft<R0, -1>::run(x[j]);
+#pragma unroll
+      for (int k = 0; k < R0; ++k) {
+        float2 v = x[j][k];
+        if (k > 0) v = cmul(v, w0.w[j][k - 1]);
+        buf[0][sidx<0>(k * P0 + b)] = v;
+      }
+    }
+    fwd_mids<1>(buf, tw);
+    sync();
+    fwd_last(buf[(S - 2) & 1], kr);
+  }
+  __device__ __forceinline__ void inv(float2 (&kr)[JL][RL], float2 (&x)[J0][R0], float2* const* buf,
+                                      const float2* tw, const Tw0& w0) const {
+    inv_first(kr, buf[(S - 1) & 1]);
+    inv_mids<S - 2>(buf, tw);
+    sync();
+    const float2* in = buf[(2 * S - 3) & 1];
+#pragma unroll
+    for (int j = 0; j < J0; ++j) {
+      if (!ok<0>(j)) continue;
+      const int b = t + T * j;
+#pragma unroll
+      for (int k = 0; k < R0; ++k) {
+        float2 w = in[sidx<0>(k * P0 + b)];
+        if (k > 0) w = cmulc(w, w0.w[j][k - 1]);
+        x[j][k] = w;
+      }
+      Dft<R0, 1>::run(x[j]);
+    }
+  }
 };
 
 template <class C>

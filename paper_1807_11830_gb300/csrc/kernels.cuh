@@ -849,6 +849,7 @@ __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSm
     }
 
   float2* bufs[2] = {s.buf0, s.buf1};
+  const typename C::Tw0 w0 = col.load_tw0(s.tw);
   const int cw = col.c - warp * CW;  // column within the warp
 #pragma unroll 1
   for (int c = 0; c < a.coils; ++c) {
@@ -866,13 +867,13 @@ __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSm
         const float2 sv = col.ok0(j) ? St::lds(sc, col.xrow(j, n)) : make_float2(0.f, 0.f);
         xr[j][n] = cmul(sv, p[j][n]);
       }
-    col.fwd(xr, kr, bufs, s.tw);
+    col.fwd(xr, kr, bufs, s.tw, w0);
 #pragma unroll
     for (int j = 0; j < C::JL; ++j)
 #pragma unroll
       for (int m = 0; m < C::RL; ++m)
         if (!((keep >> (j * C::RL + m)) & 1u)) kr[j][m] = make_float2(0.f, 0.f);
-    col.inv(kr, xr, bufs, s.tw);
+    col.inv(kr, xr, bufs, s.tw, w0);
 #pragma unroll
     for (int j = 0; j < C::J0; ++j)
 #pragma unroll
