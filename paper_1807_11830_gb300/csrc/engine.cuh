@@ -498,8 +498,13 @@ struct WCol {
   // Stage-0 twiddles of this lane held in registers: w[j][k-1] = table
   // entry (k - 1) P_0 + b for butterfly b = t + T j (the same for every
   // transform the lane runs), with fwd / inv overloads that use them.
+  // With three stages and T a multiple of P_1, stage 1's twiddles depend on
+  // the lane only (r = t mod P_1 for every butterfly of the lane): w1 holds them.
+  static constexpr bool TW1 = (S == 3) && (T % St<1>::P == 0);
+  static constexpr int R1 = St<1>::R;
   struct Tw0 {
     float2 w[J0][R0 - 1];
+    float2 w1[TW1 ? R1 - 1 : 1];
   };
   __device__ __forceinline__ Tw0 load_tw0(const float2* tw) const {
     Tw0 r;
@@ -508,7 +513,52 @@ struct WCol {
 #pragma unroll
       for (int k = 1; k < R0; ++k)
         r.w[j][k - 1] = ok<0>(j) ? tw[twoff(0) + (k - 1) * P0 + t + T * j] : make_float2(1.f, 0.f);
+    if constexpr (TW1) {
+#pragma unroll
+      for (int k = 1; k < R1; ++k) r.w1[k - 1] = tw[twoff(1) + (k - 1) * St<1>::P + t % St<1>::P];
+    }
     return r;
+  }
+  // stage 1 with register twiddles (forward and inverse)
+  __device__ __forceinline__ void fwd_mid1(const float2* in, float2* out, const Tw0& w0) const {
+    using G = St<1>;
+    constexpr int Pp = G::P * G::R;
+#pragma unroll
+    for (int j = 0; j < G::J; ++j) {
+      if (!ok<1>(j)) continue;
+      const int b = t + T * j;
+      const int kk = b / G::P, r = b - kk * G::P;
+      float2 v[G::R];
+#pragma unroll
+      for (int n = 0; n < G::R; ++n) v[n] = in[sidx<0>(kk * Pp + n * G::P + r)];
+      Dft<G::R, -1>::run(v);
+#pragma unroll
+      for (int k = 0; k < G::R; ++k) {
+        float2 w = v[k];
+        if (k > 0) w = cmul(w, w0.w1[k - 1]);
+        out[sidx<1>((kk + G::Q * k) * G::P + r)] = w;
+      }
+    }
+  }
+  __device__ __forceinline__ void inv_mid1(const float2* in, float2* out, const Tw0& w0) const {
+    using G = St<1>;
+    constexpr int Pp = G::P * G::R;
+#pragma unroll
+    for (int j = 0; j < G::J; ++j) {
+      if (!ok<1>(j)) continue;
+      const int b = t + T * j;
+      const int kk = b / G::P, r = b - kk * G::P;
+      float2 v[G::R];
+#pragma unroll
+      for (int k = 0; k < G::R; ++k) {
+        float2 w = in[sidx<1>((kk + G::Q * k) * G::P + r)];
+        if (k > 0) w = cmulc(w, w0.w1[k - 1]);
+        v[k] = w;
+      }
+      Dft<G::R, 1>::run(v);
+#pragma unroll
+      for (int n = 0; n < G::R; ++n) out[sidx<0>(kk * Pp + n * G::P + r)] = v[n];
+    }
   }
   __device__ __forceinline__ void fwd(float2 (&x)[J0][R0], float2 (&kr)[JL][RL], float2* const* buf,
                                       const float2* tw, const Tw0& w0) const {
@@ -524,14 +574,24 @@ struct WCol {
         buf[0][sidx<0>(k * P0 + b)] = v;
       }
     }
-    fwd_mids<1>(buf, tw);
+    if constexpr (TW1) {
+      sync();
+      fwd_mid1(buf[0], buf[1], w0);
+    } else {
+      fwd_mids<1>(buf, tw);
+    }
     sync();
     fwd_last(buf[(S - 2) & 1], kr);
   }
   __device__ __forceinline__ void inv(float2 (&kr)[JL][RL], float2 (&x)[J0][R0], float2* const* buf,
                                       const float2* tw, const Tw0& w0) const {
     inv_first(kr, buf[(S - 1) & 1]);
-    inv_mids<S - 2>(buf, tw);
+    if constexpr (TW1) {
+      sync();
+      inv_mid1(buf[(S - 1) & 1], buf[S & 1], w0);  // S = 3: exchange e_in = 2, written to 3
+    } else {
+      inv_mids<S - 2>(buf, tw);
+    }
     sync();
     const float2* in = buf[(2 * S - 3) & 1];
 #pragma unroll
