@@ -258,6 +258,75 @@ struct Col {
       inv_last(buf[(2 * S - 3) & 1], x, tw);
     }
   }
+
+  // Stage-0 (and, with three stages and T a multiple of P_1, stage-1)
+  // twiddles of this thread held in registers: they depend only on the
+  // thread's phase, so a kernel that runs many transforms loads them once.
+  static constexpr bool TW1 = (S == 3) && (T % St<1>::P == 0);
+  static constexpr int R1 = S > 1 ? St<1>::R : 2;
+  struct Tw0 {
+    float2 w[J0][R0 - 1];
+    float2 w1[TW1 ? R1 - 1 : 1];
+  };
+  __device__ __forceinline__ Tw0 load_tw0(const float2* tw) const {
+    Tw0 r;
+#pragma unroll
+    for (int j = 0; j < J0; ++j)
+#pragma unroll
+      for (int k = 1; k < R0; ++k) r.w[j][k - 1] = ok<0>(j) ? tw[(t + T * j) * k] : make_float2(1.f, 0.f);
+    if constexpr (TW1) {
+#pragma unroll
+      for (int k = 1; k < R1; ++k) r.w1[k - 1] = tw[(t % St<1>::P) * k * St<1>::Q];
+    }
+    return r;
+  }
+  __device__ __forceinline__ void inv(float2 (&kr)[JL][RL], float2 (&x)[J0][R0], float2* const* buf,
+                                      const float2* tw, const Tw0& w0) const {
+    if constexpr (S == 1) {
+      inv(kr, x, buf, tw);
+    } else {
+      inv_first(kr, buf[(S - 1) & 1]);
+      if constexpr (TW1) {
+        __syncthreads();
+        using G = St<1>;
+        constexpr int Pp = G::P * G::R;
+        const float2* in = buf[(S - 1) & 1];
+        float2* out = buf[S & 1];
+#pragma unroll
+        for (int j = 0; j < G::J; ++j) {
+          if (!ok<1>(j)) continue;
+          const int b = t + T * j;
+          const int kk = b / G::P, r = b - kk * G::P;
+          float2 v[G::R];
+#pragma unroll
+          for (int k = 0; k < G::R; ++k) {
+            float2 w = in[sidx((kk + G::Q * k) * G::P + r)];
+            if (k > 0) w = cmulc(w, w0.w1[k - 1]);
+            v[k] = w;
+          }
+          Dft<G::R, 1>::run(v);
+#pragma unroll
+          for (int n = 0; n < G::R; ++n) out[sidx(kk * Pp + n * G::P + r)] = v[n];
+        }
+      } else {
+        inv_mids<S - 2>(buf, tw);
+      }
+      __syncthreads();
+      const float2* in = buf[(2 * S - 3) & 1];
+#pragma unroll
+      for (int j = 0; j < J0; ++j) {
+        if (!ok<0>(j)) continue;
+        const int b = t + T * j;
+#pragma unroll
+        for (int k = 0; k < R0; ++k) {
+          float2 w = in[sidx(k * P0 + b)];
+          if (k > 0) w = cmulc(w, w0.w[j][k - 1]);
+          x[j][k] = w;
+        }
+        Dft<R0, 1>::run(x[j]);
+      }
+    }
+  }
 };
 
 // ---------------------------------------------------------------------------

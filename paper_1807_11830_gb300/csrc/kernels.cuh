@@ -358,6 +358,11 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St>
         sv[j][n] = (MODE != 2 && col.ok0(j) && xin) ? St::ld(a.S, c * img + (size_t)col.xrow(j, n) * a.nx + x)
                                                     : make_float2(0.f, 0.f);
   };
+  // Register twiddles (loaded once, reused by every coil) where the register
+  // budget has room: RSS mode, or a cap of at least 160 registers per thread.
+  constexpr bool REG_TW = MODE == 2 || 65536 / (C::THREADS * ColPass<N>::MINB) >= 160;
+  typename C::Tw0 w0;
+  if constexpr (REG_TW) w0 = col.load_tw0(s.tw);
   float2 knext[C::JL][C::RL];
   float2 snext[C::J0][C::R0];
   if (PREFETCH && a.coils > 0) {
@@ -393,7 +398,10 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St>
         for (int m = 0; m < C::RL; ++m) kr[j][m] = negate_if(kr[j][m], col.krow(j, m) & 1);
     }
     const BufPair<C> bp(s.buf0, s.buf1, c);
-    col.inv(kr, xr, bp.b, s.tw);
+    if constexpr (REG_TW)
+      col.inv(kr, xr, bp.b, s.tw, w0);
+    else
+      col.inv(kr, xr, bp.b, s.tw);
 #pragma unroll
     for (int j = 0; j < C::J0; ++j)
 #pragma unroll
