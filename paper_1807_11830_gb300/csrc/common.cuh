@@ -85,9 +85,10 @@ struct NormCfg {
     static constexpr int MINB = MINB_;           \
   };
 SENSE_NORM_VARIANT(128, 1, 1, Col<8, 32, Radices<16, 8>>)
-SENSE_NORM_VARIANT(128, 2, 4, Col<16, 16, Radices<8, 4, 4>>)
+SENSE_NORM_VARIANT(128, 2, 4, WCol<16, 8, Radices<8, 4, 4>, Pads<Pad<4, 4>, Pad<1, 4>>>)
 SENSE_NORM_VARIANT(192, 1, 1, Col<16, 16, Radices<12, 16>>)
 SENSE_NORM_VARIANT(192, 2, 2, Col<24, 16, Radices<8, 3, 8>>)
+SENSE_NORM_VARIANT(192, 3, 2, WCol<32, 8, Radices<8, 3, 8>, Pads<Pad<0, 2>, Pad<1, 4>>>)
 SENSE_NORM_VARIANT(256, 1, 2, WCol<32, 8, Radices<8, 4, 8>, Pads<Pad<8, 5>, Pad<1, 4>>>)
 SENSE_NORM_VARIANT(256, 2, 1, WCol<16, 8, Radices<16, 16>, Pads<Pad<1, 4>>>)
 SENSE_NORM_VARIANT(256, 3, 2, Col<32, 8, Radices<8, 4, 8>>)
