@@ -41,8 +41,8 @@ UNIT = "applications/s"
 FLUSH_BYTES = 512 << 20
 # ncu DRAM traffic of k_cg_persistent on this workload, bytes per CG iteration,
 # keyed by (kernel variant, CG mode): the lane-major 256-point variant in the
-# persistent kernel (38.1 MB read + 113.6 MB written over 30 iterations)
-CINE_TRAFFIC_PER_ITER = {(1, "persistent"): (38.057984e6 + 113.609984e6) / 30}
+# persistent kernel (40.4 MB read + 173.2 MB written over 30 iterations)
+CINE_TRAFFIC_PER_ITER = {(1, "persistent"): (40.359936e6 + 173.227776e6) / 30}
 PAPER_WORKLOAD = ("paper reconstruction: 16 frames x 160x160, 8 coils, fully sampled; "
                   "2D inverse FFT + root-sum-of-squares (Sec. V)")
 PAPER_METRIC, PAPER_UNIT = "reconstructions/s", "reconstructions/s"
