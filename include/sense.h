@@ -55,7 +55,7 @@ typedef enum {
   SENSE_ENOMEM = 3,             /* device allocation failed */
   SENSE_ECUDA = 4,              /* a CUDA runtime call failed */
   SENSE_ETIMEOUT = 5,           /* a bounded device-side wait gave up */
-  SENSE_ENUMERIC = 6,           /* CG breakdown: Re<p, E^H E p> not > 0 (or NaN) */
+  SENSE_ENUMERIC = 6,           /* non-finite CG values: NaN or Inf in a request's y or S (sense_queue_wait) */
   SENSE_EQUEUE_FULL = 7,        /* request queue cannot admit more work */
   SENSE_ENOTFOUND = 8,          /* unknown request id */
   SENSE_EDEVICE = 9             /* a kernel flagged invalid input (bad line index/order) */
@@ -246,6 +246,9 @@ typedef struct {
                               tolerance inside the tick, new requests join between ticks.  0: 10,
                               stretched up to 80 (the largest remaining budget of the live requests)
                               while no request waits for admission */
+  int fail_admit_every;    /* test hook, 0 = off: every k-th admission fails as if a device allocation
+                              had failed (after the others succeeded); the request ends FAILED and
+                              sense_queue_wait returns SENSE_ENOMEM */
 } sense_queue_cfg;
 
 typedef enum {
@@ -261,6 +264,13 @@ typedef struct {
   int live, pending;
 } sense_queue_stats;
 
+/* cfg may be NULL (all fields 0).  When the environment variable
+ * SENSE_QUEUE_LOG names a file, the queue appends one JSON line per request
+ * that leaves it (completed, failed or cancelled): id, shape, state, status,
+ * submit_ms / admit_ms / first_tick_ms / done_ms (milliseconds since the
+ * queue was created; first_tick_ms is the end of the request's first tick),
+ * latency_ms, ticks, max_iter, and for completed requests the largest
+ * per-frame iteration count and relative residual (null if not finite). */
 sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_queue** out);
 /* Copies the inputs (host memory, layouts of sense_cg_solve) into pinned
  * staging before returning; the caller's buffers are free on return.  A
@@ -273,7 +283,11 @@ sense_status sense_queue_poll(sense_queue* q, uint64_t req_id, int* state, int* 
  * SENSE_ETIMEOUT), then copy its image [frames][ny][nx] and, if non-NULL,
  * per-frame iterations / relative residuals / outcomes to host memory and
  * forget the request.  SENSE_ENOTFOUND for unknown ids, SENSE_EINVAL for a
- * cancelled request. */
+ * cancelled request, SENSE_ENOMEM or SENSE_ECUDA for a request that failed
+ * (admission or device work; sense_last_error says which).  SENSE_ENUMERIC
+ * when a frame stopped in breakdown with a non-finite residual -- its input
+ * held NaN or Inf; the outputs are still copied, and that frame's image is
+ * its last finite iterate (zero when b = E^H y itself is not finite). */
 sense_status sense_queue_wait(sense_queue* q, uint64_t req_id, sense_c32* x_host, int32_t* iters_host,
                               double* resid_host, int32_t* outcome_host, double timeout_s);
 /* Cancel a pending or running request (it stops at the next tick boundary). */

@@ -107,9 +107,10 @@ __global__ void k_cg_couple_start(CgState g, int frames) {
   g.iters[0] = 0;
   g.alpha[0] = 0.0;
   g.beta[0] = 0.0;
-  g.active[0] = rho > 0.0 ? 1 : 0;
-  g.outcome[0] = rho > 0.0 ? CG_RUNNING : CG_CONVERGED;
-  g.resid[0] = rho > 0.0 ? 1.0 : 0.0;
+  const bool run = rho > 0.0 && isfinite(rho);  // not finite: NaN/Inf input, breakdown with residual NaN
+  g.active[0] = run ? 1 : 0;
+  g.outcome[0] = run ? CG_RUNNING : (rho == 0.0 ? CG_CONVERGED : CG_BREAKDOWN);
+  g.resid[0] = run ? 1.0 : (rho == 0.0 ? 0.0 : rho - rho);
 }
 
 // CG iterates of a centred-k-space problem live in the modulated space

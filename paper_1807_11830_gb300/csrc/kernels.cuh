@@ -448,15 +448,15 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St>
       g.iters[f] = 0;
       g.beta[f] = 0.0;
       g.alpha[f] = 0.0;
-      if (rho > 0.0) {
+      if (rho > 0.0 && isfinite(rho)) {
         g.active[f] = 1;
         g.outcome[f] = CG_RUNNING;
         g.resid[f] = 1.0;
         atomicAdd(g.live, 1);
-      } else {
+      } else {  // b = 0 (converged at once) or not finite (NaN/Inf input: breakdown, residual NaN)
         g.active[f] = 0;
         g.outcome[f] = (rho == 0.0) ? CG_CONVERGED : CG_BREAKDOWN;
-        g.resid[f] = 0.0;
+        g.resid[f] = (rho == 0.0) ? 0.0 : rho - rho;
       }
     }
   }

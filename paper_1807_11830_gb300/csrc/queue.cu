@@ -15,10 +15,19 @@
 // fake_device mode runs the same scheduler with no GPU work (each tick
 // sleeps; every frame stops after min(max_iter, fake_iters) ticks), so
 // admission, ordering, refusal and cancellation are testable on a CPU.
+//
+// With SENSE_QUEUE_LOG set to a path, every request that leaves the queue
+// appends one JSON line there: its shape, final state and status, the times
+// of submission, admission, end of its first tick and completion (ms since
+// the queue was created), ticks applied, largest per-frame iteration count
+// and relative residual.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -73,7 +82,10 @@ struct Request {
   bool cancel = false;
   int status_off = 0;  // position of its frames in the tick's status array
   int cls = -1;
-  Clock::time_point t_submit, t_done;
+  Clock::time_point t_submit, t_admit, t_first, t_done;
+  bool admitted = false, ticked = false;
+  sense_status fail_status = SENSE_ECUDA;  // what sense_queue_wait reports for a failed request
+  std::string fail_msg = "request failed on the device";
 };
 
 struct SizeClass {
@@ -107,6 +119,9 @@ struct sense_queue {
   std::thread worker;
   sense_queue_stats st{};
   std::vector<double> lat_ms;
+  uint64_t admissions = 0;      // counts admissions for the fail_admit_every test hook
+  FILE* log = nullptr;          // per-request JSON lines (SENSE_QUEUE_LOG), written under mu
+  Clock::time_point t0;         // creation time, origin of the logged times
   cudaStream_t stream = nullptr;
   int sms = 0;
   std::map<std::tuple<int, int, int>, SizeClass> classes;  // worker thread only
@@ -201,10 +216,52 @@ size_t request_need(const sense_shape& sh) {
   return inputs + outputs + plan + (size_t)(1 << 20);
 }
 
+double ms_since(const sense_queue* q, Clock::time_point t) {
+  return std::chrono::duration<double, std::milli>(t - q->t0).count();
+}
+
+// One JSON line per request leaving the queue (caller holds q->mu).
+void log_request(sense_queue* q, const Request* r) {
+  if (!q->log) return;
+  static const char* kState[] = {"pending", "running", "done", "cancelled", "failed"};
+  const int s = (r->state >= 0 && r->state <= SENSE_REQ_FAILED) ? r->state : SENSE_REQ_FAILED;
+  const int status = r->state == SENSE_REQ_FAILED ? (int)r->fail_status : 0;
+  std::fprintf(q->log,
+               "{\"id\": %llu, \"ny\": %d, \"nx\": %d, \"coils\": %d, \"frames\": %d, \"lines\": %d, "
+               "\"storage\": \"%s\", \"centred\": %d, \"state\": \"%s\", \"status\": %d, \"submit_ms\": %.3f",
+               (unsigned long long)r->id, r->sh.ny, r->sh.nx, r->sh.coils, r->sh.frames, r->sh.lines,
+               r->sh.storage == SENSE_STORE_BF16 ? "bf16" : "c64", r->sh.centred, kState[s], status,
+               ms_since(q, r->t_submit));
+  if (r->admitted) std::fprintf(q->log, ", \"admit_ms\": %.3f", ms_since(q, r->t_admit));
+  if (r->ticked) std::fprintf(q->log, ", \"first_tick_ms\": %.3f", ms_since(q, r->t_first));
+  std::fprintf(q->log, ", \"done_ms\": %.3f, \"latency_ms\": %.3f, \"ticks\": %d, \"max_iter\": %d",
+               ms_since(q, r->t_done), std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count(),
+               r->ticks, r->max_iter);
+  if (r->state == SENSE_REQ_DONE && r->iters_h && r->resid_h) {
+    int it = 0;
+    double res = 0.0;
+    bool finite = true;
+    for (int f = 0; f < r->sh.frames; ++f) {
+      it = std::max(it, r->iters_h[f]);
+      if (std::isfinite(r->resid_h[f]))
+        res = std::max(res, r->resid_h[f]);
+      else
+        finite = false;
+    }
+    if (finite)
+      std::fprintf(q->log, ", \"iters\": %d, \"max_rel_resid\": %.6e", it, res);
+    else
+      std::fprintf(q->log, ", \"iters\": %d, \"max_rel_resid\": null", it);
+  }
+  std::fputs("}\n", q->log);
+  std::fflush(q->log);
+}
+
 void record_done(sense_queue* q, Request* r, int state) {
   std::lock_guard<std::mutex> lock(q->mu);
   r->state = state;
   r->t_done = Clock::now();
+  log_request(q, r);
   if (state == SENSE_REQ_DONE) {
     q->st.completed++;
     q->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
@@ -260,7 +317,9 @@ const float2* twiddle_table(sense_queue* q, int n) {
 // Upload inputs, create the plan (stream-ordered workspace, shared twiddle
 // tables), start CG.  Everything is queued on the queue's stream; nothing
 // synchronises.  Returns false on failure.
-bool admit_device(sense_queue* q, Request* r, std::string* err) {
+// inject_fail (test hook): fail as if the last device allocation had failed,
+// after the others succeeded, so the partial clean-up runs.
+bool admit_device(sense_queue* q, Request* r, std::string* err, bool inject_fail) {
   const sense_shape& sh = r->sh;
   const size_t F = sh.frames;
   cudaStream_t st = q->stream;
@@ -281,6 +340,10 @@ bool admit_device(sense_queue* q, Request* r, std::string* err) {
             cudaMallocAsync((void**)&r->x_d, r->x_bytes, st) == cudaSuccess &&
             cudaMallocAsync((void**)&r->out_i_d, sizeof(int) * 2 * F, st) == cudaSuccess &&
             cudaMallocAsync((void**)&r->resid_d, sizeof(double) * F, st) == cudaSuccess;
+  if (ok && inject_fail) {
+    *err = "device allocation failed (injected by the fail_admit_every test hook)";
+    return false;
+  }
   if (!ok) {
     cudaGetLastError();
     *err = "device allocation failed";
@@ -421,8 +484,13 @@ bool tick_device(sense_queue* q) {
   }
   if (cudaStreamSynchronize(q->stream) != cudaSuccess) return false;
   std::vector<Request*> still, finished, cancelled;
+  const Clock::time_point now = Clock::now();
   for (Request* r : q->live) {
     r->ticks = std::min(r->ticks + m, r->max_iter);
+    if (!r->ticked) {
+      r->ticked = true;
+      r->t_first = now;
+    }
     const SizeClass* c = launched[r->cls].first;
     bool any = false;
     for (int f = 0; f < r->sh.frames; ++f) any |= c->status_h[r->status_off + f] != 0;
@@ -458,8 +526,13 @@ bool tick_device(sense_queue* q) {
 void tick_fake(sense_queue* q) {
   if (q->cfg.fake_tick_us > 0) std::this_thread::sleep_for(std::chrono::microseconds(q->cfg.fake_tick_us));
   std::vector<Request*> still;
+  const Clock::time_point now = Clock::now();
   for (Request* r : q->live) {
     r->ticks++;
+    if (!r->ticked) {
+      r->ticked = true;
+      r->t_first = now;
+    }
     bool cancel;
     {
       std::lock_guard<std::mutex> lock(q->mu);
@@ -506,6 +579,7 @@ void worker_main(sense_queue* q) {
           r->state = SENSE_REQ_CANCELLED;
           r->t_done = Clock::now();
           q->st.cancelled++;
+          log_request(q, r);
           q->cv_done.notify_all();
           continue;
         }
@@ -515,16 +589,28 @@ void worker_main(sense_queue* q) {
         q->pending.pop_front();
         q->in_use += r->need;
         r->state = SENSE_REQ_RUNNING;
+        r->admitted = true;
+        r->t_admit = Clock::now();
         q->st.admitted++;
         admit.push_back(r);
       }
     }
     for (Request* r : admit) {
       std::string err;
-      if (q->cfg.fake_device || admit_device(q, r, &err)) {
+      const bool inject = q->cfg.fail_admit_every > 0 && ++q->admissions % (uint64_t)q->cfg.fail_admit_every == 0;
+      bool ok;
+      if (q->cfg.fake_device) {
+        ok = !inject;
+        if (inject) err = "device allocation failed (injected by the fail_admit_every test hook)";
+      } else {
+        ok = admit_device(q, r, &err, inject);
+      }
+      if (ok) {
         q->live.push_back(r);
       } else {
-        free_device(r, q->stream);
+        if (!q->cfg.fake_device) free_device(r, q->stream);
+        r->fail_status = err.rfind("device allocation failed", 0) == 0 ? SENSE_ENOMEM : SENSE_ECUDA;
+        r->fail_msg = "admission failed: " + err;
         record_done(q, r, SENSE_REQ_FAILED);
       }
     }
@@ -570,9 +656,11 @@ extern "C" {
 sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_queue** out) {
   if (!out) return qfail(SENSE_EINVAL, "out is NULL");
   *out = nullptr;
+  if (cfg && cfg->fail_admit_every < 0) return qfail(SENSE_EINVAL, "fail_admit_every must be >= 0");
   sense_queue* q = new sense_queue();
   if (cfg) q->cfg = *cfg;
   q->device = device;
+  q->t0 = Clock::now();
   if (!q->cfg.fake_device) {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -603,6 +691,16 @@ sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_qu
     q->budget = q->cfg.hbm_budget_bytes ? q->cfg.hbm_budget_bytes : ((size_t)1 << 40);
   }
   q->st.hbm_budget = q->budget;
+  if (const char* path = std::getenv("SENSE_QUEUE_LOG")) {
+    if (*path) {
+      q->log = std::fopen(path, "a");
+      if (!q->log) {
+        if (!q->cfg.fake_device) cudaStreamDestroy(q->stream);
+        delete q;
+        return qfail(SENSE_EINVAL, std::string("cannot open SENSE_QUEUE_LOG file ") + path);
+      }
+    }
+  }
   q->worker = std::thread(worker_main, q);
   *out = q;
   return SENSE_OK;
@@ -717,10 +815,17 @@ sense_status sense_queue_wait(sense_queue* q, uint64_t id, sense_c32* x_host, in
     if (iters_host) memcpy(iters_host, r->iters_h, sizeof(int) * F);
     if (resid_host) memcpy(resid_host, r->resid_h, sizeof(double) * F);
     if (outcome_host) memcpy(outcome_host, r->outcome_h, sizeof(int) * F);
+    // a frame that broke down with a non-finite residual saw NaN or Inf values
+    for (size_t f = 0; f < F; ++f)
+      if (r->outcome_h[f] == SENSE_CG_BREAKDOWN && !std::isfinite(r->resid_h[f])) {
+        rc = qfail(SENSE_ENUMERIC, "frame " + std::to_string(f) +
+                                       ": non-finite CG values (NaN or Inf in y or S); outputs were copied");
+        break;
+      }
   } else if (r->state == SENSE_REQ_CANCELLED) {
     rc = qfail(SENSE_EINVAL, "request was cancelled");
   } else {
-    rc = qfail(SENSE_ECUDA, "request failed on the device");
+    rc = qfail(r->fail_status, r->fail_msg);
   }
   if (q->cfg.fake_device) {
     free(r->x_h);
@@ -787,7 +892,9 @@ sense_status sense_queue_destroy(sense_queue* q) {
     q->stop = true;
     for (Request* r : q->pending) {
       r->state = SENSE_REQ_CANCELLED;
+      r->t_done = Clock::now();
       q->st.cancelled++;
+      log_request(q, r);
     }
   }
   q->cv_work.notify_all();
@@ -826,6 +933,7 @@ sense_status sense_queue_destroy(sense_queue* q) {
       cudaStreamDestroy(q->stream);
     }
   }
+  if (q->log) std::fclose(q->log);
   delete q;
   return SENSE_OK;
 }

@@ -79,7 +79,7 @@ class _BatchIO(ctypes.Structure):
 class _QueueCfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_live", ctypes.c_int), ("fake_device", ctypes.c_int),
                 ("fake_tick_us", ctypes.c_int), ("fake_iters", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("iters_per_tick", ctypes.c_int)]
+                ("iters_per_tick", ctypes.c_int), ("fail_admit_every", ctypes.c_int)]
 
 
 class _QueueStats(ctypes.Structure):
@@ -444,9 +444,9 @@ class Queue:
     bits), lines int32."""
 
     def __init__(self, device=0, hbm_budget_bytes=0, max_live=0, fake_device=False, fake_tick_us=0,
-                 fake_iters=0, autotune=False, iters_per_tick=0):
+                 fake_iters=0, autotune=False, iters_per_tick=0, fail_admit_every=0):
         cfg = _QueueCfg(hbm_budget_bytes, max_live, 1 if fake_device else 0, fake_tick_us, fake_iters,
-                        1 if autotune else 0, iters_per_tick)
+                        1 if autotune else 0, iters_per_tick, fail_admit_every)
         h = ctypes.c_void_p()
         _check(load_library().sense_queue_create(device, ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h

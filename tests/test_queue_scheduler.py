@@ -146,3 +146,57 @@ def test_bad_submissions():
     with pytest.raises(sense.SenseError):
         q.submit(shape, y, S, ln, max_iter=0)
     q.close()
+
+
+def test_injected_admission_failures_release_their_budget():
+    # every third admission fails as if a device allocation had failed
+    q = sense.Queue(fake_device=True, fake_tick_us=200, fake_iters=2, max_live=1, fail_admit_every=3)
+    ids = [q.submit(*_req(), max_iter=5) for _ in range(7)]
+    failed = []
+    for k, rid in enumerate(ids):
+        try:
+            q.wait(rid)
+        except sense.SenseError as e:
+            assert e.status == 3 and "injected" in str(e)  # SENSE_ENOMEM
+            failed.append(k)
+    assert failed == [2, 5]  # admissions 3 and 6 in arrival order
+    st = q.stats()
+    assert st["failed"] == 2 and st["completed"] == 5 and st["admitted"] == 7
+    assert st["hbm_in_use"] == 0 and st["live"] == 0
+    q.close()
+    with pytest.raises(sense.SenseError) as ei:
+        sense.Queue(fake_device=True, fail_admit_every=-1)
+    assert ei.value.status == 1
+
+
+def test_request_log_records_every_request(tmp_path, monkeypatch):
+    import json
+
+    log = tmp_path / "requests.jsonl"
+    monkeypatch.setenv("SENSE_QUEUE_LOG", str(log))
+    q = sense.Queue(fake_device=True, fake_tick_us=1000, fake_iters=3, max_live=1, fail_admit_every=2)
+    a = q.submit(*_req(n=64, frames=2), max_iter=10)
+    b = q.submit(*_req(n=32, frames=1), max_iter=10)  # second admission: injected failure
+    c = q.submit(*_req(n=64, frames=3), max_iter=10)
+    d = q.submit(*_req(), max_iter=10)
+    q.cancel(d)  # still pending behind a and c (one live at a time)
+    q.wait(a)
+    with pytest.raises(sense.SenseError):
+        q.wait(b)
+    q.wait(c)
+    with pytest.raises(sense.SenseError):
+        q.wait(d)
+    q.close()
+    recs = {r["id"]: r for r in map(json.loads, log.read_text().splitlines())}
+    assert set(recs) == {a, b, c, d}
+    ra, rb, rc, rd = recs[a], recs[b], recs[c], recs[d]
+    assert (ra["state"], rb["state"], rc["state"], rd["state"]) == ("done", "failed", "done", "cancelled")
+    assert rb["status"] == 3 and ra["status"] == 0
+    assert (ra["ny"], ra["frames"], rb["ny"], rc["frames"]) == (64, 2, 32, 3)
+    for r in (ra, rc):
+        assert r["submit_ms"] <= r["admit_ms"] <= r["first_tick_ms"] <= r["done_ms"]
+        assert abs(r["latency_ms"] - (r["done_ms"] - r["submit_ms"])) < 1e-2
+        assert r["ticks"] == 3 and r["iters"] == 3 and r["max_rel_resid"] == 0.0 and r["max_iter"] == 10
+    assert "first_tick_ms" not in rb and "admit_ms" in rb and "iters" not in rb
+    assert "admit_ms" not in rd and "first_tick_ms" not in rd
+    assert rc["admit_ms"] >= ra["done_ms"] - 1e-3  # one live at a time: c is admitted after a retires
