@@ -18,6 +18,7 @@
 
 #include "launch.h"
 #include "plan.h"
+#include "trace.h"
 #include "sense.h"
 
 using namespace sense;
@@ -152,6 +153,7 @@ sense_status run_batch(sense_batch* b, const sense_batch_io* io, const std::vect
 extern "C" {
 
 sense_status sense_batch_create(const sense_shape* shapes, int count, int device, sense_batch** out) {
+  sense::TraceRange trace_range("sense_batch_create");
   if (!out || !shapes || count < 1) return bfail(SENSE_EINVAL, "need shapes, count >= 1 and out");
   *out = nullptr;
   int ndev = 0;
@@ -238,6 +240,7 @@ size_t sense_batch_workspace_bytes(const sense_batch* b) {
 int sense_batch_classes(const sense_batch* b) { return b ? (int)b->classes.size() : 0; }
 
 sense_status sense_batch_autotune(sense_batch* b, const sense_batch_io* io, void* stream) {
+  sense::TraceRange trace_range("sense_batch_autotune");
   if (!b || !io) return bfail(SENSE_EINVAL, "batch and io are required");
   for (auto& c : b->classes) {
     // representative: the member with the most frames
@@ -294,6 +297,7 @@ sense_status sense_batch_set_variant(sense_batch* b, int ny, int variant) {
 
 sense_status sense_batch_cg_solve(sense_batch* b, const sense_batch_io* io, int max_iter, double rel_tol,
                                   void* stream) {
+  sense::TraceRange trace_range("sense_batch_cg_solve");
   if (!b || !io) return bfail(SENSE_EINVAL, "batch and io are required");
   if (max_iter < 0 || !(rel_tol >= 0.0)) return bfail(SENSE_EINVAL, "max_iter must be >= 0 and rel_tol >= 0");
   const int count = (int)b->plans.size();
@@ -394,6 +398,7 @@ sense_status sense_batch_cg_solve(sense_batch* b, const sense_batch_io* io, int 
 }
 
 sense_status sense_batch_check(sense_batch* b, void* stream) {
+  sense::TraceRange trace_range("sense_batch_check");
   if (!b) return bfail(SENSE_EINVAL, "batch is NULL");
   for (sense_plan* p : b->plans) {
     sense_status rc = sense_plan_check(p, stream);

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "launch.h"
+#include "trace.h"
 #include "sense.h"
 
 using namespace sense;
@@ -153,6 +154,7 @@ sense_status noalloc_adjoint(const sense_shape& sh, const DeviceTables& t, const
 
 extern "C" sense_status sense_adjoint_noalloc(const sense_shape* shape, const void* y, const void* S,
                                               const int32_t* lines, sense_c32* x, void* stream) {
+  sense::TraceRange trace_range("sense_adjoint_noalloc");
   sense_status rc = SENSE_OK;
   std::string msg;
   auto done = [&](sense_status s, const std::string& m) {

@@ -40,6 +40,7 @@
 
 #include "launch.h"
 #include "plan.h"
+#include "trace.h"
 #include "sense.h"
 
 using namespace sense;
@@ -320,6 +321,7 @@ const float2* twiddle_table(sense_queue* q, int n) {
 // inject_fail (test hook): fail as if the last device allocation had failed,
 // after the others succeeded, so the partial clean-up runs.
 bool admit_device(sense_queue* q, Request* r, std::string* err, bool inject_fail) {
+  sense::TraceRange trace_range("sense_queue_admit");
   const sense_shape& sh = r->sh;
   const size_t F = sh.frames;
   cudaStream_t st = q->stream;
@@ -414,6 +416,7 @@ bool retire_enqueue(sense_queue* q, Request* r) {
 // synchronisation completes those, and their memory is released in stream
 // order.
 bool tick_device(sense_queue* q) {
+  sense::TraceRange trace_range("sense_queue_tick");
   // Iterations per tick: the configured number, or by default 10, stretched
   // while nothing waits for admission (up to the largest remaining budget of
   // the live requests, at most 80) so a lone request is not cut into many
@@ -708,6 +711,7 @@ sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_qu
 
 sense_status sense_queue_submit(sense_queue* q, const sense_shape* shape, const void* y_host, const void* S_host,
                                 const int32_t* lines_host, int max_iter, double rel_tol, uint64_t* req_id) {
+  sense::TraceRange trace_range("sense_queue_submit");
   if (!q || !shape || !y_host || !S_host || !lines_host || !req_id)
     return qfail(SENSE_EINVAL, "queue, shape, inputs and req_id are required");
   const sense_shape& sh = *shape;
@@ -792,6 +796,7 @@ sense_status sense_queue_poll(sense_queue* q, uint64_t id, int* state, int* iter
 
 sense_status sense_queue_wait(sense_queue* q, uint64_t id, sense_c32* x_host, int32_t* iters_host, double* resid_host,
                               int32_t* outcome_host, double timeout_s) {
+  sense::TraceRange trace_range("sense_queue_wait");
   if (!q) return qfail(SENSE_EINVAL, "queue is NULL");
   Request* r = nullptr;
   {

@@ -16,6 +16,7 @@
 #include "cg_kernels.cuh"
 #include "launch.h"
 #include "plan.h"
+#include "trace.h"
 #include "sense.h"
 
 using namespace sense;
@@ -781,6 +782,7 @@ const char* sense_last_error(void) { return g_last_error.c_str(); }
 
 
 sense_status sense_plan_create(const sense_shape* shape, int device, sense_plan** out) {
+  sense::TraceRange trace_range("sense_plan_create");
   if (!out) return fail(SENSE_EINVAL, "out is NULL");
   *out = nullptr;
   sense_status rc = check_shape(shape);
@@ -832,6 +834,7 @@ size_t sense_plan_workspace_bytes(const sense_plan* plan) { return plan ? plan->
 
 sense_status sense_forward(sense_plan* pl, const sense_c32* x, const void* S, const int32_t* lines, void* y,
                            void* stream) {
+  sense::TraceRange trace_range("sense_forward");
   if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
   if (!aligned16(x) || !aligned16(S) || !aligned16(y) || !aligned4(lines))
     return fail(SENSE_EINVAL, "x, S, y must be non-NULL and 16-byte aligned; lines 4-byte aligned");
@@ -843,6 +846,7 @@ sense_status sense_forward(sense_plan* pl, const sense_c32* x, const void* S, co
 
 sense_status sense_adjoint(sense_plan* pl, const void* y, const void* S, const int32_t* lines, sense_c32* x,
                            void* stream) {
+  sense::TraceRange trace_range("sense_adjoint");
   if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
   if (!aligned16(x) || !aligned16(S) || !aligned16(y) || !aligned4(lines))
     return fail(SENSE_EINVAL, "x, S, y must be non-NULL and 16-byte aligned; lines 4-byte aligned");
@@ -855,6 +859,7 @@ sense_status sense_adjoint(sense_plan* pl, const void* y, const void* S, const i
 
 sense_status sense_normal(sense_plan* pl, const sense_c32* x, const void* S, const int32_t* lines, sense_c32* out,
                           void* stream) {
+  sense::TraceRange trace_range("sense_normal");
   if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
   if (!aligned16(x) || !aligned16(S) || !aligned16(out) || !aligned4(lines))
     return fail(SENSE_EINVAL, "x, S, out must be non-NULL and 16-byte aligned; lines 4-byte aligned");
@@ -869,6 +874,7 @@ sense_status sense_normal(sense_plan* pl, const sense_c32* x, const void* S, con
 sense_status sense_cg_solve(sense_plan* pl, const void* y, const void* S, const int32_t* lines, int max_iter,
                             double rel_tol, sense_c32* x_out, int32_t* iters_out, double* rel_resid_out,
                             int32_t* outcome_out, void* stream) {
+  sense::TraceRange trace_range("sense_cg_solve");
   if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
   if (!aligned16(x_out) || !aligned16(S) || !aligned16(y) || !aligned4(lines))
     return fail(SENSE_EINVAL, "x_out, S, y must be non-NULL and 16-byte aligned; lines 4-byte aligned");
@@ -884,6 +890,7 @@ sense_status sense_cg_solve(sense_plan* pl, const void* y, const void* S, const 
 }
 
 sense_status sense_rss(sense_plan* pl, const void* y, const int32_t* lines, float* out, void* stream) {
+  sense::TraceRange trace_range("sense_rss");
   if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
   if (!aligned16(y) || !aligned16(out) || !aligned4(lines))
     return fail(SENSE_EINVAL, "y, out must be non-NULL and 16-byte aligned; lines 4-byte aligned");
@@ -974,6 +981,7 @@ sense_status sense_plan_set_lambda(sense_plan* pl, double lambda) {
 
 sense_status sense_plan_autotune(sense_plan* pl, const void* S, const int32_t* lines, int* variant_out,
                                  double* ms_out, void* stream) {
+  sense::TraceRange trace_range("sense_plan_autotune");
   if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
   if (!aligned16(S) || !aligned4(lines)) return fail(SENSE_EINVAL, "S must be 16-byte aligned, lines 4-byte");
   DeviceGuard guard(pl->device);
@@ -1080,6 +1088,7 @@ sense_status sense_selftest_wait(int device, long max_spins) {
 }
 
 sense_status sense_plan_check(sense_plan* pl, void* stream) {
+  sense::TraceRange trace_range("sense_plan_check");
   if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
   DeviceGuard guard(pl->device);
   SENSE_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
