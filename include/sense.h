@@ -262,6 +262,8 @@ typedef struct {
   double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> result ready, completed requests */
   size_t hbm_in_use, hbm_budget;
   int live, pending;
+  size_t staging_reserved; /* host staging the queue holds (page-locked chunks of 256 MiB or more) */
+  size_t staging_in_use;   /* of which held by requests: inputs until uploaded, outputs until waited for */
 } sense_queue_stats;
 
 /* cfg may be NULL (all fields 0).  When the environment variable
@@ -273,8 +275,12 @@ typedef struct {
  * per-frame iteration count and relative residual (null if not finite). */
 sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_queue** out);
 /* Copies the inputs (host memory, layouts of sense_cg_solve) into pinned
- * staging before returning; the caller's buffers are free on return.  A
- * request that could never fit the budget is refused with SENSE_EQUEUE_FULL. */
+ * staging before returning, large inputs with several threads; the caller's
+ * buffers are free on return.  Staging comes from an arena of page-locked
+ * chunks that is reused across requests of any shape, so after warm-up a
+ * submit allocates nothing.  A request's latency is timed from the start of
+ * this call.  A request that could never fit the budget is refused with
+ * SENSE_EQUEUE_FULL. */
 sense_status sense_queue_submit(sense_queue* q, const sense_shape* shape, const void* y_host, const void* S_host,
                                 const int32_t* lines_host, int max_iter, double rel_tol, uint64_t* req_id);
 /* Non-blocking state of a request; iters = ticks applied so far. */

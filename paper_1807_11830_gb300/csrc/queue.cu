@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "launch.h"
+#include "pinned.h"
 #include "plan.h"
 #include "trace.h"
 #include "sense.h"
@@ -128,63 +129,27 @@ struct sense_queue {
   std::map<std::tuple<int, int, int>, SizeClass> classes;  // worker thread only
   std::map<std::tuple<int, int, int>, int> variants;         // guarded by mu
   std::map<int, float2*> twiddles;                            // device tables per length (worker thread)
-  // pinned host staging, recycled between requests (cudaMallocHost is slow)
-  std::mutex pin_mu;
-  std::map<size_t, std::vector<void*>> pin_free;
-  size_t pin_cached = 0;
+  // host staging of inputs and outputs (page-locked unless fake_device)
+  std::unique_ptr<PinnedArena> arena;
 };
 
 namespace {
 
-constexpr size_t kPinnedCacheBytes = (size_t)4 << 30;
-
-size_t pin_round(size_t b) { return (b + 4095) & ~(size_t)4095; }
-
-void* pin_get(sense_queue* q, size_t bytes) {
-  bytes = pin_round(bytes);
-  {
-    std::lock_guard<std::mutex> lock(q->pin_mu);
-    auto it = q->pin_free.find(bytes);
-    if (it != q->pin_free.end() && !it->second.empty()) {
-      void* p = it->second.back();
-      it->second.pop_back();
-      q->pin_cached -= bytes;
-      return p;
-    }
-  }
-  void* p = nullptr;
-  return cudaMallocHost(&p, bytes) == cudaSuccess ? p : nullptr;
-}
-
-void pin_put(sense_queue* q, void* p, size_t bytes) {
-  if (!p) return;
-  bytes = pin_round(bytes);
-  {
-    std::lock_guard<std::mutex> lock(q->pin_mu);
-    if (q->pin_cached + bytes <= kPinnedCacheBytes) {
-      q->pin_free[bytes].push_back(p);
-      q->pin_cached += bytes;
-      return;
-    }
-  }
-  cudaFreeHost(p);
-}
-
+// Input staging is released once the request's uploads have completed.
 void free_host(sense_queue* q, Request* r) {
-  pin_put(q, r->y_h, r->y_bytes);
-  pin_put(q, r->s_h, r->s_bytes);
-  pin_put(q, r->lines_h, r->l_bytes);
+  q->arena->put(r->y_h);
+  q->arena->put(r->s_h);
+  q->arena->put(r->lines_h);
   r->y_h = r->s_h = nullptr;
   r->lines_h = nullptr;
 }
 
 void free_outputs(sense_queue* q, Request* r) {
-  const size_t F = r->sh.frames;
-  pin_put(q, r->x_h, r->x_bytes);
-  pin_put(q, r->iters_h, sizeof(int) * F);
-  pin_put(q, r->resid_h, sizeof(double) * F);
-  pin_put(q, r->outcome_h, sizeof(int) * F);
-  pin_put(q, r->err_h, sizeof(int));
+  q->arena->put(r->x_h);
+  q->arena->put(r->iters_h);
+  q->arena->put(r->resid_h);
+  q->arena->put(r->outcome_h);
+  q->arena->put(r->err_h);
   r->err_h = nullptr;
   r->x_h = nullptr;
   r->iters_h = nullptr;
@@ -486,6 +451,8 @@ bool tick_device(sense_queue* q) {
     launched.emplace_back(&c, frames);
   }
   if (cudaStreamSynchronize(q->stream) != cudaSuccess) return false;
+  for (Request* r : q->live)
+    if (r->y_h) free_host(q, r);  // its uploads, queued before this tick, have completed
   std::vector<Request*> still, finished, cancelled;
   const Clock::time_point now = Clock::now();
   for (Request* r : q->live) {
@@ -546,19 +513,13 @@ void tick_fake(sense_queue* q) {
       record_done(q, r, SENSE_REQ_CANCELLED);
     } else if (r->ticks >= stop_at) {
       const size_t F = r->sh.frames;
-      r->x_h = static_cast<float2*>(calloc(r->x_bytes / sizeof(float2), sizeof(float2)));
-      r->iters_h = static_cast<int*>(calloc(F, sizeof(int)));
-      r->outcome_h = static_cast<int*>(calloc(F, sizeof(int)));
-      r->resid_h = static_cast<double*>(calloc(F, sizeof(double)));
+      memset(r->x_h, 0, r->x_bytes);
       for (size_t f = 0; f < F; ++f) {
         r->iters_h[f] = r->ticks;
         r->outcome_h[f] = r->ticks >= r->max_iter ? SENSE_CG_MAXITER : SENSE_CG_CONVERGED;
+        r->resid_h[f] = 0.0;
       }
-      free(r->y_h);
-      free(r->s_h);
-      free(r->lines_h);
-      r->y_h = r->s_h = nullptr;
-      r->lines_h = nullptr;
+      free_host(q, r);
       record_done(q, r, SENSE_REQ_DONE);
     } else {
       still.push_back(r);
@@ -664,6 +625,7 @@ sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_qu
   if (cfg) q->cfg = *cfg;
   q->device = device;
   q->t0 = Clock::now();
+  q->arena.reset(new PinnedArena(!q->cfg.fake_device));
   if (!q->cfg.fake_device) {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -721,6 +683,7 @@ sense_status sense_queue_submit(sense_queue* q, const sense_shape* shape, const 
   if (sh.centred != 0 && sh.centred != 1) return qfail(SENSE_EINVAL, "centred must be 0 or 1");
   if (!sense_size_supported(sh.ny) || !sense_size_supported(sh.nx))
     return qfail(SENSE_EUNSUPPORTED_SIZE, "no compiled transform for this ny / nx");
+  const Clock::time_point t_arrive = Clock::now();  // latency counts the staging copy
   Request* r = new Request();
   r->sh = sh;
   r->max_iter = max_iter;
@@ -740,39 +703,26 @@ sense_status sense_queue_submit(sense_queue* q, const sense_shape* shape, const 
       return qfail(SENSE_EQUEUE_FULL, "request needs more device memory than the queue's budget");
     }
   }
-  bool ok;
-  if (q->cfg.fake_device) {
-    r->y_h = malloc(r->y_bytes);
-    r->s_h = malloc(r->s_bytes);
-    r->lines_h = static_cast<int*>(malloc(r->l_bytes));
-    ok = r->y_h && r->s_h && r->lines_h;
-  } else {
-    r->y_h = pin_get(q, r->y_bytes);
-    r->s_h = pin_get(q, r->s_bytes);
-    r->lines_h = static_cast<int*>(pin_get(q, r->l_bytes));
-    r->x_h = static_cast<float2*>(pin_get(q, r->x_bytes));
-    r->iters_h = static_cast<int*>(pin_get(q, sizeof(int) * F));
-    r->outcome_h = static_cast<int*>(pin_get(q, sizeof(int) * F));
-    r->resid_h = static_cast<double*>(pin_get(q, sizeof(double) * F));
-    r->err_h = static_cast<int*>(pin_get(q, sizeof(int)));
-    ok = r->y_h && r->s_h && r->lines_h && r->x_h && r->iters_h && r->outcome_h && r->resid_h && r->err_h;
-  }
-  if (!ok) {
-    if (q->cfg.fake_device) {
-      free(r->y_h);
-      free(r->s_h);
-      free(r->lines_h);
-    } else {
-      free_host(q, r);
-      free_outputs(q, r);
-    }
+  PinnedArena& ar = *q->arena;
+  r->y_h = ar.get(r->y_bytes);
+  r->s_h = ar.get(r->s_bytes);
+  r->lines_h = static_cast<int*>(ar.get(r->l_bytes));
+  r->x_h = static_cast<float2*>(ar.get(r->x_bytes));
+  r->iters_h = static_cast<int*>(ar.get(sizeof(int) * F));
+  r->outcome_h = static_cast<int*>(ar.get(sizeof(int) * F));
+  r->resid_h = static_cast<double*>(ar.get(sizeof(double) * F));
+  r->err_h = static_cast<int*>(ar.get(sizeof(int)));
+  if (!(r->y_h && r->s_h && r->lines_h && r->x_h && r->iters_h && r->outcome_h && r->resid_h && r->err_h)) {
+    free_host(q, r);
+    free_outputs(q, r);
     delete r;
     return qfail(SENSE_ENOMEM, "pinned staging allocation failed");
   }
-  memcpy(r->y_h, y_host, r->y_bytes);
-  memcpy(r->s_h, S_host, r->s_bytes);
+  *r->err_h = 0;
+  parallel_copy(r->y_h, y_host, r->y_bytes);
+  parallel_copy(r->s_h, S_host, r->s_bytes);
   memcpy(r->lines_h, lines_host, r->l_bytes);
-  r->t_submit = Clock::now();
+  r->t_submit = t_arrive;
   {
     std::lock_guard<std::mutex> lock(q->mu);
     r->id = q->next_id++;
@@ -832,18 +782,8 @@ sense_status sense_queue_wait(sense_queue* q, uint64_t id, sense_c32* x_host, in
   } else {
     rc = qfail(r->fail_status, r->fail_msg);
   }
-  if (q->cfg.fake_device) {
-    free(r->x_h);
-    free(r->iters_h);
-    free(r->resid_h);
-    free(r->outcome_h);
-    free(r->y_h);
-    free(r->s_h);
-    free(r->lines_h);
-  } else {
-    free_outputs(q, r);
-    free_host(q, r);
-  }
+  free_outputs(q, r);
+  free_host(q, r);
   delete r;
   return rc;
 }
@@ -880,6 +820,8 @@ sense_status sense_queue_stats_get(sense_queue* q, sense_queue_stats* out) {
     if (kv.second->state == SENSE_REQ_RUNNING) ++running;
   out->live = running;
   out->pending = (int)q->pending.size();
+  out->staging_reserved = q->arena->reserved();
+  out->staging_in_use = q->arena->in_use();
   return SENSE_OK;
 }
 
@@ -906,19 +848,9 @@ sense_status sense_queue_destroy(sense_queue* q) {
   if (q->worker.joinable()) q->worker.join();
   for (auto& kv : q->reqs) {
     Request* r = kv.second;
-    if (q->cfg.fake_device) {
-      free(r->x_h);
-      free(r->iters_h);
-      free(r->resid_h);
-      free(r->outcome_h);
-      free(r->y_h);
-      free(r->s_h);
-      free(r->lines_h);
-    } else {
-      free_device(r, q->stream);
-      free_outputs(q, r);
-      free_host(q, r);
-    }
+    if (!q->cfg.fake_device) free_device(r, q->stream);
+    free_outputs(q, r);
+    free_host(q, r);
     delete r;
   }
   if (!q->cfg.fake_device) {
@@ -930,15 +862,13 @@ sense_status sense_queue_destroy(sense_queue* q) {
       if (c.status_h) cudaFreeHost(c.status_h);
     }
     for (auto& kv : q->twiddles) cudaFree(kv.second);
-    for (auto& kv : q->pin_free)
-      for (void* p : kv.second) cudaFreeHost(p);
-    q->pin_free.clear();
     if (q->stream) {
       cudaStreamSynchronize(q->stream);
       cudaStreamDestroy(q->stream);
     }
   }
   if (q->log) std::fclose(q->log);
+  q->arena.reset();  // after the stream is idle: no copy still reads or writes staging
   delete q;
   return SENSE_OK;
 }

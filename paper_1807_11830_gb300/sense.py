@@ -87,7 +87,8 @@ class _QueueStats(ctypes.Structure):
                 ("cancelled", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("refused", ctypes.c_uint64),
                 ("ticks", ctypes.c_uint64), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("hbm_in_use", ctypes.c_size_t),
-                ("hbm_budget", ctypes.c_size_t), ("live", ctypes.c_int), ("pending", ctypes.c_int)]
+                ("hbm_budget", ctypes.c_size_t), ("live", ctypes.c_int), ("pending", ctypes.c_int),
+                ("staging_reserved", ctypes.c_size_t), ("staging_in_use", ctypes.c_size_t)]
 
 
 _LIB = None

@@ -118,3 +118,38 @@ def test_queue_budget_holds_requests_back():
     st = q.stats()
     assert st["completed"] == 4 and st["ticks"] >= 4 * 6  # never two at once
     q.close()
+
+
+def test_large_requests_staged_in_parallel_equal_alone():
+    """Inputs of 32 MiB and more are copied into staging by several threads;
+    such requests, submitted back to back so their staging coexists in the
+    arena, give the same bits as the same problems solved alone."""
+    dev = "cuda:0"
+    q = sense.Queue(device=0)
+    K = 5
+    specs = [(256, 24, 8, 128, 3100), (192, 30, 10, 96, 3101), (256, 20, 6, 128, 3102)]
+    reqs = []
+    for n, C, F, L, seed in specs:
+        rng = synth.rng_for(seed)
+        S = np.ascontiguousarray(synth.sensitivities(C, n, n), np.complex64)
+        lines = np.ascontiguousarray(synth.mask_lines(n, L, synth.centre_for(n), F, rng), np.int32)
+        y = np.ascontiguousarray(synth.random_complex((F, C, L, n), rng), np.complex64)
+        assert y.nbytes >= 32 << 20
+        shape = dict(ny=n, nx=n, coils=C, frames=F, lines=L)
+        reqs.append((shape, y, S, lines, q.submit(shape, y, S, lines, max_iter=K)))
+    assert q.stats()["staging_reserved"] >= 256 << 20
+    for shape, y, S, lines, rid in reqs:
+        F, n = shape["frames"], shape["ny"]
+        x = np.empty((F, n, n), np.complex64)
+        q.wait(rid, x)
+        plan = sense.Plan(n, n, shape["coils"], F, shape["lines"])
+        sense.sense_plan_set_variant(plan, q.variant(n, n))
+        sense.sense_plan_set_cg_mode(plan, sense.CG_MODE_PERSISTENT)
+        xa = torch.empty((F, n, n), dtype=torch.complex64, device=dev)
+        sense.sense_cg_solve(plan, torch.from_numpy(y).to(dev), torch.from_numpy(S).to(dev),
+                             torch.from_numpy(lines).to(dev), K, 0.0, xa)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(xa.cpu().numpy(), x)
+    st = q.stats()
+    assert st["staging_in_use"] == 0 and st["hbm_in_use"] == 0
+    q.close()

@@ -200,3 +200,42 @@ def test_request_log_records_every_request(tmp_path, monkeypatch):
     assert "first_tick_ms" not in rb and "admit_ms" in rb and "iters" not in rb
     assert "admit_ms" not in rd and "first_tick_ms" not in rd
     assert rc["admit_ms"] >= ra["done_ms"] - 1e-3  # one live at a time: c is admitted after a retires
+
+
+MiB = 1 << 20
+
+
+def test_staging_arena_reuses_space_across_shapes():
+    q = sense.Queue(fake_device=True, fake_tick_us=100, fake_iters=1)
+    shapes = [dict(n=64, coils=4, frames=2, lines=16), dict(n=128, coils=8, frames=3, lines=40),
+              dict(n=96, coils=6, frames=1, lines=30)]
+    for rep in range(3):
+        for sp in shapes:
+            q.wait(q.submit(*_req(**sp), max_iter=2))
+        st = q.stats()
+        assert st["staging_in_use"] == 0  # everything returned after the waits
+        assert st["staging_reserved"] == 256 * MiB  # one chunk serves every shape, every time
+    # several requests held at once still share the one chunk, and their space coalesces back
+    ids = [q.submit(*_req(**sp), max_iter=2) for sp in shapes * 3]
+    assert q.stats()["staging_in_use"] > 0
+    for rid in ids[1::2] + ids[0::2]:  # out of order
+        q.wait(rid)
+    st = q.stats()
+    assert st["staging_in_use"] == 0 and st["staging_reserved"] == 256 * MiB
+    q.close()
+
+
+def test_staging_arena_large_request_gets_its_own_chunk():
+    q = sense.Queue(fake_device=True, fake_tick_us=100, fake_iters=1)
+    big = dict(n=384, coils=8, frames=8, lines=384)  # y: 8*8*384*384*8 B = 72 MiB, well under a chunk
+    q.wait(q.submit(*_req(**big), max_iter=2))
+    assert q.stats()["staging_reserved"] == 256 * MiB
+    huge = dict(n=384, coils=30, frames=8, lines=384)  # y: 270 MiB, more than a chunk
+    q.wait(q.submit(*_req(**huge), max_iter=2))
+    st = q.stats()
+    assert st["staging_reserved"] == 256 * MiB + 270 * MiB and st["staging_in_use"] == 0
+    # the freed large chunk is reused, no third chunk
+    reserved = st["staging_reserved"]
+    q.wait(q.submit(*_req(**huge), max_iter=2))
+    assert q.stats()["staging_reserved"] == reserved
+    q.close()
