@@ -243,12 +243,15 @@ typedef struct {
   int fake_iters;
   int autotune;            /* 1: autotune each size class on its first request; 0: variant 0 */
   int iters_per_tick;      /* CG iterations per tick; each frame still stops at its own max_iter /
-                              tolerance inside the tick, new requests join between ticks.  0: 10,
-                              stretched up to 80 (the largest remaining budget of the live requests)
-                              while no request waits for admission */
+                              tolerance inside the tick, new requests join between ticks.  0: adaptive --
+                              while requests wait for admission, as many as fit in about 4 ms at the
+                              last tick's time per iteration (1 to 10); otherwise 10, stretched up to 80
+                              (the largest remaining budget of the live requests) */
   int fail_admit_every;    /* test hook, 0 = off: every k-th admission fails as if a device allocation
                               had failed (after the others succeeded); the request ends FAILED and
                               sense_queue_wait returns SENSE_ENOMEM */
+  size_t staging_reserve_bytes; /* page-locked host staging allocated at creation (0: none); the
+                                   staging arena grows on demand beyond it */
 } sense_queue_cfg;
 
 typedef enum {

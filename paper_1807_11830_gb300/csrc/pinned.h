@@ -50,8 +50,13 @@ class PinnedArena {
       std::lock_guard<std::mutex> lock(mu_);
       if (void* p = take(need)) return p;
     }
-    // new chunk, allocated outside the lock (cudaMallocHost is slow)
-    const size_t size = std::max(kChunkBytes, need);
+    // new chunk, allocated outside the lock (cudaMallocHost is slow); chunks
+    // grow with what is already reserved, so a growing load pays for few
+    size_t size;
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      size = std::max(std::max(kChunkBytes, need), round(reserved_ / 2));
+    }
     char* base = static_cast<char*>(acquire(size));
     if (!base) return nullptr;
     std::lock_guard<std::mutex> lock(mu_);
@@ -62,6 +67,23 @@ class PinnedArena {
     chunks_.push_back(std::move(c));
     reserved_ += size;
     return take(need);  // fits: the new chunk is free and large enough
+  }
+
+  // One chunk of `bytes` up front (queue creation), so the first requests
+  // do not pay for page-locking.  Returns false if the host refused it.
+  bool reserve(size_t bytes) {
+    if (bytes == 0) return true;
+    const size_t size = round(bytes);
+    char* base = static_cast<char*>(acquire(size));
+    if (!base) return false;
+    std::lock_guard<std::mutex> lock(mu_);
+    Chunk c;
+    c.base = base;
+    c.size = size;
+    c.free[0] = size;
+    chunks_.push_back(std::move(c));
+    reserved_ += size;
+    return true;
   }
 
   void put(void* p) {

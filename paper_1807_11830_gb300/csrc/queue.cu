@@ -122,6 +122,7 @@ struct sense_queue {
   sense_queue_stats st{};
   std::vector<double> lat_ms;
   uint64_t admissions = 0;      // counts admissions for the fail_admit_every test hook
+  double iter_ms = 0.0;         // last tick's time per CG iteration (worker thread)
   FILE* log = nullptr;          // per-request JSON lines (SENSE_QUEUE_LOG), written under mu
   Clock::time_point t0;         // creation time, origin of the logged times
   cudaStream_t stream = nullptr;
@@ -385,7 +386,9 @@ bool tick_device(sense_queue* q) {
   // Iterations per tick: the configured number, or by default 10, stretched
   // while nothing waits for admission (up to the largest remaining budget of
   // the live requests, at most 80) so a lone request is not cut into many
-  // host round trips.
+  // host round trips, and shortened while requests wait, to what fits in
+  // kWaitTickMs at the last tick's time per iteration, so they join soon.
+  constexpr double kWaitTickMs = 4.0;
   int m = q->cfg.iters_per_tick > 0 ? q->cfg.iters_per_tick : 10;
   if (q->cfg.iters_per_tick <= 0) {
     bool waiting;
@@ -397,8 +400,11 @@ bool tick_device(sense_queue* q) {
       int remaining = 0;
       for (Request* r : q->live) remaining = std::max(remaining, r->max_iter - r->ticks);
       m = std::max(m, std::min(remaining, 8 * m));
+    } else if (q->iter_ms > 0.0) {
+      m = (int)std::max(1.0, std::min((double)m, std::floor(kWaitTickMs / q->iter_ms)));
     }
   }
+  const Clock::time_point t_tick = Clock::now();
   std::map<std::tuple<int, int, int>, std::vector<Request*>> by_class;
   for (Request* r : q->live) by_class[std::make_tuple(r->sh.ny, r->sh.nx, r->sh.storage)].push_back(r);
   std::vector<std::pair<SizeClass*, int>> launched;
@@ -451,6 +457,7 @@ bool tick_device(sense_queue* q) {
     launched.emplace_back(&c, frames);
   }
   if (cudaStreamSynchronize(q->stream) != cudaSuccess) return false;
+  q->iter_ms = std::chrono::duration<double, std::milli>(Clock::now() - t_tick).count() / m;
   for (Request* r : q->live)
     if (r->y_h) free_host(q, r);  // its uploads, queued before this tick, have completed
   std::vector<Request*> still, finished, cancelled;
@@ -626,6 +633,10 @@ sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_qu
   q->device = device;
   q->t0 = Clock::now();
   q->arena.reset(new PinnedArena(!q->cfg.fake_device));
+  if (!q->arena->reserve(q->cfg.staging_reserve_bytes)) {
+    delete q;
+    return qfail(SENSE_ENOMEM, "staging reservation of page-locked host memory failed");
+  }
   if (!q->cfg.fake_device) {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {

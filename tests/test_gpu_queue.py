@@ -127,7 +127,7 @@ def test_large_requests_staged_in_parallel_equal_alone():
     dev = "cuda:0"
     q = sense.Queue(device=0)
     K = 5
-    specs = [(256, 24, 8, 128, 3100), (192, 30, 10, 96, 3101), (256, 20, 6, 128, 3102)]
+    specs = [(256, 24, 8, 128, 3100), (192, 30, 10, 96, 3101), (256, 20, 8, 128, 3102)]
     reqs = []
     for n, C, F, L, seed in specs:
         rng = synth.rng_for(seed)

@@ -239,3 +239,22 @@ def test_staging_arena_large_request_gets_its_own_chunk():
     q.wait(q.submit(*_req(**huge), max_iter=2))
     assert q.stats()["staging_reserved"] == reserved
     q.close()
+
+
+def test_staging_reservation_and_growth():
+    q = sense.Queue(fake_device=True, fake_tick_us=2000, fake_iters=100, max_live=1,
+                    staging_reserve_bytes=300 * MiB)
+    assert q.stats()["staging_reserved"] == 300 * MiB
+    # requests held at once beyond the reservation: chunks grow with what is reserved
+    big = dict(n=384, coils=16, frames=8, lines=384)  # y: 144 MiB
+    ids = [q.submit(*_req(**big), max_iter=100) for _ in range(4)]
+    st = q.stats()
+    assert st["staging_in_use"] >= 4 * 144 * MiB and st["staging_reserved"] >= st["staging_in_use"]
+    assert st["staging_reserved"] < 2 * st["staging_in_use"] + 300 * MiB  # growth stays proportionate
+    for rid in ids:
+        q.cancel(rid)
+    for rid in ids:
+        with pytest.raises(sense.SenseError):
+            q.wait(rid)
+    assert q.stats()["staging_in_use"] == 0
+    q.close()
