@@ -101,6 +101,8 @@ struct SizeClass {
   PFrame* table_h = nullptr;  // pinned
   int* status_d = nullptr;
   int* status_h = nullptr;  // pinned
+  cudaStream_t stream = nullptr;  // its persistent launches overlap those of other classes
+  cudaEvent_t done = nullptr;
 };
 
 size_t elem_bytes(int storage) { return storage == SENSE_STORE_BF16 ? 4 : 8; }
@@ -123,6 +125,10 @@ struct sense_queue {
   std::vector<double> lat_ms;
   uint64_t admissions = 0;      // counts admissions for the fail_admit_every test hook
   double iter_ms = 0.0;         // last tick's time per CG iteration (worker thread)
+  double gap_ms = 0.0;          // running mean of the time between submissions (under mu)
+  Clock::time_point last_submit;
+  bool any_submit = false;
+  cudaEvent_t admitted = nullptr;  // recorded after each round of admissions
   FILE* log = nullptr;          // per-request JSON lines (SENSE_QUEUE_LOG), written under mu
   Clock::time_point t0;         // creation time, origin of the logged times
   cudaStream_t stream = nullptr;
@@ -243,6 +249,9 @@ void record_done(sense_queue* q, Request* r, int state) {
 }
 
 bool ensure_class_capacity(sense_queue* q, SizeClass& c, int frames) {
+  if (!c.stream && (cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming) != cudaSuccess))
+    return false;
   if (c.cap >= frames && c.upd_cap > 0) return true;
   int cap = std::max(frames, std::max(64, c.cap * 2));
   // free the old buffers (the stream is idle between ticks)
@@ -383,28 +392,37 @@ bool retire_enqueue(sense_queue* q, Request* r) {
 // order.
 bool tick_device(sense_queue* q) {
   sense::TraceRange trace_range("sense_queue_tick");
-  // Iterations per tick: the configured number, or by default 10, stretched
-  // while nothing waits for admission (up to the largest remaining budget of
-  // the live requests, at most 80) so a lone request is not cut into many
-  // host round trips, and shortened while requests wait, to what fits in
-  // kWaitTickMs at the last tick's time per iteration, so they join soon.
+  // Iterations per tick: the configured number, or by default
+  //  * while requests wait for admission, what fits in kWaitTickMs at the
+  //    last tick's time per iteration (1 to 10), so they join soon;
+  //  * otherwise 10, stretched up to the largest remaining budget of the live
+  //    requests (at most 80) so a lone request is not cut into many host
+  //    round trips, but no longer than the recent mean time between
+  //    submissions (at least kWaitTickMs): the next arrival is then likely
+  //    to come during the tick and should not wait long for its end.
   constexpr double kWaitTickMs = 4.0;
   int m = q->cfg.iters_per_tick > 0 ? q->cfg.iters_per_tick : 10;
   if (q->cfg.iters_per_tick <= 0) {
     bool waiting;
+    double gap;
     {
       std::lock_guard<std::mutex> lock(q->mu);
       waiting = !q->pending.empty();
+      gap = q->gap_ms;
     }
     if (!waiting) {
       int remaining = 0;
       for (Request* r : q->live) remaining = std::max(remaining, r->max_iter - r->ticks);
       m = std::max(m, std::min(remaining, 8 * m));
+      if (q->iter_ms > 0.0 && gap > 0.0)
+        m = (int)std::max(1.0, std::min((double)m, std::floor(std::max(kWaitTickMs, gap) / q->iter_ms)));
     } else if (q->iter_ms > 0.0) {
       m = (int)std::max(1.0, std::min((double)m, std::floor(kWaitTickMs / q->iter_ms)));
     }
   }
   const Clock::time_point t_tick = Clock::now();
+  // the admissions just queued on q->stream come before every class's launch
+  if (cudaEventRecord(q->admitted, q->stream) != cudaSuccess) return false;
   std::map<std::tuple<int, int, int>, std::vector<Request*>> by_class;
   for (Request* r : q->live) by_class[std::make_tuple(r->sh.ny, r->sh.nx, r->sh.storage)].push_back(r);
   std::vector<std::pair<SizeClass*, int>> launched;
@@ -443,15 +461,19 @@ bool tick_device(sense_queue* q) {
     a.st.part_nrm = c.part_nrm;
     a.st.part_upd = c.part_upd;
     if (a.chunks > c.upd_cap) return false;
-    bool ok = cudaMemcpyAsync(c.table_d, c.table_h, sizeof(PFrame) * frames, cudaMemcpyHostToDevice, q->stream) ==
+    // each class on its own stream: the launches of different classes overlap
+    // (each kernel's blocks wait only on blocks of the same launch)
+    cudaStream_t cs = c.stream;
+    bool ok = cudaStreamWaitEvent(cs, q->admitted, 0) == cudaSuccess &&
+              cudaMemcpyAsync(c.table_d, c.table_h, sizeof(PFrame) * frames, cudaMemcpyHostToDevice, cs) ==
                   cudaSuccess &&
-              cudaMemsetAsync(c.ints, 0, sizeof(int) * (4 * (size_t)frames + 1), q->stream) == cudaSuccess;
-    cudaError_t e = c.storage == SENSE_STORE_BF16 ? launch_cg_persistent<StBF16>(c.ny, variant, a, q->sms, q->stream)
-                                                  : launch_cg_persistent<StC64>(c.ny, variant, a, q->sms, q->stream);
+              cudaMemsetAsync(c.ints, 0, sizeof(int) * (4 * (size_t)frames + 1), cs) == cudaSuccess;
+    cudaError_t e = c.storage == SENSE_STORE_BF16 ? launch_cg_persistent<StBF16>(c.ny, variant, a, q->sms, cs)
+                                                  : launch_cg_persistent<StC64>(c.ny, variant, a, q->sms, cs);
     if (!ok || e != cudaSuccess) return false;
-    k_gather_active<<<(frames + 255) / 256, 256, 0, q->stream>>>(c.table_d, frames, c.status_d);
-    if (cudaMemcpyAsync(c.status_h, c.status_d, sizeof(int) * frames, cudaMemcpyDeviceToHost, q->stream) !=
-        cudaSuccess)
+    k_gather_active<<<(frames + 255) / 256, 256, 0, cs>>>(c.table_d, frames, c.status_d);
+    if (cudaMemcpyAsync(c.status_h, c.status_d, sizeof(int) * frames, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaEventRecord(c.done, cs) != cudaSuccess || cudaStreamWaitEvent(q->stream, c.done, 0) != cudaSuccess)
       return false;
     for (Request* r : kv.second) r->cls = (int)launched.size();
     launched.emplace_back(&c, frames);
@@ -655,7 +677,8 @@ sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_qu
       uint64_t keep = UINT64_MAX;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    const cudaError_t e = cudaStreamCreateWithFlags(&q->stream, cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithFlags(&q->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q->admitted, cudaEventDisableTiming);
     cudaSetDevice(prev);
     if (e != cudaSuccess) {
       delete q;
@@ -671,7 +694,10 @@ sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_qu
     if (*path) {
       q->log = std::fopen(path, "a");
       if (!q->log) {
-        if (!q->cfg.fake_device) cudaStreamDestroy(q->stream);
+        if (!q->cfg.fake_device) {
+          cudaEventDestroy(q->admitted);
+          cudaStreamDestroy(q->stream);
+        }
         delete q;
         return qfail(SENSE_EINVAL, std::string("cannot open SENSE_QUEUE_LOG file ") + path);
       }
@@ -740,6 +766,12 @@ sense_status sense_queue_submit(sense_queue* q, const sense_shape* shape, const 
     q->reqs[r->id] = r;
     q->pending.push_back(r);
     *req_id = r->id;
+    if (q->any_submit) {
+      const double gap = std::chrono::duration<double, std::milli>(t_arrive - q->last_submit).count();
+      q->gap_ms = q->gap_ms > 0.0 ? 0.75 * q->gap_ms + 0.25 * gap : gap;
+    }
+    q->any_submit = true;
+    q->last_submit = t_arrive;
   }
   q->cv_work.notify_all();
   return SENSE_OK;
@@ -871,8 +903,14 @@ sense_status sense_queue_destroy(sense_queue* q) {
         if (p) cudaFree(p);
       if (c.table_h) cudaFreeHost(c.table_h);
       if (c.status_h) cudaFreeHost(c.status_h);
+      if (c.stream) {
+        cudaStreamSynchronize(c.stream);
+        cudaStreamDestroy(c.stream);
+      }
+      if (c.done) cudaEventDestroy(c.done);
     }
     for (auto& kv : q->twiddles) cudaFree(kv.second);
+    if (q->admitted) cudaEventDestroy(q->admitted);
     if (q->stream) {
       cudaStreamSynchronize(q->stream);
       cudaStreamDestroy(q->stream);
