@@ -635,8 +635,10 @@ def run_serve(args):
         sense.sense_forward(plan, torch.from_numpy(p.x_true.astype(np.complex64)).to(dev), S_d, l_d, y_d)
         y_d += torch.from_numpy(p.noise.astype(np.complex64)).to(dev)
         # serial plain solve time of this request: inputs in from pinned host memory, the same
-        # kernels with per-iteration launches, image back to pinned host memory
+        # kernels with per-iteration launches (the variant autotuned for them), image back to
+        # pinned host memory
         sense.sense_plan_set_cg_mode(plan, sense.CG_MODE_DIRECT)
+        sense.sense_plan_autotune(plan, S_d, l_d)
         x_d = torch.empty((F, n, n), dtype=torch.complex64, device=dev)
         y_h, S_h, l_h = y_d.cpu().pin_memory(), S_d.cpu().pin_memory(), l_d.cpu().pin_memory()
         x_h = torch.empty(x_d.shape, dtype=x_d.dtype).pin_memory()
@@ -657,12 +659,27 @@ def run_serve(args):
         pool.append(dict(shape=dict(ny=n, nx=n, coils=C, frames=F, lines=L), y=y_d.cpu().numpy(),
                          S=p.S.astype(np.complex64), lines=p.lines, solve_s=solve_s, frames=F, n=n))
         plan.close()
+    # kernel variant per size class for the queue: autotuned in persistent mode on the class's
+    # first pool shape, once, before any stream (as a deployment would load it from a cache)
+    class_variant = {}
+    for e in pool:
+        n = e["n"]
+        if n in class_variant:
+            continue
+        sh = e["shape"]
+        tp = sense.Plan(n, n, sh["coils"], sh["frames"], sh["lines"])
+        sense.sense_plan_set_cg_mode(tp, sense.CG_MODE_PERSISTENT)
+        class_variant[n], _ = sense.sense_plan_autotune(tp, torch.from_numpy(e["S"]).to(dev),
+                                                        torch.from_numpy(e["lines"]).to(dev))
+        tp.close()
     results = {}
     for rate in [float(r) for r in args.serve_rates.split(",")]:
         count = args.serve_requests
         arrivals = synth.poisson_arrivals(rate, count, seed=int(rate) + 1811)
         picks = synth.rng_for(int(rate) + 7).integers(0, len(pool), size=count)
         q = sense.Queue(device=0, staging_reserve_bytes=SERVE_STAGING_BYTES)
+        for n, v in class_variant.items():
+            q.set_variant(n, n, v)
         t0 = time.perf_counter()
         ids = []
         for a, pk in zip(arrivals, picks):
@@ -698,6 +715,7 @@ def run_serve(args):
         "config": {"workload": "serving: Poisson arrivals, sizes from the uneven-batch distribution, "
                                "CG to a relative residual of 1e-4 or 100 iterations",
                    "pool_shapes": len(pool),
+                   "queue_variants": {str(n): v for n, v in sorted(class_variant.items())},
                    "staging": "%d GiB of page-locked host staging reserved at queue creation, before the "
                               "stream starts" % (SERVE_STAGING_BYTES >> 30)},
         "rates": results,

@@ -304,6 +304,12 @@ sense_status sense_queue_cancel(sense_queue* q, uint64_t req_id);
 sense_status sense_queue_stats_get(sense_queue* q, sense_queue_stats* out);
 /* Kernel variant the queue uses for a size class (-1 if none yet). */
 int sense_queue_variant(sense_queue* q, int ny, int nx, int storage);
+/* Fix the kernel variant of a size class (ny, nx, storage) before its first
+ * request is admitted -- e.g. one sense_plan_autotune chose in persistent
+ * mode on a representative shape -- instead of variant 0 or tuning on the
+ * first request.  SENSE_EINVAL if the class already runs another variant or
+ * the variant does not exist for ny. */
+sense_status sense_queue_set_variant(sense_queue* q, int ny, int nx, int storage, int variant);
 /* Stop the scheduler (running requests are cancelled) and free everything. */
 sense_status sense_queue_destroy(sense_queue* q);
 

@@ -173,9 +173,10 @@ class PinnedArena {
   size_t reserved_ = 0, in_use_ = 0;
 };
 
-// memcpy, split over up to 8 threads for copies of 32 MiB and more.
+// memcpy, split over up to 8 threads (pieces of at least 2 MiB) for copies
+// of 4 MiB and more.
 inline void parallel_copy(void* dst, const void* src, size_t bytes) {
-  constexpr size_t kPiece = (size_t)16 << 20;
+  constexpr size_t kPiece = (size_t)2 << 20;
   const size_t hw = std::max(1u, std::thread::hardware_concurrency());
   const size_t parts = std::min<size_t>(std::min<size_t>(8, hw), bytes / kPiece);
   if (parts < 2) {

@@ -868,6 +868,22 @@ sense_status sense_queue_stats_get(sense_queue* q, sense_queue_stats* out) {
   return SENSE_OK;
 }
 
+sense_status sense_queue_set_variant(sense_queue* q, int ny, int nx, int storage, int variant) {
+  if (!q) return qfail(SENSE_EINVAL, "queue is NULL");
+  if (!sense_size_supported(ny) || !sense_size_supported(nx))
+    return qfail(SENSE_EUNSUPPORTED_SIZE, "no compiled transform for this ny / nx");
+  if (storage != SENSE_STORE_C64 && storage != SENSE_STORE_BF16) return qfail(SENSE_EINVAL, "bad storage");
+  if (variant < 0 || variant >= kNormVariants || normal_variant_width(ny, variant) <= 0)
+    return qfail(SENSE_EINVAL, "no such normal-operator variant for this ny");
+  std::lock_guard<std::mutex> lock(q->mu);
+  const auto key = std::make_tuple(ny, nx, storage);
+  auto it = q->variants.find(key);
+  if (it != q->variants.end() && it->second != variant)
+    return qfail(SENSE_EINVAL, "the size class already runs another variant (set it before its first request)");
+  q->variants[key] = variant;
+  return SENSE_OK;
+}
+
 int sense_queue_variant(sense_queue* q, int ny, int nx, int storage) {
   if (!q) return -1;
   std::lock_guard<std::mutex> lock(q->mu);

@@ -39,7 +39,7 @@ EXPORTED = (
     "sense_batch_create", "sense_batch_destroy", "sense_batch_workspace_bytes", "sense_batch_classes",
     "sense_batch_autotune", "sense_batch_set_variant", "sense_batch_cg_solve", "sense_batch_check",
     "sense_queue_create", "sense_queue_submit", "sense_queue_poll", "sense_queue_wait", "sense_queue_cancel",
-    "sense_queue_stats_get", "sense_queue_variant", "sense_queue_destroy",
+    "sense_queue_stats_get", "sense_queue_variant", "sense_queue_set_variant", "sense_queue_destroy",
 )
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = 0, 1, 2, 3, 4
 NORM_VARIANTS = 4
@@ -179,6 +179,8 @@ def load_library(path=LIB_PATH):
     lib.sense_queue_stats_get.restype = st
     lib.sense_queue_variant.argtypes = [vp, i, i, i]
     lib.sense_queue_variant.restype = i
+    lib.sense_queue_set_variant.argtypes = [vp, i, i, i, i]
+    lib.sense_queue_set_variant.restype = st
     lib.sense_queue_destroy.argtypes = [vp]
     lib.sense_queue_destroy.restype = st
     lib.sense_last_error.argtypes = []
@@ -480,6 +482,9 @@ class Queue:
     def variant(self, ny, nx, storage=STORE_C64):
         return load_library().sense_queue_variant(self.handle, ny, nx, storage)
 
+    def set_variant(self, ny, nx, variant, storage=STORE_C64):
+        _check(load_library().sense_queue_set_variant(self.handle, int(ny), int(nx), int(storage), int(variant)))
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             load_library().sense_queue_destroy(self.handle)
@@ -518,6 +523,10 @@ def sense_queue_stats_get(q):
 
 def sense_queue_variant(q, ny, nx, storage=STORE_C64):
     return q.variant(ny, nx, storage)
+
+
+def sense_queue_set_variant(q, ny, nx, variant, storage=STORE_C64):
+    return q.set_variant(ny, nx, variant, storage)
 
 
 def sense_queue_destroy(q):

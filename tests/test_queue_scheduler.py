@@ -258,3 +258,20 @@ def test_staging_reservation_and_growth():
             q.wait(rid)
     assert q.stats()["staging_in_use"] == 0
     q.close()
+
+
+def test_set_variant_before_first_request():
+    q = sense.Queue(fake_device=True, fake_tick_us=100, fake_iters=1)
+    assert q.variant(64, 64) == -1
+    q.set_variant(256, 256, 1)
+    assert q.variant(256, 256) == 1
+    q.set_variant(256, 256, 1)  # the same again is fine
+    with pytest.raises(sense.SenseError) as ei:
+        q.set_variant(256, 256, 2)  # the class already has one
+    assert ei.value.status == 1
+    with pytest.raises(sense.SenseError):
+        q.set_variant(64, 64, 3)  # 64 has no variant 3
+    with pytest.raises(sense.SenseError) as ei:
+        q.set_variant(100, 100, 0)
+    assert ei.value.status == 2
+    q.close()
