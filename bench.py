@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--mix-count", type=int, default=512)
     ap.add_argument("--serve-rates", default="50,200,800")
     ap.add_argument("--serve-requests", type=int, default=160)
+    ap.add_argument("--serve-live-work", type=int, default=0,
+                    help="serving: the queue's max_live_work (frames x coils x ny x nx live at once; 0 = default)")
     ap.add_argument("--cg-mode", default="auto", choices=("auto", "graph", "persistent"),
                     help="CG iteration scheme; 'auto' times both briefly and keeps the faster")
     ap.add_argument("--lam", type=float, default=0.0,
@@ -677,7 +679,7 @@ def run_serve(args):
         count = args.serve_requests
         arrivals = synth.poisson_arrivals(rate, count, seed=int(rate) + 1811)
         picks = synth.rng_for(int(rate) + 7).integers(0, len(pool), size=count)
-        q = sense.Queue(device=0, staging_reserve_bytes=SERVE_STAGING_BYTES)
+        q = sense.Queue(device=0, staging_reserve_bytes=SERVE_STAGING_BYTES, max_live_work=args.serve_live_work)
         for n, v in class_variant.items():
             q.set_variant(n, n, v)
         t0 = time.perf_counter()
@@ -716,6 +718,7 @@ def run_serve(args):
                                "CG to a relative residual of 1e-4 or 100 iterations",
                    "pool_shapes": len(pool),
                    "queue_variants": {str(n): v for n, v in sorted(class_variant.items())},
+                   "max_live_work": args.serve_live_work or "library default (2^26)",
                    "staging": "%d GiB of page-locked host staging reserved at queue creation, before the "
                               "stream starts" % (SERVE_STAGING_BYTES >> 30)},
         "rates": results,

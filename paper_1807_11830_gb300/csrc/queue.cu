@@ -230,6 +230,14 @@ void log_request(sense_queue* q, const Request* r) {
   std::fflush(q->log);
 }
 
+// Work of a request per CG iteration, in coil-pixels: frames x coils x ny x nx.
+double request_work(const sense_shape& sh) { return (double)sh.frames * sh.coils * sh.ny * sh.nx; }
+
+// Live work above which admission waits (sense_queue_cfg.max_live_work = 0):
+// about four times a 20-frame, 12-coil 256 x 256 cine series, which alone
+// keeps every SM of the GPU busy.
+constexpr double kDefaultLiveWork = (double)(1 << 26);
+
 void record_done(sense_queue* q, Request* r, int state) {
   std::lock_guard<std::mutex> lock(q->mu);
   r->state = state;
@@ -561,6 +569,9 @@ void worker_main(sense_queue* q) {
   if (!q->cfg.fake_device) cudaSetDevice(q->device);
   for (;;) {
     std::vector<Request*> admit;
+    const double work_cap = q->cfg.max_live_work > 0 ? (double)q->cfg.max_live_work : kDefaultLiveWork;
+    double live_work = 0.0;
+    for (const Request* r : q->live) live_work += request_work(r->sh);
     {
       std::unique_lock<std::mutex> lock(q->mu);
       q->cv_work.wait(lock, [&] { return q->stop || !q->pending.empty() || !q->live.empty(); });
@@ -579,6 +590,10 @@ void worker_main(sense_queue* q) {
         const size_t n_live = q->live.size() + admit.size();
         if (q->cfg.max_live > 0 && (int)n_live >= q->cfg.max_live) break;
         if (q->in_use + r->need > q->budget) break;  // arrival order: the head waits for room
+        // enough work live to fill the GPU: later requests wait, in arrival order, rather
+        // than share every tick and all finish late (a lone request over the cap is admitted)
+        if (live_work > 0 && live_work + request_work(r->sh) > work_cap) break;
+        live_work += request_work(r->sh);
         q->pending.pop_front();
         q->in_use += r->need;
         r->state = SENSE_REQ_RUNNING;

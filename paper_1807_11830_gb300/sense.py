@@ -80,7 +80,7 @@ class _QueueCfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_live", ctypes.c_int), ("fake_device", ctypes.c_int),
                 ("fake_tick_us", ctypes.c_int), ("fake_iters", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("iters_per_tick", ctypes.c_int), ("fail_admit_every", ctypes.c_int),
-                ("staging_reserve_bytes", ctypes.c_size_t)]
+                ("staging_reserve_bytes", ctypes.c_size_t), ("max_live_work", ctypes.c_size_t)]
 
 
 class _QueueStats(ctypes.Structure):
@@ -448,9 +448,11 @@ class Queue:
     bits), lines int32."""
 
     def __init__(self, device=0, hbm_budget_bytes=0, max_live=0, fake_device=False, fake_tick_us=0,
-                 fake_iters=0, autotune=False, iters_per_tick=0, fail_admit_every=0, staging_reserve_bytes=0):
+                 fake_iters=0, autotune=False, iters_per_tick=0, fail_admit_every=0, staging_reserve_bytes=0,
+                 max_live_work=0):
         cfg = _QueueCfg(hbm_budget_bytes, max_live, 1 if fake_device else 0, fake_tick_us, fake_iters,
-                        1 if autotune else 0, iters_per_tick, fail_admit_every, staging_reserve_bytes)
+                        1 if autotune else 0, iters_per_tick, fail_admit_every, staging_reserve_bytes,
+                        max_live_work)
         h = ctypes.c_void_p()
         _check(load_library().sense_queue_create(device, ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h

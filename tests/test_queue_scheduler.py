@@ -275,3 +275,28 @@ def test_set_variant_before_first_request():
         q.set_variant(100, 100, 0)
     assert ei.value.status == 2
     q.close()
+
+
+def test_live_work_cap_admits_in_arrival_order():
+    one = 64 * 64 * 4 * 2  # frames x coils x ny x nx of _req()
+    q = sense.Queue(fake_device=True, fake_tick_us=1000, fake_iters=5, max_live_work=2 * one)
+    ids = [q.submit(*_req(), max_iter=5) for _ in range(6)]
+    peak, order, pending = 0, [], set(ids)
+    while pending:
+        peak = max(peak, q.stats()["live"])
+        for rid in sorted(pending):
+            if q.poll(rid)[0] == sense.REQ_DONE:
+                order.append(rid)
+                pending.discard(rid)
+        time.sleep(0.0002)
+    assert peak == 2 and order == ids
+    for rid in ids:
+        q.wait(rid)
+    q.close()
+    # a request larger than the cap still runs, alone
+    q = sense.Queue(fake_device=True, fake_tick_us=200, fake_iters=2, max_live_work=one // 2)
+    a, b = q.submit(*_req(), max_iter=2), q.submit(*_req(), max_iter=2)
+    q.wait(a)
+    q.wait(b)
+    assert q.stats()["completed"] == 2
+    q.close()
