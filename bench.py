@@ -718,7 +718,7 @@ def run_serve(args):
                                "CG to a relative residual of 1e-4 or 100 iterations",
                    "pool_shapes": len(pool),
                    "queue_variants": {str(n): v for n, v in sorted(class_variant.items())},
-                   "max_live_work": args.serve_live_work or "library default (2^26)",
+                   "max_live_work": args.serve_live_work or "no limit",
                    "staging": "%d GiB of page-locked host staging reserved at queue creation, before the "
                               "stream starts" % (SERVE_STAGING_BYTES >> 30)},
         "rates": results,

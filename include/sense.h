@@ -252,11 +252,12 @@ typedef struct {
                               sense_queue_wait returns SENSE_ENOMEM */
   size_t staging_reserve_bytes; /* page-locked host staging allocated at creation (0: none); the
                                    staging arena grows on demand beyond it */
-  size_t max_live_work;    /* admit while the live requests' work, sum of frames x coils x ny x nx,
-                              stays at or below this (a request is admitted alone whatever its size);
-                              0 = 2^26, about four 20-frame 12-coil 256^2 series.  Requests beyond it
-                              wait in arrival order instead of sharing every tick, which keeps the GPU
-                              full while early requests finish early */
+  size_t max_live_work;    /* 0 = no limit.  Otherwise admit while the live requests' work, the sum of
+                              frames x coils x ny x nx, stays at or below this (a request is admitted
+                              alone whatever its size): under overload, requests beyond it wait in
+                              arrival order instead of sharing every tick, so early ones finish early.
+                              Too low a value leaves the GPU part idle; waiting requests keep their
+                              host staging */
 } sense_queue_cfg;
 
 typedef enum {

@@ -233,11 +233,6 @@ void log_request(sense_queue* q, const Request* r) {
 // Work of a request per CG iteration, in coil-pixels: frames x coils x ny x nx.
 double request_work(const sense_shape& sh) { return (double)sh.frames * sh.coils * sh.ny * sh.nx; }
 
-// Live work above which admission waits (sense_queue_cfg.max_live_work = 0):
-// about four times a 20-frame, 12-coil 256 x 256 cine series, which alone
-// keeps every SM of the GPU busy.
-constexpr double kDefaultLiveWork = (double)(1 << 26);
-
 void record_done(sense_queue* q, Request* r, int state) {
   std::lock_guard<std::mutex> lock(q->mu);
   r->state = state;
@@ -569,7 +564,7 @@ void worker_main(sense_queue* q) {
   if (!q->cfg.fake_device) cudaSetDevice(q->device);
   for (;;) {
     std::vector<Request*> admit;
-    const double work_cap = q->cfg.max_live_work > 0 ? (double)q->cfg.max_live_work : kDefaultLiveWork;
+    const double work_cap = q->cfg.max_live_work > 0 ? (double)q->cfg.max_live_work : 1e300;
     double live_work = 0.0;
     for (const Request* r : q->live) live_work += request_work(r->sh);
     {
