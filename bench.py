@@ -661,18 +661,18 @@ def run_serve(args):
         pool.append(dict(shape=dict(ny=n, nx=n, coils=C, frames=F, lines=L), y=y_d.cpu().numpy(),
                          S=p.S.astype(np.complex64), lines=p.lines, solve_s=solve_s, frames=F, n=n))
         plan.close()
-    # kernel variant per size class for the queue: autotuned in persistent mode on the class's
-    # first pool shape, once, before any stream (as a deployment would load it from a cache)
+    # kernel variant per size class for the queue: autotuned in persistent mode once, before any
+    # stream (as a deployment would load it from a cache), on a loaded class -- 30 frames of 16
+    # coils at R = 4 -- since under load each class launch carries the frames of many requests
     class_variant = {}
-    for e in pool:
-        n = e["n"]
-        if n in class_variant:
-            continue
-        sh = e["shape"]
-        tp = sense.Plan(n, n, sh["coils"], sh["frames"], sh["lines"])
+    for n in sorted({e["n"] for e in pool}):
+        F_t, C_t, L_t = 30, 16, n // 4
+        tp = sense.Plan(n, n, C_t, F_t, L_t)
         sense.sense_plan_set_cg_mode(tp, sense.CG_MODE_PERSISTENT)
-        class_variant[n], _ = sense.sense_plan_autotune(tp, torch.from_numpy(e["S"]).to(dev),
-                                                        torch.from_numpy(e["lines"]).to(dev))
+        lines_t = synth.mask_lines(n, L_t, synth.centre_for(n), F_t, synth.rng_for(4242 + n))
+        S_t = synth.sensitivities(C_t, n, n).astype(np.complex64)
+        class_variant[n], _ = sense.sense_plan_autotune(tp, torch.from_numpy(S_t).to(dev),
+                                                        torch.from_numpy(np.ascontiguousarray(lines_t, np.int32)).to(dev))
         tp.close()
     results = {}
     for rate in [float(r) for r in args.serve_rates.split(",")]:
