@@ -11,6 +11,8 @@
 //
 // Transforms are unitary: every length-N pass scales by 1/sqrt(N).
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sense {
@@ -57,9 +59,10 @@ struct RowPass {
 };
 
 template <int N>
-constexpr size_t row_smem_bytes() {
+__host__ __device__ constexpr size_t row_smem_bytes() {
   using R = RowPass<N>;
-  return sizeof(float2) * (size_t)N + sizeof(float2) * (size_t)R::C::W * R::P + sizeof(float2) * (size_t)R::C::W * N;
+  return sizeof(float2) * (size_t)N + sizeof(float2) * (size_t)R::C::W * R::P + sizeof(float2) * (size_t)R::C::W * N +
+         16;  // mbarrier of the bulk row copies
 }
 
 struct ColSmem {
@@ -209,6 +212,7 @@ struct RowArgs {
   long rows;
   int centred;  // 1: k-space elements times cs (-1)^kx (inverse: on input; forward: on output)
   float cs;     // (-1)^(ny/2 + nx/2)
+  int* err;     // error word (ERR_TIMEOUT from a bulk copy that never landed); may be NULL
 };
 
 template <int N, int DIR, class InSt, class OutSt, int TH = RowPass<N>::C::THREADS>
@@ -216,15 +220,42 @@ __global__ void __launch_bounds__(TH)
     k_rows(RowArgs<typename InSt::T, typename OutSt::T> a) {
   using C = typename RowPass<N>::C;
   constexpr int P = RowPass<N>::P;  // padded row pitch (conflict-free column access)
+  // Complex64 rows move between global and shared memory as 1D bulk copies,
+  // one per row, instead of through registers: with N even and the pitch
+  // N + 2, every global row and every shared row starts 16-byte aligned
+  // when the base pointer is (checked at run time; otherwise the threads copy).
+  constexpr bool kBulkIn = std::is_same<typename InSt::T, float2>::value && P == N + 2;
+  constexpr bool kBulkOut = std::is_same<typename OutSt::T, float2>::value && P == N + 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tw = reinterpret_cast<float2*>(smem_raw);
   float2* tile = tw + N;
   float2* bufs[2] = {tile, tile + C::W * P};  // the tile doubles as the first exchange buffer
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + row_smem_bytes<N>() - 16);
   const C col;
   const long r0 = (long)blockIdx.x * C::W;
-  // every load of the tile is issued before the first shared store
-  constexpr int PER = (C::W * N + C::THREADS - 1) / C::THREADS;
-  {
+  const int nrows = (int)((a.rows - r0) < (long)C::W ? (a.rows - r0) : (long)C::W);
+  const bool bulk_in = kBulkIn && (reinterpret_cast<uintptr_t>(a.in) & 15u) == 0;
+  const bool bulk_out = kBulkOut && (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0;
+  constexpr unsigned kRowBytes = (unsigned)(sizeof(float2) * N);
+  if (bulk_in) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_arrive_expect_tx(bar, kRowBytes * (unsigned)nrows);
+      for (int rr = 0; rr < nrows; ++rr)
+        bulk_load(tile + rr * P, reinterpret_cast<const float2*>(a.in) + (size_t)(r0 + rr) * N, kRowBytes, bar);
+    }
+    for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = a.tw[i];
+    if (!mbar_wait(bar, 0)) {  // never expected; flag it and let the copies land before going on
+      if (threadIdx.x == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
+      mbar_wait(bar, 0);
+    }
+  } else {
+    // every load of the tile is issued before the first shared store
+    constexpr int PER = (C::W * N + C::THREADS - 1) / C::THREADS;
     float2 v[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
@@ -254,16 +285,26 @@ __global__ void __launch_bounds__(TH)
     __syncthreads();  // the tile becomes the exchange buffer
     col.fwd(xr, kr, bufs, tw);
     __syncthreads();
+    // centred k-space: with the bulk store the signs go on here, not at the global store
+    const bool sign_here = bulk_out && a.centred;
 #pragma unroll
     for (int j = 0; j < C::JL; ++j)
 #pragma unroll
       for (int m = 0; m < C::RL; ++m)
-        if (col.okL(j)) row[col.krow(j, m)] = cscale(kr[j][m], scale);
+        if (col.okL(j)) {
+          const int e = col.krow(j, m);
+          row[e] = cscale(kr[j][m], sign_here ? ((e & 1) ? -scale * a.cs : scale * a.cs) : scale);
+        }
   } else {
+    const bool sign_here = bulk_in && a.centred;  // the bulk load did not apply the k-space signs
 #pragma unroll
     for (int j = 0; j < C::JL; ++j)
 #pragma unroll
-      for (int m = 0; m < C::RL; ++m) kr[j][m] = col.okL(j) ? row[col.krow(j, m)] : make_float2(0.f, 0.f);
+      for (int m = 0; m < C::RL; ++m) {
+        const int e = col.krow(j, m);
+        kr[j][m] = col.okL(j) ? row[e] : make_float2(0.f, 0.f);
+        if (sign_here) kr[j][m] = cscale(kr[j][m], (e & 1) ? -a.cs : a.cs);
+      }
     __syncthreads();
     col.inv(kr, xr, bufs, tw);
     __syncthreads();
@@ -273,8 +314,19 @@ __global__ void __launch_bounds__(TH)
       for (int n = 0; n < C::R0; ++n)
         if (col.ok0(j)) row[col.xrow(j, n)] = cscale(xr[j][n], scale);
   }
+  if (bulk_out) {
+    fence_proxy_async_smem();  // this thread's shared writes, before the bulk engine reads them
+    __syncthreads();
+    if ((int)threadIdx.x < nrows) {
+      bulk_store(reinterpret_cast<float2*>(a.out) + (size_t)(r0 + threadIdx.x) * N, tile + threadIdx.x * P,
+                 kRowBytes);
+      bulk_commit_wait_read();
+    }
+    return;
+  }
   __syncthreads();
   {
+    constexpr int PER = (C::W * N + C::THREADS - 1) / C::THREADS;
     float2 v[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {

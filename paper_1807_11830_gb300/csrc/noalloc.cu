@@ -123,6 +123,7 @@ sense_status noalloc_adjoint(const sense_shape& sh, const DeviceTables& t, const
   ra.rows = (long)sh.frames * sh.coils * sh.lines;
   ra.centred = sh.centred;
   ra.cs = ((sh.ny / 2 + sh.nx / 2) & 1) ? -1.0f : 1.0f;
+  ra.err = t.err;
   cudaError_t e = launch_rows_inv<St>(sh.nx, ra, st);
   if (e != cudaSuccess) {
     *msg = std::string("adjoint row pass: ") + cudaGetErrorString(e);

@@ -256,6 +256,7 @@ sense_status run_forward(sense_plan* pl, const float2* x, const void* S, const i
   ra.rows = (long)sh.frames * sh.coils * sh.lines;
   ra.centred = sh.centred;
   ra.cs = centred_sign(sh);
+  ra.err = pl->err();
   PhaseScope ps(pl, SENSE_PHASE_ROWS_FWD, st);
   return launch_status(launch_rows_fwd<St>(sh.nx, ra, st), "forward row pass");
 }
@@ -270,6 +271,7 @@ sense_status run_rows_inv(sense_plan* pl, const void* y, cudaStream_t st) {
   ra.rows = (long)sh.frames * sh.coils * sh.lines;
   ra.centred = sh.centred;
   ra.cs = centred_sign(sh);
+  ra.err = pl->err();
   PhaseScope ps(pl, SENSE_PHASE_ROWS_INV, st);
   return launch_status(launch_rows_inv<St>(sh.nx, ra, st), "adjoint row pass");
 }
