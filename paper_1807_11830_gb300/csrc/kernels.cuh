@@ -344,6 +344,112 @@ __global__ void __launch_bounds__(TH)
   }
 }
 
+// Row pass over complex64 rows in and out, persistent: each block loops over
+// row tiles (blockIdx.x, + gridDim.x, ...).  While it transforms one tile,
+// the bulk-copy engine brings the next tile's rows into the other of two
+// tile buffers, so the HBM latency of a block's loads hides behind its own
+// arithmetic.  Results go back by per-row bulk stores from the tile.  The
+// launcher uses it when both pointers are 16-byte aligned (rows then start
+// 16-byte aligned, N being even) and the pitch is N + 2.
+template <int N>
+__host__ __device__ constexpr size_t row_bulk_smem_bytes() {
+  using R = RowPass<N>;
+  return sizeof(float2) * ((size_t)N + 2 * (size_t)R::C::W * R::P + (size_t)R::C::W * N) + 16;
+}
+
+template <int N, int DIR, int TH = RowPass<N>::C::THREADS>
+__global__ void __launch_bounds__(TH) k_rows_bulk(RowArgs<float2, float2> a) {
+  using C = typename RowPass<N>::C;
+  constexpr int P = RowPass<N>::P;
+  static_assert(P == N + 2, "bulk row copies need the 16-byte row pitch N + 2");
+  constexpr unsigned kRowBytes = (unsigned)(sizeof(float2) * N);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* const tile0 = tw + N;  // picked with selects: a run-time index would put a pointer array in local memory
+  float2* const tile1 = tw + N + C::W * P;
+  float2* buf1 = tw + N + 2 * C::W * P;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(buf1 + C::W * N);  // one per tile buffer
+  const long ntiles = (a.rows + C::W - 1) / C::W;
+  const C col;
+  // thread 0: arm bar[b] and copy the rows of tile t into buffer b
+  auto fetch = [&](long t, int b) {
+    const long r0 = t * C::W;
+    const int nrows = (int)((a.rows - r0) < (long)C::W ? (a.rows - r0) : (long)C::W);
+    mbar_arrive_expect_tx(bar + b, kRowBytes * (unsigned)nrows);
+    float2* dst = b ? tile1 : tile0;
+    for (int rr = 0; rr < nrows; ++rr) bulk_load(dst + rr * P, a.in + (size_t)(r0 + rr) * N, kRowBytes, bar + b);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && (long)blockIdx.x < ntiles) fetch(blockIdx.x, 0);
+  for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = a.tw[i];
+  __syncthreads();
+  const float scale = rsqrtf((float)N);
+  int it = 0;
+  for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int cur = it & 1;
+    const long r0 = t * C::W;
+    const int nrows = (int)((a.rows - r0) < (long)C::W ? (a.rows - r0) : (long)C::W);
+    // the other buffer's last stores have read it (waited below, then a barrier)
+    if (threadIdx.x == 0 && t + gridDim.x < ntiles) fetch(t + gridDim.x, cur ^ 1);
+    const unsigned parity = (unsigned)(it >> 1) & 1u;
+    if (!mbar_wait(bar + cur, parity)) {  // never expected; flag it and let the copies land
+      if (threadIdx.x == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
+      mbar_wait(bar + cur, parity);
+    }
+    float2* tile = cur ? tile1 : tile0;
+    float2* bufs[2] = {tile, buf1};  // the tile doubles as the first exchange buffer
+    float2* row = tile + col.c * P;
+    float2 xr[C::J0][C::R0];
+    float2 kr[C::JL][C::RL];
+    if (DIR < 0) {
+#pragma unroll
+      for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+        for (int n = 0; n < C::R0; ++n) xr[j][n] = col.ok0(j) ? row[col.xrow(j, n)] : make_float2(0.f, 0.f);
+      __syncthreads();
+      col.fwd(xr, kr, bufs, tw);
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < C::JL; ++j)
+#pragma unroll
+        for (int m = 0; m < C::RL; ++m)
+          if (col.okL(j)) {
+            const int e = col.krow(j, m);  // centred k-space: sign (-1)^kx on the output
+            row[e] = cscale(kr[j][m], a.centred ? ((e & 1) ? -scale * a.cs : scale * a.cs) : scale);
+          }
+    } else {
+#pragma unroll
+      for (int j = 0; j < C::JL; ++j)
+#pragma unroll
+        for (int m = 0; m < C::RL; ++m) {
+          const int e = col.krow(j, m);  // centred k-space: sign (-1)^kx on the input
+          kr[j][m] = col.okL(j) ? row[e] : make_float2(0.f, 0.f);
+          if (a.centred) kr[j][m] = cscale(kr[j][m], (e & 1) ? -a.cs : a.cs);
+        }
+      __syncthreads();
+      col.inv(kr, xr, bufs, tw);
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+        for (int n = 0; n < C::R0; ++n)
+          if (col.ok0(j)) row[col.xrow(j, n)] = cscale(xr[j][n], scale);
+    }
+    fence_proxy_async_smem();  // this thread's shared writes, before the bulk engine reads them
+    __syncthreads();
+    if ((int)threadIdx.x < nrows) {
+      bulk_store(a.out + (size_t)(r0 + threadIdx.x) * N, tile + threadIdx.x * P, kRowBytes);
+      bulk_commit_wait_read();
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // E^H, column pass.  MODE 0: x = sum_c conj(S_c) F_y^H(...)
 //                    MODE 1: same, written as CG start r = p = b, x = 0, rho0
