@@ -621,6 +621,9 @@ void worker_main(sense_queue* q) {
     if (q->cfg.fake_device) {
       tick_fake(q);
     } else if (!tick_device(q)) {
+      // launches already issued on the class streams may still read the requests' memory
+      for (auto& kv : q->classes)
+        if (kv.second.stream) cudaStreamSynchronize(kv.second.stream);
       for (Request* r : q->live) {
         free_device(r, q->stream);
         record_done(q, r, SENSE_REQ_FAILED);
