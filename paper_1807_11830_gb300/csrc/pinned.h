@@ -187,13 +187,20 @@ inline void parallel_copy(void* dst, const void* src, size_t bytes) {
   char* d = static_cast<char*>(dst);
   const char* s = static_cast<const char*>(src);
   std::vector<std::thread> workers;
+  size_t done_to = step;  // bytes [0, done_to) are this thread's or a worker's
   for (size_t i = 1; i < parts; ++i) {
     const size_t off = i * step;
     if (off >= bytes) break;
     const size_t len = std::min(step, bytes - off);
-    workers.emplace_back([=] { std::memcpy(d + off, s + off, len); });
+    try {
+      workers.emplace_back([=] { std::memcpy(d + off, s + off, len); });
+    } catch (...) {  // no thread to be had: copy the rest here (no exception crosses the C ABI)
+      break;
+    }
+    done_to = off + len;
   }
   std::memcpy(d, s, std::min(step, bytes));
+  if (done_to < bytes) std::memcpy(d + done_to, s + done_to, bytes - done_to);
   for (std::thread& t : workers) t.join();
 }
 
