@@ -153,3 +153,30 @@ def test_large_requests_staged_in_parallel_equal_alone():
     st = q.stats()
     assert st["staging_in_use"] == 0 and st["hbm_in_use"] == 0
     q.close()
+
+
+def test_pinned_class_variant_is_used():
+    """A size class pinned with sense_queue_set_variant runs that variant:
+    served results equal a plan solve with it, bit for bit."""
+    dev = "cuda:0"
+    n, C, F, L, K = 256, 6, 3, 64, 6
+    rng = synth.rng_for(3200)
+    S = np.ascontiguousarray(synth.sensitivities(C, n, n), np.complex64)
+    lines = np.ascontiguousarray(synth.mask_lines(n, L, synth.centre_for(n), F, rng), np.int32)
+    y = np.ascontiguousarray(synth.random_complex((F, C, L, n), rng), np.complex64)
+    shape = dict(ny=n, nx=n, coils=C, frames=F, lines=L)
+    for variant in (1, 3):
+        q = sense.Queue(device=0)
+        q.set_variant(n, n, variant)
+        x = np.empty((F, n, n), np.complex64)
+        q.wait(q.submit(shape, y, S, lines, max_iter=K), x)
+        assert q.variant(n, n) == variant
+        q.close()
+        plan = sense.Plan(n, n, C, F, L)
+        sense.sense_plan_set_variant(plan, variant)
+        sense.sense_plan_set_cg_mode(plan, sense.CG_MODE_PERSISTENT)
+        xa = torch.empty((F, n, n), dtype=torch.complex64, device=dev)
+        sense.sense_cg_solve(plan, torch.from_numpy(y).to(dev), torch.from_numpy(S).to(dev),
+                             torch.from_numpy(lines).to(dev), K, 0.0, xa)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(xa.cpu().numpy(), x)
