@@ -276,6 +276,49 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
+def time_operators(plan, x_img, y, S, lines, flush, stream, dev, reps=20):
+    """E (sense_forward), E^H (sense_adjoint) and E^H E (sense_normal) on the
+    cine configuration, each call timed alone with CUDA events on `stream`
+    after 3 warm-up calls, L2 flushed before each.  Applications = frames.
+    Algorithmic bytes per call: the operator's inputs and outputs once (S
+    once for all frames); the two-pass intermediate is not counted."""
+    import torch
+
+    from paper_1807_11830_gb300 import sense
+
+    F, ny, nx = x_img.shape
+    C, L = S.shape[0], lines.shape[1]
+    img = ny * nx
+    y_out = torch.empty_like(y)
+    x_out = torch.empty_like(x_img)
+    calls = {
+        "forward": (lambda: sense.sense_forward(plan, x_img, S, lines, y_out, stream=stream),
+                    8 * (F * img + C * img + F * C * L * nx)),
+        "adjoint": (lambda: sense.sense_adjoint(plan, y, S, lines, x_out, stream=stream),
+                    8 * (F * C * L * nx + C * img + F * img)),
+        "normal": (lambda: sense.sense_normal(plan, x_img, S, lines, x_out, stream=stream),
+                   8 * (C * img + 2 * F * img)),
+    }
+    hbm_gbs, _, _ = peaks()
+    out = {}
+    for name, (call, nbytes) in calls.items():
+        for _ in range(3):
+            call()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in ev:
+            flush.fill_(3)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sense.sense_plan_check(plan)
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / reps
+        gbs = nbytes / (ms / 1e3) / 1e9
+        out[name] = {"applications_per_s": F / (ms / 1e3), "ms": ms, "algorithmic_mb": nbytes / 1e6,
+                     "achieved_gbs": gbs, "hbm_frac": gbs / hbm_gbs}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -422,6 +465,9 @@ def run_ours(args):
             phase[name] = {"ms_per_launch": ms / n, "launches": n, "ms_total": ms}
     sense.sense_plan_set_timing(plan, False)
 
+    # ---- the operators on their own (steps A, B, C outside CG), same plan and inputs ----
+    operators = time_operators(plan, x_true, y, S, lines, flush, stream, dev) if rank == 0 else None
+
     # max over ranks
     total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], world, dev)
 
@@ -483,6 +529,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clocks.summary(t_wall0, t_wall1),
             "kernels_us": {k: round(v["ms_per_launch"] * 1e3, 2) for k, v in phase.items()},
+            "operators": operators,
             "normal_variant": variant,
             "cg_mode": cg_mode,
             "cg_mode_ms": {k: round(v, 4) for k, v in mode_ms.items()},
