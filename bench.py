@@ -48,10 +48,9 @@ PAPER_WORKLOAD = ("paper reconstruction: 16 frames x 160x160, 8 coils, fully sam
 PAPER_METRIC, PAPER_UNIT = "reconstructions/s", "reconstructions/s"
 # OpenCLIPER's own time for this workload on a GTX 970 (Table II: clFFT 1.361 ms + RSS 0.252 ms): context
 PAPER_GTX970_MS = 1.361 + 0.252
-# ncu DRAM traffic per launch of the paper workload's kernels (read + write); None where the
-# kernel has changed since its counters were taken (the row pass became the persistent
-# bulk-copy kernel after its last capture)
-PAPER_TRAFFIC = {"rows_inv": None, "adj_col": 26.254848e6 + 0.0}
+# ncu DRAM traffic per launch of the paper workload's kernels (read + write), from one launch
+# list of `bench.py --workload paper` (k_rows_bulk<160,+1>, k_adj_col<160,c64,rss>)
+PAPER_TRAFFIC = {"rows_inv": 26.232576e6 + 0.0, "adj_col": 26.254848e6 + 0.0}
 
 
 def parse_args():
