@@ -51,6 +51,17 @@ MUTANTS = {
     # centred transform shifts the input the wrong way (differs for odd n)
     "centred_shift_direction": ("rotate_strided(n, v, stride, -(n / 2));  // ifftshift",
                                 "rotate_strided(n, v, stride, n / 2);  // ifftshift"),
+    # RSS sums magnitudes instead of squared magnitudes
+    "rss_abs_not_square": ("acc[i] += std::norm(z[i]);", "acc[i] += std::abs(z[i]);"),
+    # RSS forgets the square root
+    "rss_no_sqrt": ("out[f * npix + i] = std::sqrt(acc[i]);", "out[f * npix + i] = acc[i];"),
+    # column-wise normal operator forgets the mask
+    "collapsed_no_mask": ("          if (!sampled[r]) col[r] = 0.0;\n", "\n"),
+    # column-wise normal operator applies the second transform in the forward direction
+    "collapsed_second_forward": ("        fft1_strided(ny, +1, col.data(), 1, a, b);\n"
+                                 "        for (int r = 0; r < ny; ++r) of[(long)r * nx + j]",
+                                 "        fft1_strided(ny, -1, col.data(), 1, a, b);\n"
+                                 "        for (int r = 0; r < ny; ++r) of[(long)r * nx + j]"),
 }
 
 QUICK_PINS = [
@@ -68,6 +79,8 @@ QUICK_PINS = [
     lambda: centred.test_centred_adjoint_identity_and_full_sampling((16, 12, 3, 7, 2)),
     lambda: pins.test_regularised_cg_against_dense_solves(0.0625),
     lambda: pins.test_temporal_cg_against_dense_solves(3, 0.0, 0.5),
+    pins.test_rss_closed_forms,
+    lambda: pins.test_normal_equals_collapsed_form(pins.SHAPES[0]),
 ]
 
 
