@@ -83,6 +83,27 @@ __device__ __forceinline__ float2 cfma_conj(float2 acc, float2 b, float2 a) {
   return make_float2(fmaf(b.x, a.x, fmaf(b.y, a.y, acc.x)), fmaf(b.x, a.y, fmaf(-b.y, a.x, acc.y)));
 }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// Compensated (Kahan) accumulation of a coil sum, hi + lo ~ sum_c conj(b_c) a_c.
+// A plain FP32 running sum rounds every step relative to the partial sum, so
+// its error grows with the number of coils and, inside CG, with the iteration
+// count; lo carries the low-order bits each addition drops.  The steps use
+// explicit round-to-nearest operations so that nothing is contracted or
+// reassociated.
+// y = (the new term) - lo is formed by the fused multiply-adds that make the
+// term, so each component costs two FMAs and three adds.
+__device__ __forceinline__ void kahan_step(float& hi, float& lo, float y) {
+  const float t = __fadd_rn(hi, y);
+  lo = __fsub_rn(__fsub_rn(t, hi), y);
+  hi = t;
+}
+__device__ __forceinline__ void csum_fma_conj(float2& hi, float2& lo, float2 b, float2 a) {
+  kahan_step(hi.x, lo.x, __fmaf_rn(b.x, a.x, __fmaf_rn(b.y, a.y, -lo.x)));
+  kahan_step(hi.y, lo.y, __fmaf_rn(b.x, a.y, __fmaf_rn(-b.y, a.x, -lo.y)));
+}
+__device__ __forceinline__ float2 csum_value(float2 hi, float2 lo) {
+  return make_float2(__fsub_rn(hi.x, lo.x), __fsub_rn(hi.y, lo.y));
+}
 // multiply by DIR * i
 template <int DIR>
 __device__ __forceinline__ float2 mul_i(float2 a) {

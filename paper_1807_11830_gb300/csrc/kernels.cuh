@@ -237,6 +237,7 @@ __global__ void __launch_bounds__(TH)
   const bool bulk_in = kBulkIn && (reinterpret_cast<uintptr_t>(a.in) & 15u) == 0;
   const bool bulk_out = kBulkOut && (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0;
   constexpr unsigned kRowBytes = (unsigned)(sizeof(float2) * N);
+  bool landed = true;  // false if the bulk row copies never completed: the block then stores nothing
   if (bulk_in) {
     if (threadIdx.x == 0) {
       mbar_init(bar, 1);
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(TH)
     for (int i = threadIdx.x; i < N; i += C::THREADS) tw[i] = a.tw[i];
     if (!mbar_wait(bar, 0)) {  // never expected; flag it and let the copies land before going on
       if (threadIdx.x == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
-      mbar_wait(bar, 0);
+      landed = mbar_wait(bar, 0);
     }
   } else {
     // every load of the tile is issued before the first shared store
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(TH)
       if (i < C::W * N) tile[rr * P + e] = v[k];
     }
   }
-  __syncthreads();
+  if (!__syncthreads_and(landed)) return;  // uniform: the tile never arrived (ERR_TIMEOUT raised)
   const float scale = rsqrtf((float)N);
   float2 xr[C::J0][C::R0];
   float2 kr[C::JL][C::RL];
@@ -397,10 +398,13 @@ __global__ void __launch_bounds__(TH) k_rows_bulk(RowArgs<float2, float2> a) {
     // the other buffer's last stores have read it (waited below, then a barrier)
     if (threadIdx.x == 0 && t + gridDim.x < ntiles) fetch(t + gridDim.x, cur ^ 1);
     const unsigned parity = (unsigned)(it >> 1) & 1u;
+    bool landed = true;
     if (!mbar_wait(bar + cur, parity)) {  // never expected; flag it and let the copies land
       if (threadIdx.x == 0 && a.err) atomicOr(a.err, ERR_TIMEOUT);
-      mbar_wait(bar + cur, parity);
+      landed = mbar_wait(bar + cur, parity);
     }
+    // a tile that never arrived is skipped by the whole block (its rows keep their contents)
+    const bool skip = !__syncthreads_and(landed);
     float2* tile = cur ? tile1 : tile0;
     float2* bufs[2] = {tile, buf1};  // the tile doubles as the first exchange buffer
     float2* row = tile + col.c * P;
@@ -442,7 +446,7 @@ __global__ void __launch_bounds__(TH) k_rows_bulk(RowArgs<float2, float2> a) {
     }
     fence_proxy_async_smem();  // this thread's shared writes, before the bulk engine reads them
     __syncthreads();
-    if ((int)threadIdx.x < nrows) {
+    if (!skip && (int)threadIdx.x < nrows) {
       bulk_store(a.out + (size_t)(r0 + threadIdx.x) * N, tile + threadIdx.x * P, kRowBytes);
       bulk_commit_wait_read();
     }
@@ -483,13 +487,14 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St>
   load_tw_and_linemap<N, C::THREADS>(s, a.tw, a.lines + (size_t)f * a.L, a.L, a.err);
   const size_t img = (size_t)N * a.nx;
 
-  float2 acc[C::J0][C::R0];
+  float2 acc[C::J0][C::R0], accl[C::J0][C::R0];  // compensated coil sum (MODE 0, 1)
   float accr[C::J0][C::R0];
 #pragma unroll
   for (int j = 0; j < C::J0; ++j)
 #pragma unroll
     for (int n = 0; n < C::R0; ++n) {
       acc[j][n] = make_float2(0.f, 0.f);
+      accl[j][n] = make_float2(0.f, 0.f);
       accr[j][n] = 0.f;
     }
 
@@ -567,7 +572,7 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St>
         if (MODE == 2)
           accr[j][n] = fmaf(xr[j][n].x, xr[j][n].x, fmaf(xr[j][n].y, xr[j][n].y, accr[j][n]));
         else
-          acc[j][n] = cfma_conj(acc[j][n], sv[j][n], xr[j][n]);
+          csum_fma_conj(acc[j][n], accl[j][n], sv[j][n], xr[j][n]);
       }
   }
 
@@ -582,7 +587,7 @@ __global__ void __launch_bounds__(TH, ColPass<N>::MINB) k_adj_col(AdjColArgs<St>
       if (MODE == 2) {
         a.rss[idx] = sqrtf(accr[j][n] * (1.0f / (float)N));
       } else {
-        const float2 v = cscale(acc[j][n], scale);
+        const float2 v = cscale(csum_value(acc[j][n], accl[j][n]), scale);
         if (MODE == 0) {
           a.x[idx] = negate_if(v, a.centred && ((col.xrow(j, n) + x) & 1));
         } else {
@@ -672,7 +677,7 @@ __device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem&
   const int x = a.tile * C::W + col.c;
   const bool xin = x < a.nx;
   const size_t img = (size_t)N * a.nx;
-  float2 p[C::J0][C::R0], q[C::J0][C::R0];
+  float2 p[C::J0][C::R0], q[C::J0][C::R0], ql[C::J0][C::R0];  // q: compensated coil sum
 #pragma unroll
   for (int j = 0; j < C::J0; ++j)
 #pragma unroll
@@ -693,6 +698,7 @@ __device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem&
       }
       p[j][n] = v;
       q[j][n] = make_float2(0.f, 0.f);
+      ql[j][n] = make_float2(0.f, 0.f);
     }
 
   float2* bufs[2] = {s.buf0, s.buf1};
@@ -722,7 +728,7 @@ __device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem&
       for (int n = 0; n < C::R0; ++n) {
         float2 sv = make_float2(0.f, 0.f);
         if (col.ok0(j) && xin) sv = St::ld(Sc, (size_t)col.xrow(j, n) * a.nx);
-        q[j][n] = cfma_conj(q[j][n], sv, xr[j][n]);
+        csum_fma_conj(q[j][n], ql[j][n], sv, xr[j][n]);
       }
   }
 
@@ -734,7 +740,7 @@ __device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem&
     for (int n = 0; n < C::R0; ++n) {
       if (!(col.ok0(j) && xin)) continue;
       const size_t idx = (size_t)col.xrow(j, n) * a.nx + x;
-      float2 qv = cscale(q[j][n], invN);
+      float2 qv = cscale(csum_value(q[j][n], ql[j][n]), invN);
       if (CG) {
         qv = make_float2(fmaf(a.lambda, p[j][n].x, qv.x), fmaf(a.lambda, p[j][n].y, qv.y));
         if (a.lambda_t != 0.f) qv = cadd(qv, temporal_term(a, idx, p[j][n]));
@@ -785,7 +791,7 @@ __device__ __forceinline__ float normal_tile_tma(const NormalTile& a, const ColS
   const C col;
   const int x = a.tile * C::W + col.c;
   const bool xin = x < a.nx;
-  float2 p[C::J0][C::R0], q[C::J0][C::R0];
+  float2 p[C::J0][C::R0], q[C::J0][C::R0], ql[C::J0][C::R0];  // q: compensated coil sum
 #pragma unroll
   for (int j = 0; j < C::J0; ++j)
 #pragma unroll
@@ -802,6 +808,7 @@ __device__ __forceinline__ float normal_tile_tma(const NormalTile& a, const ColS
       }
       p[j][n] = v;
       q[j][n] = make_float2(0.f, 0.f);
+      ql[j][n] = make_float2(0.f, 0.f);
     }
 
   float2* bufs[2] = {s.buf0, s.buf1};
@@ -832,7 +839,7 @@ __device__ __forceinline__ float normal_tile_tma(const NormalTile& a, const ColS
 #pragma unroll
       for (int n = 0; n < C::R0; ++n) {
         const float2 sv = col.ok0(j) ? St::lds(sb, col.xrow(j, n) * C::W + col.c) : make_float2(0.f, 0.f);
-        q[j][n] = cfma_conj(q[j][n], sv, xr[j][n]);
+        csum_fma_conj(q[j][n], ql[j][n], sv, xr[j][n]);
       }
   }
 
@@ -844,7 +851,7 @@ __device__ __forceinline__ float normal_tile_tma(const NormalTile& a, const ColS
     for (int n = 0; n < C::R0; ++n) {
       if (!(col.ok0(j) && xin)) continue;
       const size_t idx = (size_t)col.xrow(j, n) * a.nx + x;
-      float2 qv = cscale(q[j][n], invN);
+      float2 qv = cscale(csum_value(q[j][n], ql[j][n]), invN);
       qv = make_float2(fmaf(a.lambda, p[j][n].x, qv.x), fmaf(a.lambda, p[j][n].y, qv.y));
       if (a.lambda_t != 0.f) qv = cadd(qv, temporal_term(a, idx, p[j][n]));
       __stcg(a.q + idx, qv);
@@ -1005,13 +1012,14 @@ __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSm
     s.buf0[cc * CP + row] = v;
   }
   __syncthreads();
-  float2 p[C::J0][C::R0], q[C::J0][C::R0];
+  float2 p[C::J0][C::R0], q[C::J0][C::R0], ql[C::J0][C::R0];  // q: compensated coil sum
 #pragma unroll
   for (int j = 0; j < C::J0; ++j)
 #pragma unroll
     for (int n = 0; n < C::R0; ++n) {
       p[j][n] = col.ok0(j) ? s.buf0[col.c * CP + col.xrow(j, n)] : make_float2(0.f, 0.f);
       q[j][n] = make_float2(0.f, 0.f);
+      ql[j][n] = make_float2(0.f, 0.f);
     }
 
   float2* bufs[2] = {s.buf0, s.buf1};
@@ -1045,7 +1053,7 @@ __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSm
 #pragma unroll
       for (int n = 0; n < C::R0; ++n) {
         const float2 sv = col.ok0(j) ? St::lds(sc, col.xrow(j, n)) : make_float2(0.f, 0.f);
-        q[j][n] = cfma_conj(q[j][n], sv, xr[j][n]);
+        csum_fma_conj(q[j][n], ql[j][n], sv, xr[j][n]);
       }
   }
 
@@ -1058,7 +1066,7 @@ __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSm
 #pragma unroll
     for (int n = 0; n < C::R0; ++n) {
       if (!col.ok0(j)) continue;
-      float2 qv = cscale(q[j][n], invN);
+      float2 qv = cscale(csum_value(q[j][n], ql[j][n]), invN);
       if (CG) {
         qv = make_float2(fmaf(a.lambda, p[j][n].x, qv.x), fmaf(a.lambda, p[j][n].y, qv.y));
         if (a.lambda_t != 0.f && xin) qv = cadd(qv, temporal_term(a, (size_t)col.xrow(j, n) * a.nx + x0 + col.c, p[j][n]));

@@ -49,10 +49,13 @@ def test_pass_kernels_use_no_local_memory(kernels, family):
 
 def test_headline_normal_kernels_use_no_local_memory(kernels):
     # every 256-point normal-operator kernel (all variants, both storages,
-    # persistent and per-launch): no local memory other than register spills,
-    # and spills of at most 32 bytes (the lane-major variant trades a few
-    # bytes of spill for keeping its stage-0 twiddles in registers)
+    # persistent and per-launch): no local memory beyond a small spill area
+    # (a stack frame at most one 16-byte slot larger than the spill stores)
+    # and spills of at most 64 bytes.  At two blocks of 256 threads per SM the
+    # register cap is 128; the lane-major variant keeps its stage-0 twiddles in
+    # registers and every variant carries the compensation words of its coil
+    # sums, which costs a few words of spill in some variants.
     sel = {**_select(kernels, "k_cg_persistentILi256"), **_select(kernels, "k_normalILi256")}
     assert len(sel) >= 8
-    bad = {n: v for n, v in sel.items() if v[1] > v[2] or v[2] > 32}
+    bad = {n: v for n, v in sel.items() if v[1] > v[2] + 16 or v[2] > 64}
     assert not bad, bad
