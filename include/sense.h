@@ -142,8 +142,10 @@ sense_status sense_adjoint(sense_plan* plan, const void* y, const void* S, const
  *   - Every call shares the one array and leaves its contents behind: calls
  *     that overlap on the GPU (different streams, or different host threads)
  *     race on it and must be serialised by the caller.
- *   - Line-index errors are skipped by the kernels but not reported (there is
- *     no plan to hold the flag); pass valid lines. */
+ *   - Line-index errors are skipped by the kernels but not reported, and
+ *     neither is a bounded wait of the row pass that gives up (never
+ *     expected; the block then stores nothing): there is no plan to hold the
+ *     device flag.  Pass valid lines. */
 sense_status sense_adjoint_noalloc(const sense_shape* shape, const void* y, const void* S, const int32_t* lines,
                                    sense_c32* x, void* stream);
 
@@ -170,6 +172,20 @@ sense_status sense_normal(sense_plan* plan, const sense_c32* x, const void* S, c
 sense_status sense_cg_solve(sense_plan* plan, const void* y, const void* S, const int32_t* lines, int max_iter,
                             double rel_tol, sense_c32* x_out, int32_t* iters_out, double* rel_resid_out,
                             int32_t* outcome_out, void* stream);
+
+/* CG-SENSE with every input and output in HOST memory: the same solve as
+ * sense_cg_solve (same stopping rules), for callers that do not manage device
+ * memory.  On `stream` the call copies y, S and lines to
+ * device buffers the plan owns (allocated on the first call and kept for the
+ * plan's life), runs the solve, copies x and the per-frame outputs back, and
+ * synchronises `stream` before returning; the return value then also reports
+ * errors the kernels flagged (as sense_plan_check does).  Page-locked host
+ * buffers make the copies asynchronous DMA transfers; pageable memory works
+ * but is staged by the driver.  iters_host, rel_resid_host and outcome_host
+ * may be NULL.  Layouts and storage types are those of sense_cg_solve. */
+sense_status sense_cg_solve_host(sense_plan* plan, const void* y_host, const void* S_host, const int32_t* lines_host,
+                                 int max_iter, double rel_tol, sense_c32* x_host, int32_t* iters_host,
+                                 double* rel_resid_host, int32_t* outcome_host, void* stream);
 
 /* ---- Uneven batching ----
  * A batch holds many independent CG-SENSE problems ("instances") of
@@ -342,6 +358,16 @@ sense_status sense_c32_to_bf16(const sense_c32* in, void* out, size_t count, voi
  * sums (the per-tile and per-chunk partitions differ). */
 sense_status sense_plan_set_cg_mode(sense_plan* plan, int mode);
 
+/* Column passes of E, E^H and root-sum-of-squares (the y-direction transforms
+ * with the maps, line mask and coil sum).  1 (default): persistent kernels
+ * that loop over (frame, 8-column tile) items and stage each coil's map tile
+ * and k-space tile in shared memory by TMA one coil ahead, for every length
+ * from 64 up whose 8-column tile fills whole warps (the other lengths use
+ * the per-tile kernels whatever the setting).  0: per-tile kernels, one
+ * block per (frame, column tile), tiles loaded through registers.  Both give
+ * the same results up to the rounding order of the coil sums. */
+sense_status sense_plan_set_column_pass(sense_plan* plan, int staged);
+
 /* Kernel variants.  Each transform length has one or more compiled variants
  * of the normal-operator kernel (threads per column, columns per block,
  * radix schedule, register cap).  A plan starts with variant 0.
@@ -426,6 +452,14 @@ sense_status sense_plan_phase_time(sense_plan* plan, int phase, double* ms_total
  * Returns SENSE_ETIMEOUT when the wait gave up as designed (the expected
  * outcome), anything else on failure.  The device stays usable. */
 sense_status sense_selftest_wait(int device, long max_spins);
+
+/* FP32 throughput of device `device`, measured (diagnostic; the paper has no
+ * counterpart): a launch covering every SM at full occupancy runs independent
+ * chains of fused multiply-adds, and the best of five timed launches gives
+ * *tflops_out = 2 x FMAs / time in TFLOP/s.  This is the measured peak that
+ * the transform-bound kernels' ALU roofline is stated against.  Synchronous;
+ * takes a few milliseconds; allocates 4 bytes per launched block. */
+sense_status sense_fp32_peak(int device, double* tflops_out);
 
 /* Message describing the last non-OK status returned on this thread. */
 const char* sense_last_error(void);

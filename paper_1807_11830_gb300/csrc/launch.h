@@ -2,6 +2,7 @@
 // length.  Each returns cudaErrorInvalidValue for a length without a
 // compiled configuration, else the launch status.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
@@ -39,6 +40,20 @@ cudaError_t launch_rows_fwd(int n, const RowArgs<float2, typename St::T>& a, cud
 // inverse row pass: storage St in, FP32 out
 template <class St>
 cudaError_t launch_rows_inv(int n, const RowArgs<typename St::T, float2>& a, cudaStream_t s);
+
+// TMA-staged persistent column passes (one wave of resident blocks looping
+// over (frame, column tile) items).  cudaErrorNotSupported when the length
+// has none or its tiles do not fit shared memory: the caller then uses the
+// register-staged kernels above.  tmK: the intermediate [F*C*L][nx] float2,
+// box 8 x kbox_rows(L); tmS: S [C*ny][nx] in storage type, box 8 x
+// min(ny, ny/2 when ny > 256).
+bool coltma_supported(int n);
+template <class St>
+cudaError_t launch_adj_col_tma(int n, int mode, const CUtensorMap& tmK, const CUtensorMap& tmS,
+                               const AdjColArgs<St>& a, int frames, int sms, cudaStream_t s);
+template <class St>
+cudaError_t launch_fwd_col_tma(int n, const CUtensorMap& tmS, const FwdColArgs<St>& a, int tiles, int frames,
+                               int sms, cudaStream_t s);
 
 // Set the dynamic shared memory limit of `kern` once per device.
 template <class K>

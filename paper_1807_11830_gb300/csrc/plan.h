@@ -23,6 +23,8 @@ struct sense_plan {
   int norm_variant = 0;  // kernel variant of the normal operator (autotuned)
   int norm_tiles = 0;    // column tiles per frame of that variant
   int cg_mode = 1;       // 0: per-phase kernels replayed as CUDA graphs; 1: one persistent launch
+  int col_tma = 1;       // 1: TMA-staged persistent column passes where the length has them; 0: per-tile kernels
+  int tiles8 = 0;        // 8-column tiles per frame (TMA column passes)
   double lambda = 0.0;   // Tikhonov weight of CG: (E^H E + lambda I) x = E^H y
   double lambda_t = 0.0; // temporal weight: > 0 couples the frames into one CG (persistent mode)
   cudaStream_t pool = nullptr;  // non-null: workspace is stream-ordered (cudaMallocAsync) on this stream
@@ -49,6 +51,13 @@ struct sense_plan {
   float2* pp[2] = {nullptr, nullptr};  // search directions, ping-pong between iterations
   float2* q = nullptr;
   void* maps_t = nullptr;  // S^T [C][nx][ny] for variants with lane-major tiles (allocated on first use)
+  // device copies of the host buffers of sense_cg_solve_host (allocated on its first call)
+  void* hio_y = nullptr;
+  void* hio_S = nullptr;
+  int* hio_lines = nullptr;
+  float2* hio_x = nullptr;
+  int* hio_ints = nullptr;      // iterations, outcomes ([2][F])
+  double* hio_resid = nullptr;  // [F]
 
   double* dbl = nullptr;  // rho, rho0, alpha, beta, resid  ([5][F])
   int* ints = nullptr;    // iters, outcome, active ([3][F]), live, err

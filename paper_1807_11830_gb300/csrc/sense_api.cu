@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "cg_kernels.cuh"
+#include "colpass.cuh"
 #include "launch.h"
 #include "plan.h"
 #include "trace.h"
@@ -47,6 +48,46 @@ sense_status fail(sense_status st, const std::string& msg) {
 
 bool aligned16(const void* p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 bool aligned4(const void* p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// Tensor map of `rows` rows of `cols` elements (4 or 8 bytes each, rows
+// contiguous) with a box of box_cols x box_rows elements; a pure host
+// computation (no device work), so it may run during stream capture.
+bool encode_rows_2d(CUtensorMap* m, const void* base, int elem_bytes, size_t cols, size_t rows, int box_cols,
+                    int box_rows) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * (cuuint64_t)elem_bytes};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 2,
+             const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Maps of the TMA column passes: S [coils * ny] rows of nx, box 8 x (ny or ny / 2).
+bool encode_maps_col(CUtensorMap* m, const sense_shape& sh, const void* S) {
+  return encode_rows_2d(m, S, sh.storage == SENSE_STORE_BF16 ? 4 : 8, (size_t)sh.nx, (size_t)sh.coils * sh.ny, 8,
+                        sh.ny <= 256 ? sh.ny : sh.ny / 2);
+}
 
 // exp(-2 pi i m / n), m = 0..n-1, in FP64 and rounded once to FP32.
 std::vector<float2> twiddles(int n) {
@@ -246,7 +287,12 @@ sense_status run_forward(sense_plan* pl, const float2* x, const void* S, const i
   sense_status rc;
   {
     PhaseScope ps(pl, SENSE_PHASE_FWD_COL, st);
-    rc = launch_status(launch_fwd_col<St>(sh.ny, a, pl->tiles, sh.frames, st), "forward column pass");
+    cudaError_t e = cudaErrorNotSupported;
+    CUtensorMap tmS;
+    if (pl->col_tma && coltma_supported(sh.ny) && encode_maps_col(&tmS, sh, S))
+      e = launch_fwd_col_tma<St>(sh.ny, tmS, a, pl->tiles8, sh.frames, pl->sms, st);
+    if (e == cudaErrorNotSupported) e = launch_fwd_col<St>(sh.ny, a, pl->tiles, sh.frames, st);
+    rc = launch_status(e, "forward column pass");
   }
   if (rc != SENSE_OK) return rc;
   RowArgs<float2, typename St::T> ra{};
@@ -282,6 +328,12 @@ sense_status run_adjoint(sense_plan* pl, int mode, const void* y, const void* S,
   const sense_shape& sh = pl->sh;
   sense_status rc = run_rows_inv<St>(pl, y, st);
   if (rc != SENSE_OK) return rc;
+  // TMA column passes: the intermediate [F*C*L][nx] as a tensor map (box 8 x rows per box)
+  CUtensorMap tmK, tmS;
+  const bool tma = pl->col_tma && coltma_supported(sh.ny) &&
+                   encode_rows_2d(&tmK, pl->tmp, 8, (size_t)sh.nx, (size_t)sh.frames * sh.coils * sh.lines, 8,
+                                  kbox_rows(sh.lines)) &&
+                   (mode == 2 ? encode_rows_2d(&tmS, pl->tmp, 8, (size_t)sh.nx, 1, 8, 1) : encode_maps_col(&tmS, sh, S));
   if (mode == 2) {
     AdjColArgs<StC64> a{};
     a.tmp = pl->tmp;
@@ -295,7 +347,14 @@ sense_status run_adjoint(sense_plan* pl, int mode, const void* y, const void* S,
     a.centred = sh.centred;
     a.err = pl->err();
     PhaseScope ps(pl, SENSE_PHASE_ADJ_COL, st);
-    return launch_status(launch_adj_col<StC64>(sh.ny, 2, a, pl->tiles, sh.frames, st), "rss column pass");
+    cudaError_t e = cudaErrorNotSupported;
+    if (tma) {
+      a.tiles = pl->tiles8;
+      e = launch_adj_col_tma<StC64>(sh.ny, 2, tmK, tmS, a, sh.frames, pl->sms, st);
+      a.tiles = pl->tiles;
+    }
+    if (e == cudaErrorNotSupported) e = launch_adj_col<StC64>(sh.ny, 2, a, pl->tiles, sh.frames, st);
+    return launch_status(e, "rss column pass");
   }
   AdjColArgs<St> a{};
   a.tmp = pl->tmp;
@@ -313,7 +372,14 @@ sense_status run_adjoint(sense_plan* pl, int mode, const void* y, const void* S,
   a.err = pl->err();
   a.cg = pl->cg(tol);
   PhaseScope ps(pl, SENSE_PHASE_ADJ_COL, st);
-  return launch_status(launch_adj_col<St>(sh.ny, mode, a, pl->tiles, sh.frames, st), "adjoint column pass");
+  cudaError_t e = cudaErrorNotSupported;
+  if (tma) {
+    a.tiles = pl->tiles8;
+    e = launch_adj_col_tma<St>(sh.ny, mode, tmK, tmS, a, sh.frames, pl->sms, st);
+    a.tiles = pl->tiles;
+  }
+  if (e == cudaErrorNotSupported) e = launch_adj_col<St>(sh.ny, mode, a, pl->tiles, sh.frames, st);
+  return launch_status(e, "adjoint column pass");
 }
 
 template <class St>
@@ -585,6 +651,7 @@ sense_status plan_allocate(sense_plan* pl) {
   const sense_shape& sh = pl->sh;
   const int W = col_width(sh.ny);
   pl->tiles = (sh.nx + W - 1) / W;
+  pl->tiles8 = (sh.nx + 7) / 8;
   pl->img = (size_t)sh.ny * sh.nx;
   pl->upd_blocks = (int)((pl->img + UPD_PER_BLOCK - 1) / UPD_PER_BLOCK);
   pl->norm_variant = 0;
@@ -675,27 +742,6 @@ sense_status plan_cg_start(sense_plan* pl, const void* y, const void* S, const i
 }
 
 std::vector<float2> plan_twiddles(int n) { return twiddles(n); }
-
-namespace {
-
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_tiled() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q{};
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  });
-  return fn;
-}
-
-}  // namespace
 
 sense_status plan_prepare_tmap(sense_plan* pl, const void* S, cudaStream_t st) {
   const sense_shape& sh = pl->sh;
@@ -889,6 +935,57 @@ sense_status sense_cg_solve(sense_plan* pl, const void* y, const void* S, const 
                                 as_stream(stream));
   return run_cg_solve<StC64>(pl, y, S, lines, max_iter, rel_tol, xf, iters_out, rel_resid_out, outcome_out,
                              as_stream(stream));
+}
+
+sense_status sense_cg_solve_host(sense_plan* pl, const void* y_host, const void* S_host, const int32_t* lines_host,
+                                 int max_iter, double rel_tol, sense_c32* x_host, int32_t* iters_host,
+                                 double* rel_resid_host, int32_t* outcome_host, void* stream) {
+  sense::TraceRange trace_range("sense_cg_solve_host");
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (!y_host || !S_host || !lines_host || !x_host) return fail(SENSE_EINVAL, "y, S, lines and x must be non-NULL");
+  if (max_iter < 0 || !(rel_tol >= 0.0)) return fail(SENSE_EINVAL, "max_iter must be >= 0 and rel_tol >= 0");
+  DeviceGuard guard(pl->device);
+  const sense_shape& sh = pl->sh;
+  const size_t sb = sh.storage == SENSE_STORE_BF16 ? 4 : 8;
+  const size_t F = (size_t)sh.frames;
+  const size_t y_bytes = F * sh.coils * sh.lines * sh.nx * sb, S_bytes = (size_t)sh.coils * pl->img * sb;
+  const size_t l_bytes = F * sh.lines * sizeof(int32_t), x_bytes = F * pl->img * sizeof(float2);
+  sense_status rc = SENSE_OK;
+  if (!pl->hio_y) {  // first call: device copies of the caller's buffers, owned by the plan
+    unsigned char* yb = nullptr;
+    unsigned char* sbuf = nullptr;
+    if ((rc = dalloc(pl, &yb, y_bytes)) != SENSE_OK || (rc = dalloc(pl, &sbuf, S_bytes)) != SENSE_OK ||
+        (rc = dalloc(pl, &pl->hio_lines, F * sh.lines)) != SENSE_OK || (rc = dalloc(pl, &pl->hio_x, F * pl->img)) != SENSE_OK ||
+        (rc = dalloc(pl, &pl->hio_ints, 2 * F)) != SENSE_OK || (rc = dalloc(pl, &pl->hio_resid, F)) != SENSE_OK)
+      return rc;
+    pl->hio_y = yb;
+    pl->hio_S = sbuf;
+  }
+  cudaStream_t st = as_stream(stream);
+  SENSE_CUDA_TRY(cudaMemcpyAsync(pl->hio_y, y_host, y_bytes, cudaMemcpyHostToDevice, st));
+  SENSE_CUDA_TRY(cudaMemcpyAsync(pl->hio_S, S_host, S_bytes, cudaMemcpyHostToDevice, st));
+  SENSE_CUDA_TRY(cudaMemcpyAsync(pl->hio_lines, lines_host, l_bytes, cudaMemcpyHostToDevice, st));
+  rc = sh.storage == SENSE_STORE_BF16
+           ? run_cg_solve<StBF16>(pl, pl->hio_y, pl->hio_S, pl->hio_lines, max_iter, rel_tol, pl->hio_x, pl->hio_ints,
+                                  pl->hio_resid, pl->hio_ints + F, st)
+           : run_cg_solve<StC64>(pl, pl->hio_y, pl->hio_S, pl->hio_lines, max_iter, rel_tol, pl->hio_x, pl->hio_ints,
+                                 pl->hio_resid, pl->hio_ints + F, st);
+  if (rc != SENSE_OK) return rc;
+  SENSE_CUDA_TRY(cudaMemcpyAsync(x_host, pl->hio_x, x_bytes, cudaMemcpyDeviceToHost, st));
+  if (iters_host)
+    SENSE_CUDA_TRY(cudaMemcpyAsync(iters_host, pl->hio_ints, F * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (outcome_host)
+    SENSE_CUDA_TRY(cudaMemcpyAsync(outcome_host, pl->hio_ints + F, F * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (rel_resid_host)
+    SENSE_CUDA_TRY(cudaMemcpyAsync(rel_resid_host, pl->hio_resid, F * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return sense_plan_check(pl, stream);  // synchronises `stream`; reports flags the kernels raised
+}
+
+sense_status sense_plan_set_column_pass(sense_plan* pl, int staged) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (staged != 0 && staged != 1) return fail(SENSE_EINVAL, "staged must be 0 or 1");
+  pl->col_tma = staged;
+  return SENSE_OK;
 }
 
 sense_status sense_rss(sense_plan* pl, const void* y, const int32_t* lines, float* out, void* stream) {

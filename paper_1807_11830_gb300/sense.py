@@ -31,10 +31,11 @@ CG_CONVERGED, CG_MAXITER, CG_BREAKDOWN = 1, 2, 3
 
 EXPORTED = (
     "sense_size_supported", "sense_plan_create", "sense_plan_destroy", "sense_plan_workspace_bytes",
-    "sense_forward", "sense_adjoint", "sense_normal", "sense_cg_solve", "sense_rss", "sense_c32_to_bf16",
+    "sense_forward", "sense_adjoint", "sense_normal", "sense_cg_solve", "sense_cg_solve_host", "sense_rss",
+    "sense_c32_to_bf16",
     "sense_plan_check", "sense_last_error", "sense_plan_set_timing", "sense_plan_phase_time",
     "sense_adjoint_noalloc", "sense_plan_set_variant", "sense_plan_variant", "sense_plan_autotune",
-    "sense_plan_set_cg_mode", "sense_selftest_wait", "sense_plan_set_lambda", "sense_batch_set_lambda",
+    "sense_plan_set_cg_mode", "sense_selftest_wait", "sense_fp32_peak", "sense_plan_set_column_pass", "sense_plan_set_lambda", "sense_batch_set_lambda",
     "sense_plan_set_temporal", "sense_batch_set_temporal",
     "sense_batch_create", "sense_batch_destroy", "sense_batch_workspace_bytes", "sense_batch_classes",
     "sense_batch_autotune", "sense_batch_set_variant", "sense_batch_cg_solve", "sense_batch_check",
@@ -117,6 +118,8 @@ def load_library(path=LIB_PATH):
         getattr(lib, name).restype = st
     lib.sense_cg_solve.argtypes = [vp, vp, vp, vp, i, ctypes.c_double, vp, vp, vp, vp, vp]
     lib.sense_cg_solve.restype = st
+    lib.sense_cg_solve_host.argtypes = [vp, vp, vp, vp, i, ctypes.c_double, vp, vp, vp, vp, vp]
+    lib.sense_cg_solve_host.restype = st
     lib.sense_rss.argtypes = [vp, vp, vp, vp, vp]
     lib.sense_rss.restype = st
     lib.sense_c32_to_bf16.argtypes = [vp, vp, ctypes.c_size_t, vp]
@@ -143,10 +146,14 @@ def load_library(path=LIB_PATH):
     lib.sense_batch_set_temporal.restype = st
     lib.sense_plan_autotune.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), vp]
     lib.sense_plan_autotune.restype = st
+    lib.sense_plan_set_column_pass.argtypes = [vp, i]
+    lib.sense_plan_set_column_pass.restype = st
     lib.sense_plan_set_cg_mode.argtypes = [vp, i]
     lib.sense_plan_set_cg_mode.restype = st
     lib.sense_selftest_wait.argtypes = [i, ctypes.c_long]
     lib.sense_selftest_wait.restype = st
+    lib.sense_fp32_peak.argtypes = [i, ctypes.POINTER(ctypes.c_double)]
+    lib.sense_fp32_peak.restype = st
     bp = ctypes.POINTER(_BatchIO)
     lib.sense_batch_create.argtypes = [ctypes.POINTER(_Shape), i, i, ctypes.POINTER(vp)]
     lib.sense_batch_create.restype = st
@@ -282,6 +289,24 @@ def sense_cg_solve(plan, y, S, lines, max_iter, rel_tol, x_out, iters_out=None, 
     return x_out
 
 
+def _host_ptr(t):
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous host tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def sense_cg_solve_host(plan, y, S, lines, max_iter, rel_tol, x_out, iters_out=None, rel_resid_out=None,
+                        outcome_out=None, stream=None):
+    """CG-SENSE on host tensors (pinned for asynchronous copies); returns once
+    the results are in `x_out` (and the optional per-frame outputs)."""
+    _check(load_library().sense_cg_solve_host(plan.handle, _host_ptr(y), _host_ptr(S), _host_ptr(lines),
+                                              int(max_iter), float(rel_tol), _host_ptr(x_out),
+                                              _host_ptr(iters_out), _host_ptr(rel_resid_out),
+                                              _host_ptr(outcome_out), _stream(stream)))
+
+
 def sense_rss(plan, y, lines, out, stream=None):
     _check(load_library().sense_rss(plan.handle, _ptr(y), _ptr(lines), _ptr(out), _stream(stream)))
     return out
@@ -332,6 +357,10 @@ def sense_plan_set_cg_mode(plan, mode):
     _check(load_library().sense_plan_set_cg_mode(plan.handle, int(mode)))
 
 
+def sense_plan_set_column_pass(plan, staged):
+    _check(load_library().sense_plan_set_column_pass(plan.handle, int(staged)))
+
+
 def sense_plan_set_variant(plan, variant):
     _check(load_library().sense_plan_set_variant(plan.handle, int(variant)))
 
@@ -352,6 +381,13 @@ def sense_plan_autotune(plan, S, lines, stream=None):
 def sense_selftest_wait(device=0, max_spins=1000):
     """Returns the status of the bounded-wait self-test (5 = SENSE_ETIMEOUT expected)."""
     return load_library().sense_selftest_wait(int(device), int(max_spins))
+
+
+def sense_fp32_peak(device=0):
+    """Measured FP32 FMA throughput of the device, TFLOP/s."""
+    out = ctypes.c_double()
+    _check(load_library().sense_fp32_peak(int(device), ctypes.byref(out)))
+    return out.value
 
 
 def to_bf16_pairs(t, stream=None):

@@ -367,3 +367,29 @@ def test_cg_persistent_every_length(n):
     xg, ig, _, sg = gpu_cg(y, S, lines, K, plan=plan)
     assert rel(xg, xo) <= CG_TOL
     np.testing.assert_array_equal(ig, io)
+
+
+@pytest.mark.parametrize("storage", [sense.STORE_C64, sense.STORE_BF16])
+def test_cg_solve_host_equals_device_call(storage):
+    """sense_cg_solve_host (host buffers in and out) gives the device call's
+    bits: the same kernels on the same data; two calls in a row reuse the
+    plan's device copies."""
+    from tests.gpu_util import storage_tensor
+
+    ny, nx, C, L, F = 192, 128, 5, 48, 3
+    x, S, lines, y = _problem((ny, nx, C, L, F), seed=4242 + storage)
+    plan = make_plan(S, lines, storage)
+    xd, itd, rrd, ocd = gpu_cg(y, S, lines, 12, plan=plan, storage=storage)
+    y_t = storage_tensor(y, storage).cpu().pin_memory()
+    S_t = storage_tensor(S, storage).cpu().pin_memory()
+    l_t = torch.from_numpy(np.ascontiguousarray(lines, np.int32)).pin_memory()
+    for _ in range(2):
+        xh = torch.empty((F, ny, nx), dtype=torch.complex64).pin_memory()
+        ith = torch.zeros(F, dtype=torch.int32)
+        rrh = torch.zeros(F, dtype=torch.float64)
+        och = torch.zeros(F, dtype=torch.int32)
+        sense.sense_cg_solve_host(plan, y_t, S_t, l_t, 12, 0.0, xh, ith, rrh, och)
+        np.testing.assert_array_equal(xh.numpy().astype(np.complex128), xd)
+        np.testing.assert_array_equal(ith.numpy(), itd)
+        np.testing.assert_array_equal(rrh.numpy(), rrd)
+        np.testing.assert_array_equal(och.numpy(), ocd)
