@@ -34,8 +34,39 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-FRAMES, COILS, N, ACCEL, CENTRE, ITERS = 20, 12, 256, 4, 16, 30
-WORKLOAD = "cine 256x256, 20 frames, 12 coils, R=4 (64 lines, 16 centre), 30 CG-SENSE iterations"
+class Workload:
+    """A CG-SENSE workload: n x n images, `frames` sharing `coils` maps,
+    acceleration `accel` with `centre` fully sampled centre lines, `iters` CG
+    iterations per frame; `make` draws its seeded inputs (synth)."""
+
+    def __init__(self, name, n, frames, coils, accel, centre, iters, make, desc):
+        self.name, self.n, self.frames, self.coils = name, n, frames, coils
+        self.accel, self.centre, self.iters, self.make, self.desc = accel, centre, iters, make, desc
+        self.lines = int(round(n / accel))
+
+
+def _cine(frames):
+    from paper_1807_11830_gb300 import synth
+    return synth.cine_256(frames=frames)
+
+
+def _slices(frames):
+    from paper_1807_11830_gb300 import synth
+    return synth.slices_320(frames=frames)
+
+
+WORKLOADS = {
+    "cine": Workload("cine", 256, 20, 12, 4, 16, 30, _cine,
+                     "cine 256x256, 20 frames, 12 coils, R=4 (64 lines, 16 centre), 30 CG-SENSE iterations"),
+    "slices320": Workload("slices320", 320, 16, 32, 3, 24, 50, _slices,
+                          "slices 320x320, 16 slices, 32 coils, R=3 (107 lines, 24 centre), "
+                          "50 CG-SENSE iterations"),
+}
+CINE = WORKLOADS["cine"]
+FRAMES, COILS, N, ACCEL, CENTRE, ITERS = CINE.frames, CINE.coils, CINE.n, CINE.accel, CINE.centre, CINE.iters
+WORKLOAD = CINE.desc
+STORAGE_NAMES = {"c64": "complex64", "bf16": "bfloat16 pairs (S and y); FP32 transforms, coil sums and CG "
+                                              "vectors; FP64 CG inner products"}
 METRIC = "E^H·E applications/s"
 UNIT = "applications/s"
 FLUSH_BYTES = 512 << 20
@@ -44,7 +75,7 @@ FLUSH_BYTES = 512 << 20
 # persistent kernel (40.4 MB read + 173.2 MB written over 30 iterations)
 CINE_TRAFFIC_PER_ITER = {(1, "persistent"): (40.359936e6 + 173.227776e6) / 30}
 PAPER_WORKLOAD = ("paper reconstruction: 16 frames x 160x160, 8 coils, fully sampled; "
-                  "2D inverse FFT + root-sum-of-squares (Sec. V)")
+                  "2D inverse FFT + root-sum-of-squares (Sec. IV-B)")
 PAPER_METRIC, PAPER_UNIT = "reconstructions/s", "reconstructions/s"
 # OpenCLIPER's own time for this workload on a GTX 970 (Table II: clFFT 1.361 ms + RSS 0.252 ms): context
 PAPER_GTX970_MS = 1.361 + 0.252
@@ -61,10 +92,16 @@ def parse_args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=20)
-    ap.add_argument("--workload", default="cine", choices=("cine", "mix", "serve", "paper"),
-                    help="cine: the headline line; mix: 512-instance uneven batch vs the plain loop; "
+    ap.add_argument("--workload", default="cine", choices=("cine", "slices320", "mix", "serve", "paper"),
+                    help="cine: the headline line; slices320: the 320x320, 32-coil, 50-iteration precision-study "
+                         "shape; mix: 512-instance uneven batch vs the plain loop; "
                          "serve: Poisson request streams through the serving queue vs serial plain solves; "
                          "paper: the paper's timed FFT + RSS reconstruction (and the Eq. 1 combine)")
+    ap.add_argument("--storage", default="c64", choices=("c64", "bf16"),
+                    help="storage of S and y for the cine and slices320 workloads")
+    ap.add_argument("--accuracy-iters", type=int, default=0,
+                    help="CG iterations of the accuracy sample against the FP64 oracle (0: the workload's own "
+                         "count for cine, 4 for slices320)")
     ap.add_argument("--mix-count", type=int, default=512)
     ap.add_argument("--serve-rates", default="50,200,800")
     ap.add_argument("--serve-requests", type=int, default=160)
@@ -120,10 +157,12 @@ def shard_instances(specs, world, rank):
     return [i for i in range(len(specs)) if owner[i] == rank]
 
 
-def base_config(world, centred=False):
+def base_config(world, centred=False, wl=CINE, storage="c64"):
     return {
-        "workload": WORKLOAD + (", centred k-space" if centred else ""), "ny": N, "nx": N, "frames": FRAMES,
-        "coils": COILS, "lines": N // ACCEL, "centre_lines": CENTRE, "cg_iterations": ITERS, "storage": "complex64",
+        "workload": wl.desc + (", centred k-space" if centred else "") + (", BF16 storage" if storage == "bf16" else ""),
+        "ny": wl.n, "nx": wl.n, "frames": wl.frames,
+        "coils": wl.coils, "lines": wl.lines, "centre_lines": wl.centre, "cg_iterations": wl.iters,
+        "storage": STORAGE_NAMES[storage],
         "kspace": "centred (DC at n/2)" if centred else "uncentred (DC at 0)",
         "l2": "flushed before every timed step (512 MiB device write)",
         "parallelism": "replicas x%d (independent problems, no collective)" % world,
@@ -136,32 +175,36 @@ def base_config(world, centred=False):
 _ORACLE_INPUTS = {}
 
 
-def oracle_inputs(centred=False):
+def oracle_inputs(centred=False, wl=CINE):
     """k-space of the whole workload made once by the oracle's E (untimed)."""
-    if not _ORACLE_INPUTS:
+    key = (wl.name, centred)
+    if key not in _ORACLE_INPUTS:
         import oracle
         from paper_1807_11830_gb300 import synth
 
-        p = synth.cine_256(frames=FRAMES)
-        lines = synth.centred_lines(p.lines, N) if centred else p.lines
+        p = wl.make(wl.frames)
+        lines = synth.centred_lines(p.lines, wl.n) if centred else p.lines
         S = p.S.astype(np.complex64).astype(np.complex128)
         y = oracle.forward(p.x_true.astype(np.complex64), S, lines, centred=centred) + p.noise
-        _ORACLE_INPUTS.update(y=y, S=S, lines=lines, centred=centred)
-    return _ORACLE_INPUTS
+        _ORACLE_INPUTS[key] = dict(y=y, S=S, lines=lines, centred=centred)
+    return _ORACLE_INPUTS[key]
 
 
-def oracle_sample(frames, iters, seed_offset=0, centred=False, lam=0.0, lam_t=0.0):
+def oracle_sample(frames, iters, seed_offset=0, centred=False, lam=0.0, lam_t=0.0, wl=CINE, y=None, S=None):
     """Time oracle CG-SENSE on `frames` frames of the workload for `iters`
-    iterations.  Returns (applications/s, wall seconds, threads)."""
+    iterations (on the given k-space and maps if passed, e.g. BF16-rounded
+    ones).  Returns (applications/s, wall seconds, threads, images, frame indices)."""
     import oracle
 
-    d = oracle_inputs(centred)
-    sel = [(i + seed_offset) % FRAMES for i in range(frames)]
-    y, S, lines = d["y"][sel], d["S"], d["lines"][sel]
+    d = oracle_inputs(centred, wl)
+    sel = [(i + seed_offset) % wl.frames for i in range(frames)]
+    yy = (d["y"] if y is None else y)[sel]
+    SS = d["S"] if S is None else S
+    lines = d["lines"][sel]
     t0 = time.perf_counter()
-    oracle.cg(y, S, lines, iters, centred=d["centred"], lam=lam, lam_t=lam_t)
+    x = oracle.cg(yy, SS, lines, iters, centred=d["centred"], lam=lam, lam_t=lam_t)[0]
     wall = time.perf_counter() - t0
-    return frames * iters / wall, wall, min(oracle.threads(), frames)
+    return frames * iters / wall, wall, min(oracle.threads(), frames), x, sel
 
 
 def run_reference(args):
@@ -172,25 +215,27 @@ def run_reference(args):
         return run_reference_paper(args)
     import oracle
 
+    wl = WORKLOADS.get(args.workload, CINE)
     threads = oracle.threads()
-    frames = max(1, min(FRAMES, threads))
-    iters = 2
+    frames = max(1, min(wl.frames, threads))
+    iters = 2 if wl.n <= 256 else 1
     for _ in range(args.warmup):
-        oracle_sample(frames, 1, centred=args.centred)
+        oracle_sample(frames, 1, centred=args.centred, wl=wl)
     walls = []
     apps = 0
     for k in range(args.steps):
-        _, wall, _ = oracle_sample(frames, iters, seed_offset=k, centred=args.centred)
+        _, wall, _, _, _ = oracle_sample(frames, iters, seed_offset=k, centred=args.centred, wl=wl)
         walls.append(wall)
         apps += frames * iters
     total = sum(walls)
     value = apps / total
-    sample = "%d of %d frames x %d CG iterations per step (full 256x256, 12 coils, R=4)" % (frames, FRAMES, iters)
+    sample = "%d of %d frames x %d CG iterations per step (full %dx%d, %d coils, R=%d)" % (
+        frames, wl.frames, iters, wl.n, wl.n, wl.coils, wl.accel)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": base_config(1, args.centred),
+        "config": base_config(1, args.centred, wl, args.storage),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(threads, frames), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -275,12 +320,66 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
-def time_operators(plan, x_img, y, S, lines, flush, stream, dev, reps=20):
+def cg_accuracy(plan, y, S, lines, x_ref, sel, iters, wl, args, requant_sample):
+    """Relative L2 error of this plan's CG images (frames `sel`, `iters`
+    iterations) against the FP64 oracle's on the same k-space and maps.  For
+    BF16 storage the oracle also runs on the BF16-rounded inputs, which
+    separates the storage error from the arithmetic error."""
+    import torch
+
+    import oracle
+    from paper_1807_11830_gb300 import sense
+
+    F, ny, nx = wl.frames, wl.n, wl.n
+    x = torch.empty((F, ny, nx), dtype=torch.complex64, device=y.device)
+    it = torch.zeros(F, dtype=torch.int32, device=y.device)
+    sense.sense_cg_solve(plan, y, S, lines, iters, 0.0, x, it)
+    sense.sense_plan_check(plan)
+    xg = x.cpu().numpy()[sel].astype(np.complex128)
+
+    def rel(a, b):
+        return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+    out = {"cg_iterations": iters, "frames": len(sel), "metric": "relative L2 over the sampled frames",
+           "vs_fp64_oracle": rel(xg, x_ref)}
+    if requant_sample is not None:
+        d = oracle_inputs(args.centred, wl)
+        _, _, _, x_q, _ = requant_sample(len(sel), iters, centred=args.centred, lam=args.lam, lam_t=args.lam_t,
+                                         wl=wl, y=oracle.quantize_c64_bf16(d["y"]),
+                                         S=oracle.quantize_c64_bf16(d["S"]))
+        out["vs_fp64_oracle_on_bf16_inputs"] = rel(xg, x_q)
+        out["note"] = ("vs_fp64_oracle: storage + arithmetic error (exact inputs); "
+                       "vs_fp64_oracle_on_bf16_inputs: arithmetic error alone")
+    return out
+
+
+_FP32_PEAK = {}
+
+
+def fp32_peak(device, sm_max_mhz):
+    """(TFLOP/s, source) of the FP32 ALU roofline: the library's FMA-chain
+    microbenchmark on this GPU (measured once per process)."""
+    from paper_1807_11830_gb300 import sense
+
+    if device not in _FP32_PEAK:
+        try:
+            _FP32_PEAK[device] = (sense.sense_fp32_peak(device),
+                                  "measured: sense_fp32_peak FMA-chain microbenchmark on this GPU")
+        except Exception as exc:  # report the derived figure and say so
+            _FP32_PEAK[device] = (152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12,
+                                  "derived (measurement failed: %s): 152 SMs x 128 lanes x 2 flop x %.0f MHz"
+                                  % (exc, sm_max_mhz))
+    return _FP32_PEAK[device]
+
+
+def time_operators(plan, x_img, y, S, lines, flush, stream, dev, sbytes=8, reps=20, only=None):
     """E (sense_forward), E^H (sense_adjoint) and E^H E (sense_normal) on the
-    cine configuration, each call timed alone with CUDA events on `stream`
-    after 3 warm-up calls, L2 flushed before each.  Applications = frames.
-    Algorithmic bytes per call: the operator's inputs and outputs once (S
-    once for all frames); the two-pass intermediate is not counted."""
+    workload's configuration, each call timed alone with CUDA events on
+    `stream` after 3 warm-up calls, L2 flushed before each.  Applications =
+    frames.  Algorithmic bytes per call: the operator's inputs and outputs once
+    (S once for all frames; `sbytes` per stored complex value of S and y); the
+    two-pass intermediate is not counted.  `hbm_frac_s_per_frame` counts S
+    once per frame instead (the per-frame minimum of the forward operator)."""
     import torch
 
     from paper_1807_11830_gb300 import sense
@@ -292,15 +391,17 @@ def time_operators(plan, x_img, y, S, lines, flush, stream, dev, reps=20):
     x_out = torch.empty_like(x_img)
     calls = {
         "forward": (lambda: sense.sense_forward(plan, x_img, S, lines, y_out, stream=stream),
-                    8 * (F * img + C * img + F * C * L * nx)),
+                    8 * F * img + sbytes * (C * img + F * C * L * nx), sbytes * (F - 1) * C * img),
         "adjoint": (lambda: sense.sense_adjoint(plan, y, S, lines, x_out, stream=stream),
-                    8 * (F * C * L * nx + C * img + F * img)),
+                    sbytes * (F * C * L * nx + C * img) + 8 * F * img, sbytes * (F - 1) * C * img),
         "normal": (lambda: sense.sense_normal(plan, x_img, S, lines, x_out, stream=stream),
-                   8 * (C * img + 2 * F * img)),
+                   sbytes * C * img + 16 * F * img, sbytes * (F - 1) * C * img),
     }
     hbm_gbs, _, _ = peaks()
     out = {}
-    for name, (call, nbytes) in calls.items():
+    for name, (call, nbytes, s_extra) in calls.items():
+        if only and name not in only:
+            continue
         for _ in range(3):
             call()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
@@ -314,7 +415,8 @@ def time_operators(plan, x_img, y, S, lines, flush, stream, dev, reps=20):
         ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / reps
         gbs = nbytes / (ms / 1e3) / 1e9
         out[name] = {"applications_per_s": F / (ms / 1e3), "ms": ms, "algorithmic_mb": nbytes / 1e6,
-                     "achieved_gbs": gbs, "hbm_frac": gbs / hbm_gbs}
+                     "achieved_gbs": gbs, "hbm_frac": gbs / hbm_gbs,
+                     "hbm_frac_s_per_frame": (nbytes + s_extra) / (ms / 1e3) / 1e9 / hbm_gbs}
     return out
 
 
@@ -334,21 +436,33 @@ def run_ours(args):
         sense_build.build()
     sense.load_library()
 
+    wl = WORKLOADS[args.workload]
+    FRAMES, COILS, N, ITERS = wl.frames, wl.coils, wl.n, wl.iters
+    bf16 = args.storage == "bf16"
+    store = sense.STORE_BF16 if bf16 else sense.STORE_C64
+    sbytes = 4 if bf16 else 8  # bytes per stored complex value of S and y
+
     # ---- inputs (seeded; k-space made on the device by the library's E) ----
-    p = synth.cine_256(frames=FRAMES)
+    p = wl.make(FRAMES)
     L = p.lines.shape[1]
     x_true = torch.from_numpy(p.x_true.astype(np.complex64)).to(dev)
     S = torch.from_numpy(p.S.astype(np.complex64)).to(dev)
     lines_np = synth.centred_lines(p.lines, N) if args.centred else p.lines
     lines = torch.from_numpy(lines_np).to(dev)
-    plan = sense.Plan(N, N, COILS, FRAMES, L, device=local_rank, centred=args.centred)
+    y = torch.empty((FRAMES, COILS, L, N), dtype=torch.complex64, device=dev)
+    mk = sense.Plan(N, N, COILS, FRAMES, L, device=local_rank, centred=args.centred)
+    sense.sense_forward(mk, x_true, S, lines, y)
+    y += torch.from_numpy(p.noise.astype(np.complex64)).to(dev)
+    torch.cuda.synchronize(dev)
+    mk.close()
+    if bf16:  # S and y stored as bfloat16 pairs, rounded by the library's RNE conversion
+        S, y = sense.to_bf16_pairs(S), sense.to_bf16_pairs(y)
+        torch.cuda.synchronize(dev)
+    plan = sense.Plan(N, N, COILS, FRAMES, L, store, device=local_rank, centred=args.centred)
     if args.lam:
         sense.sense_plan_set_lambda(plan, args.lam)
     if args.lam_t:
         sense.sense_plan_set_temporal(plan, args.lam_t)
-    y = torch.empty((FRAMES, COILS, L, N), dtype=torch.complex64, device=dev)
-    sense.sense_forward(plan, x_true, S, lines, y)
-    y += torch.from_numpy(p.noise.astype(np.complex64)).to(dev)
     if args.normal_variant == "auto":
         variant, tune_ms = sense.sense_plan_autotune(plan, S, lines)
     else:
@@ -418,21 +532,16 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
 
-    # ---- end to end: pinned host inputs in, image out, inside the timed region ----
+    # ---- end to end through the host-buffer C-ABI call: pinned host inputs in, image out ----
+    # (sense_cg_solve_host copies y, S and lines to the device, solves, copies x back and
+    # synchronises the stream, all inside the timed region)
     y_h = y.cpu().pin_memory()
     S_h = S.cpu().pin_memory()
     lines_h = lines.cpu().pin_memory()
     x_h = torch.empty(x.shape, dtype=x.dtype).pin_memory()
-    y_d = torch.empty_like(y)
-    S_d = torch.empty_like(S)
-    lines_d = torch.empty_like(lines)
 
     def e2e_step():
-        y_d.copy_(y_h, non_blocking=True)
-        S_d.copy_(S_h, non_blocking=True)
-        lines_d.copy_(lines_h, non_blocking=True)
-        sense.sense_cg_solve(plan, y_d, S_d, lines_d, ITERS, 0.0, x, iters, stream=stream)
-        x_h.copy_(x, non_blocking=True)
+        sense.sense_cg_solve_host(plan, y_h, S_h, lines_h, ITERS, 0.0, x_h, stream=stream)
 
     for _ in range(3):
         e2e_step()
@@ -447,8 +556,8 @@ def run_ours(args):
     barrier()
     clocks.stop()
     e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends))
-    h2d = y.numel() * 8 + S.numel() * 8 + lines.numel() * 4
-    d2h = x.numel() * 8
+    h2d = sum(t.numel() * t.element_size() for t in (y, S, lines))
+    d2h = x.numel() * x.element_size()
 
     # ---- kernel roofline: the same step with the plan's event timers on ----
     timed_steps = 5
@@ -465,7 +574,12 @@ def run_ours(args):
     sense.sense_plan_set_timing(plan, False)
 
     # ---- the operators on their own (steps A, B, C outside CG), same plan and inputs ----
-    operators = time_operators(plan, x_true, y, S, lines, flush, stream, dev) if rank == 0 else None
+    operators = time_operators(plan, x_true, y, S, lines, flush, stream, dev, sbytes) if rank == 0 else None
+    if operators is not None:  # the same calls with the per-tile column kernels, for comparison
+        sense.sense_plan_set_column_pass(plan, 0)
+        reg = time_operators(plan, x_true, y, S, lines, flush, stream, dev, sbytes, only=("forward", "adjoint"))
+        sense.sense_plan_set_column_pass(plan, 1)
+        operators["per_tile_column_kernels"] = {k: {"ms": v["ms"], "hbm_frac": v["hbm_frac"]} for k, v in reg.items()}
 
     # max over ranks
     total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], world, dev)
@@ -477,9 +591,11 @@ def run_ours(args):
     if rank == 0:
         hbm_gbs, sm_max_mhz, peak_src = peaks()
         img = N * N
-        # dominant kernel: E^H E inside CG.  Algorithmic work per launch (all 20 frames):
+        # dominant kernel: the CG iteration.  Algorithmic work per CG iteration (all 20 frames):
         #   flops = C * F * (2 * Nx * 5 Ny log2 Ny + 14 Ny Nx)   (5 n log2 n per length-n transform)
-        #   bytes = 8 * img * (C + 4 F)   (S once; r, p read; p, q written per frame)
+        #   bytes = 8 * img * (C + 10 F): S once for the plan's frames; per frame the normal
+        #           product with its p-update prologue moves 4 image vectors (r, p_prev read;
+        #           p, q written) and the fused x/r update 6 (x, p, q, r read; x, r written)
         cgn = phase.get("cg_normal", {})
         dur_s = cgn.get("ms_per_launch", float("nan")) / 1e3
         kernel_name = "k_normal (CG mode)"
@@ -487,45 +603,58 @@ def run_ours(args):
             # one launch runs every iteration: normal products and updates, all frames
             pers = phase.get("cg_persistent", {})
             dur_s = pers.get("ms_per_launch", float("nan")) / 1e3 / ITERS
-            kernel_name = "k_cg_persistent (per CG iteration: normal product + update, 20 frames)"
+            kernel_name = "k_cg_persistent (per CG iteration: normal product + update, %d frames)" % FRAMES
         flops = COILS * FRAMES * (2 * N * 5 * N * np.log2(N) + 14 * img)
-        bytes_ = 8 * img * (COILS + 4 * FRAMES)
-        alu_peak_tflops = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+        bytes_ = img * (sbytes * COILS + 80 * FRAMES)
+        bytes_s_per_frame = img * FRAMES * (sbytes * COILS + 80)
+        alu_peak_tflops, alu_peak_src = fp32_peak(local_rank, sm_max_mhz)
         achieved_tflops = flops / dur_s / 1e12
         # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu
         # capture of this launch configuration, per CG iteration; null for any
         # other configuration
-        traffic = CINE_TRAFFIC_PER_ITER.get((variant, cg_mode))
+        traffic = CINE_TRAFFIC_PER_ITER.get((variant, cg_mode)) if (wl is CINE and not bf16) else None
         roofline = {
             "kernel": kernel_name, "bound": "alu", "achieved": achieved_tflops, "peak": alu_peak_tflops,
             "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak_tflops, "traffic": traffic,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max)" % (sm_max_mhz, peak_src),
+            "peak_source": alu_peak_src,
             "algorithmic_gflop_per_launch": flops / 1e9, "algorithmic_mb_per_launch": bytes_ / 1e6,
             "hbm_achieved_gbs": bytes_ / dur_s / 1e9, "hbm_peak_gbs": hbm_gbs,
-            "hbm_frac": bytes_ / dur_s / 1e9 / hbm_gbs, "duration_us": dur_s * 1e6,
+            "hbm_frac": bytes_ / dur_s / 1e9 / hbm_gbs,
+            "hbm_frac_s_per_frame": bytes_s_per_frame / dur_s / 1e9 / hbm_gbs,
+            "hbm_peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % peak_src,
+            "duration_us": dur_s * 1e6,
         }
         cpu = None
+        accuracy = None
         if world == 1 and not args.no_cpu_baseline:
             import oracle
             frames = max(1, min(FRAMES, oracle.threads()))
-            v, wall, cores = oracle_sample(frames, args.cpu_sample_iters, centred=args.centred, lam=args.lam,
-                                           lam_t=args.lam_t)
+            acc_iters = args.accuracy_iters or (ITERS if N <= 256 else 4)
+            # the oracle on the same inputs: the timed sample doubles as the accuracy check of this
+            # run's images (the GPU solves again for acc_iters iterations when that differs)
+            v, wall, cores, x_ref, sel = oracle_sample(frames, acc_iters, centred=args.centred, lam=args.lam,
+                                                       lam_t=args.lam_t, wl=wl)
             cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": "%d of %d frames x %d CG iterations (full 256x256, 12 coils, R=4), %.1f s"
-                             % (frames, FRAMES, args.cpu_sample_iters, wall)}
+                   "sample": "%d of %d frames x %d CG iterations (full %dx%d, %d coils, R=%d, FP64), %.1f s"
+                             % (frames, FRAMES, acc_iters, N, N, COILS, wl.accel, wall)}
+            accuracy = cg_accuracy(plan, y, S, lines, x_ref, sel, acc_iters, wl, args, oracle_sample if bf16 else None)
         # our kernels per step, counted by the plan's launch timers in the timing pass
         launches_per_step = sum(v["launches"] for v in phase.values()) / timed_steps
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(base_config(world, args.centred), **({"tikhonov_lambda": args.lam} if args.lam else {}),
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 storage / f32 math / f64 dots" if bf16 else "f32", "data": "synthetic",
+            "config": dict(base_config(world, args.centred, wl, args.storage),
+                           **({"tikhonov_lambda": args.lam} if args.lam else {}),
                            **({"temporal_lambda": args.lam_t} if args.lam_t else {})),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "ms_per_step": e2e_ms / args.steps},
+                    "ms_per_step": e2e_ms / args.steps,
+                    "path": "sense_cg_solve_host: pinned host buffers through the C ABI (copies in the timed region)"},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "accuracy": accuracy,
             "clocks": clocks.summary(t_wall0, t_wall1),
             "kernels_us": {k: round(v["ms_per_launch"] * 1e3, 2) for k, v in phase.items()},
             "operators": operators,
@@ -1002,7 +1131,7 @@ def main():
         return run_serve(args)
     if args.workload == "paper":
         return run_paper(args)
-    return run_ours(args)
+    return run_ours(args)  # cine, slices320
 
 
 if __name__ == "__main__":

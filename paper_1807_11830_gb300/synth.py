@@ -207,7 +207,7 @@ MIX_ACCEL = (2, 3, 4, 6)
 
 
 def paper_160(seed=BASE_SEED + 5, frames=16, noise_sigma=1e-3):
-    """The shapes of the timed reconstruction of Sec. V (16 cine frames of
+    """The shapes of the timed reconstruction of Sec. IV-B (16 cine frames of
     160x160, 8 coils, fully sampled Cartesian k-space), with 10-ellipse
     phantoms; it feeds the 2D inverse FFT + root-sum-of-squares and the
     Eq. 1 combine."""
