@@ -74,6 +74,9 @@ FLUSH_BYTES = 512 << 20
 # keyed by (kernel variant, CG mode): the lane-major 256-point variant in the
 # persistent kernel (40.4 MB read + 173.2 MB written over 30 iterations)
 CINE_TRAFFIC_PER_ITER = {(1, "persistent"): (40.359936e6 + 173.227776e6) / 30}
+# ncu DRAM traffic (read + write) of one k_cg_persistent launch of a mix size class, bytes per CG
+# iteration (empty until captured)
+MIX_TRAFFIC_PER_ITER = {}
 PAPER_WORKLOAD = ("paper reconstruction: 16 frames x 160x160, 8 coils, fully sampled; "
                   "2D inverse FFT + root-sum-of-squares (Sec. IV-B)")
 PAPER_METRIC, PAPER_UNIT = "reconstructions/s", "reconstructions/s"
@@ -104,7 +107,16 @@ def parse_args():
                          "count for cine, 4 for slices320)")
     ap.add_argument("--mix-count", type=int, default=512)
     ap.add_argument("--serve-rates", default="50,200,800")
-    ap.add_argument("--serve-requests", type=int, default=160)
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-pool", type=int, default=256,
+                    help="serving: distinct request instances drawn from the uneven-batch distribution")
+    ap.add_argument("--serve-log-dir", default="",
+                    help="serving: keep each rate's per-request queue log (JSON lines) in this directory")
+    ap.add_argument("--serve-queue-only", action="store_true",
+                    help="serving: skip the serial baseline (for tuning the queue)")
+    ap.add_argument("--serve-admit-waves", default="0",
+                    help="serving: the queue's admit_waves (0 = its default, negative = no saturation limit); "
+                         "a comma list runs the queue once per value")
     ap.add_argument("--serve-live-work", type=int, default=0,
                     help="serving: the queue's max_live_work (frames x coils x ny x nx live at once; 0 = default)")
     ap.add_argument("--cg-mode", default="auto", choices=("auto", "graph", "persistent"),
@@ -739,6 +751,48 @@ def run_mix(args):
     batch_ms = statistics.median(ms)
     ws = batch.workspace_bytes
     batch.close()
+    # per size class: a batch of that class's instances alone (one persistent launch per solve plus
+    # the instances' CG starts), timed the same way; its algorithmic bytes and flops per CG iteration
+    hbm_gbs, _, peak_src = peaks()
+    fp32_tflops, fp32_src = fp32_peak(local_rank, 2070.0)
+    classes = {}
+    for n in sorted({sp["n"] for sp in specs}):
+        sel = [k for k, sp in enumerate(specs) if sp["n"] == n]
+        cb = sense.Batch([shapes[k] for k in sel])
+        citems = [items[k] for k in sel]
+        sense.sense_batch_autotune(cb, citems)
+        sense.sense_batch_cg_solve(cb, citems, ITER)
+        torch.cuda.synchronize(dev)
+        cms = []
+        for _ in range(max(1, min(args.steps, 3))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sense.sense_batch_cg_solve(cb, citems, ITER)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            cms.append(e0.elapsed_time(e1))
+        sense.sense_batch_check(cb)
+        cb.close()
+        c_ms = statistics.median(cms)
+        img = n * n
+        nbytes = sum(8 * img * (specs[k]["coils"] + 10 * specs[k]["frames"]) for k in sel) * ITER
+        flops = sum(specs[k]["coils"] * specs[k]["frames"] for k in sel) * (2 * n * 5 * n * np.log2(n) + 14 * img) * ITER
+        classes[str(n)] = {"instances": len(sel), "frames": sum(specs[k]["frames"] for k in sel), "ms": c_ms,
+                           "algorithmic_gb": nbytes / 1e9, "achieved_gbs": nbytes / (c_ms / 1e3) / 1e9,
+                           "hbm_frac": nbytes / (c_ms / 1e3) / 1e9 / hbm_gbs,
+                           "achieved_tflops": flops / (c_ms / 1e3) / 1e12,
+                           "fp32_frac": flops / (c_ms / 1e3) / 1e12 / fp32_tflops}
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    d = classes[dom]
+    roofline = {"kernel": "k_cg_persistent, size class %s (%d instances, %d frames, %d CG iterations in one launch)"
+                          % (dom, d["instances"], d["frames"], ITER),
+                "bound": "alu", "achieved": d["achieved_tflops"], "peak": fp32_tflops, "unit": "TFLOP/s",
+                "frac": d["fp32_frac"], "traffic": MIX_TRAFFIC_PER_ITER.get(dom), "peak_source": fp32_src,
+                "hbm_achieved_gbs": d["achieved_gbs"], "hbm_peak_gbs": hbm_gbs, "hbm_frac": d["hbm_frac"],
+                "hbm_peak_source": "%s copy bandwidth (MEASURED_PEAKS.json)" % peak_src,
+                "algorithmic_bytes": "8 n^2 (C + 10 F) per instance and CG iteration (S once; 4 image vectors for "
+                                     "the normal product and its p update, 6 for the x/r update per frame)",
+                "duration_us_per_iteration": d["ms"] * 1e3 / ITER}
     # plain per-instance loop: the same kernels, per-iteration launches, no graphs, one instance at a time
     plans = []
     for d, sp in zip(inst, specs):
@@ -778,6 +832,7 @@ def run_mix(args):
                        "kind": "same kernels, per-iteration launches, one instance at a time"},
         "speedup_vs_plain": plain_ms / batch_ms,
         "workspace_gb": ws / 1e9, "setup_s": setup_s,
+        "roofline": roofline, "size_classes": classes,
     }
     print(json.dumps(line))
     return 0
@@ -786,12 +841,45 @@ def run_mix(args):
 # ---------------------------------------------------------------------------
 # serving: Poisson request streams through the queue
 # ---------------------------------------------------------------------------
-# page-locked staging the serving queue reserves up front: about what the 160-request
-# streams hold at once (every result stays staged until the stream has been submitted)
-SERVE_STAGING_BYTES = 2 << 30
+# page-locked staging the serving queue reserves up front: the inputs of the whole stream (under
+# overload every request's inputs are staged at once), at most 64 GiB
+SERVE_STAGING_CAP = 64 << 30
+
+
+def serve_pool(count, dev):
+    """`count` request instances drawn from the uneven-batch distribution (n,
+    coils, frames, acceleration), each its own phantom series, lines and
+    noise; maps per (n, coils); k-space = E x + noise made by the library's E.
+    Host copies (the queue and the serial loop both take host buffers)."""
+    import torch
+
+    from paper_1807_11830_gb300 import sense, synth
+
+    specs = synth.draw_mix(count, seed=1811)
+    maps = {}
+    pool = []
+    for k, sp in enumerate(specs):
+        p = synth.mix_instance(sp, 30000 + k)
+        F, n = p.x_true.shape[0], p.x_true.shape[1]
+        C, L = p.S.shape[0], p.lines.shape[1]
+        if (n, C) not in maps:
+            maps[(n, C)] = p.S.astype(np.complex64)
+        S = maps[(n, C)]
+        plan = sense.Plan(n, n, C, F, L)
+        S_d = torch.from_numpy(S).to(dev)
+        l_d = torch.from_numpy(p.lines).to(dev)
+        y_d = torch.empty((F, C, L, n), dtype=torch.complex64, device=dev)
+        sense.sense_forward(plan, torch.from_numpy(p.x_true.astype(np.complex64)).to(dev), S_d, l_d, y_d)
+        y_d += torch.from_numpy(p.noise.astype(np.complex64)).to(dev)
+        pool.append(dict(shape=dict(ny=n, nx=n, coils=C, frames=F, lines=L), y=y_d.cpu().numpy(), S=S,
+                         lines=np.ascontiguousarray(p.lines, np.int32), frames=F, n=n, spec=sp))
+        plan.close()
+    return pool
 
 
 def run_serve(args):
+    import tempfile
+
     import torch
 
     from paper_1807_11830_gb300 import sense, synth
@@ -800,44 +888,26 @@ def run_serve(args):
     torch.cuda.set_device(dev)
     sense.load_library()
     MAXIT, TOL = 100, 1e-4
-    # a pool of request shapes drawn from the mix distribution; k-space = E x + noise made by the library's E
-    specs = synth.draw_mix(24, seed=1811)
-    pool = []
-    for k, sp in enumerate(specs):
-        p = synth.mix_instance(sp, 30000 + k)
-        F, n = p.x_true.shape[0], p.x_true.shape[1]
-        C, L = p.S.shape[0], p.lines.shape[1]
-        plan = sense.Plan(n, n, C, F, L)
-        S_d = torch.from_numpy(p.S.astype(np.complex64)).to(dev)
-        l_d = torch.from_numpy(p.lines).to(dev)
-        y_d = torch.empty((F, C, L, n), dtype=torch.complex64, device=dev)
-        sense.sense_forward(plan, torch.from_numpy(p.x_true.astype(np.complex64)).to(dev), S_d, l_d, y_d)
-        y_d += torch.from_numpy(p.noise.astype(np.complex64)).to(dev)
-        # serial plain solve time of this request: inputs in from pinned host memory, the same
-        # kernels with per-iteration launches (the variant autotuned for them), image back to
-        # pinned host memory
-        sense.sense_plan_set_cg_mode(plan, sense.CG_MODE_DIRECT)
-        sense.sense_plan_autotune(plan, S_d, l_d)
-        x_d = torch.empty((F, n, n), dtype=torch.complex64, device=dev)
-        y_h, S_h, l_h = y_d.cpu().pin_memory(), S_d.cpu().pin_memory(), l_d.cpu().pin_memory()
-        x_h = torch.empty(x_d.shape, dtype=x_d.dtype).pin_memory()
-
-        def serial_solve():
-            y_d.copy_(y_h, non_blocking=True)
-            S_d.copy_(S_h, non_blocking=True)
-            l_d.copy_(l_h, non_blocking=True)
-            sense.sense_cg_solve(plan, y_d, S_d, l_d, MAXIT, TOL, x_d)
-            x_h.copy_(x_d, non_blocking=True)
-            torch.cuda.synchronize(dev)
-
-        serial_solve()
-        t = time.perf_counter()
-        for _ in range(2):
-            serial_solve()
-        solve_s = (time.perf_counter() - t) / 2
-        pool.append(dict(shape=dict(ny=n, nx=n, coils=C, frames=F, lines=L), y=y_d.cpu().numpy(),
-                         S=p.S.astype(np.complex64), lines=p.lines, solve_s=solve_s, frames=F, n=n))
-        plan.close()
+    t_setup = time.time()
+    pool = serve_pool(args.serve_pool, dev)
+    # serial plain solver: a plan per pool instance in direct mode (per-iteration launches, no graphs,
+    # one request at a time), its kernel variant autotuned for that mode, inputs and image through the
+    # host-buffer C-ABI call; plans and their device buffers made before any stream (untimed)
+    plans = []
+    for e in pool:
+        sh = e["shape"]
+        pl = sense.Plan(sh["ny"], sh["nx"], sh["coils"], sh["frames"], sh["lines"])
+        sense.sense_plan_set_cg_mode(pl, sense.CG_MODE_DIRECT)
+        sense.sense_plan_autotune(pl, torch.from_numpy(e["S"]).to(dev), torch.from_numpy(e["lines"]).to(dev))
+        plans.append(pl)
+    host = []
+    for e, pl in zip(pool, plans):
+        F, n = e["frames"], e["n"]
+        h = dict(y=torch.from_numpy(e["y"]), S=torch.from_numpy(e["S"]), lines=torch.from_numpy(e["lines"]),
+                 x=torch.empty((F, n, n), dtype=torch.complex64), it=torch.zeros(F, dtype=torch.int32),
+                 res=torch.zeros(F, dtype=torch.float64))
+        sense.sense_cg_solve_host(pl, h["y"], h["S"], h["lines"], 1, 0.0, h["x"])  # device buffers, warm-up
+        host.append(h)
     # kernel variant per size class for the queue: autotuned in persistent mode once, before any
     # stream (as a deployment would load it from a cache), on a loaded class -- 30 frames of 16
     # coils at R = 4 -- since under load each class launch carries the frames of many requests
@@ -851,56 +921,117 @@ def run_serve(args):
         class_variant[n], _ = sense.sense_plan_autotune(tp, torch.from_numpy(S_t).to(dev),
                                                         torch.from_numpy(np.ascontiguousarray(lines_t, np.int32)).to(dev))
         tp.close()
+    setup_s = time.time() - t_setup
+
+    def pct(v, p):
+        return float(np.percentile(v, p)) if len(v) else None
+
+    def converged(iters, resid):
+        return bool(np.all((resid <= TOL) | (iters >= MAXIT)))
+
     results = {}
-    for rate in [float(r) for r in args.serve_rates.split(",")]:
+    wave_list = [float(w) for w in str(args.serve_admit_waves).split(",")]
+    for rate, waves in [(float(r), w) for r in args.serve_rates.split(",") for w in wave_list]:
         count = args.serve_requests
         arrivals = synth.poisson_arrivals(rate, count, seed=int(rate) + 1811)
         picks = synth.rng_for(int(rate) + 7).integers(0, len(pool), size=count)
-        q = sense.Queue(device=0, staging_reserve_bytes=SERVE_STAGING_BYTES, max_live_work=args.serve_live_work)
+        # ---- the queue: latency from each request's arrival time to its retirement (queue log) ----
+        log_path = tempfile.mktemp(prefix="sense_queue_", suffix=".jsonl")
+        os.environ["SENSE_QUEUE_LOG"] = log_path
+        staging = min(SERVE_STAGING_CAP, int(sum(pool[pk]["y"].nbytes + pool[pk]["S"].nbytes + pool[pk]["lines"].nbytes
+                                                 + 8 * pool[pk]["frames"] * pool[pk]["n"] ** 2 for pk in picks)))
+        try:
+            q = sense.Queue(device=0, staging_reserve_bytes=staging, max_live_work=args.serve_live_work,
+                            admit_waves=waves)
+        except sense.SenseError:  # not that much page-locked memory: let the arena grow on demand
+            staging = 4 << 30
+            q = sense.Queue(device=0, staging_reserve_bytes=staging, max_live_work=args.serve_live_work,
+                            admit_waves=waves)
+        os.environ.pop("SENSE_QUEUE_LOG", None)
         for n, v in class_variant.items():
             q.set_variant(n, n, v)
         t0 = time.perf_counter()
-        ids = []
+        ids, sub_t, late = [], [], 0.0
         for a, pk in zip(arrivals, picks):
             now = time.perf_counter() - t0
             if a > now:
                 time.sleep(a - now)
+            else:
+                late = max(late, now - a)
             e = pool[pk]
+            sub_t.append(time.perf_counter() - t0)
             ids.append(q.submit(e["shape"], e["y"], e["S"], e["lines"], MAXIT, TOL))
-        for rid in ids:
-            q.wait(rid)
+        q_ok = True
+        for rid, pk in zip(ids, picks):
+            F = pool[pk]["frames"]
+            it, rs = np.zeros(F, np.int32), np.zeros(F, np.float64)
+            q.wait(rid, iters=it, resid=rs)
+            q_ok = q_ok and converged(it, rs)
         wall = time.perf_counter() - t0
         st = q.stats()
         q.close()
-        # serial plain solves of the same stream: one at a time in arrival order
-        finish, lat = 0.0, []
-        for a, pk in zip(arrivals, picks):
-            start = max(a, finish)
-            finish = start + pool[pk]["solve_s"]
-            lat.append((finish - a) * 1e3)
-        frames = sum(pool[pk]["frames"] for pk in picks)
-        results[str(int(rate))] = {
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+        done_ms, submit_ms = {}, {}
+        with open(log_path) as fh:
+            for line in fh:
+                d = json.loads(line)
+                done_ms[d["id"]] = d["done_ms"]
+                submit_ms[d["id"]] = d["submit_ms"]
+        if args.serve_log_dir:  # keep the queue's per-request log
+            os.makedirs(args.serve_log_dir, exist_ok=True)
+            os.replace(log_path, os.path.join(args.serve_log_dir, "queue_%dhz_w%g.jsonl" % (int(rate), waves)))
+        else:
+            os.remove(log_path)
+        # the queue log's clock (ms since its creation) against ours: each submit call's start is
+        # stamped by both, so their median difference maps retirement times onto arrival times
+        offset = float(np.median([submit_ms[rid] - 1e3 * t for rid, t in zip(ids, sub_t)]))
+        q_lat = [done_ms[rid] - offset - 1e3 * a for rid, a in zip(ids, arrivals)]
+        # ---- serial plain solves, live: one request at a time in arrival order ----
+        s_lat, s_ok = [], True
+        t0 = time.perf_counter()
+        for a, pk in zip(arrivals, picks if not args.serve_queue_only else []):
+            now = time.perf_counter() - t0
+            if a > now:
+                time.sleep(a - now)
+            h = host[pk]
+            sense.sense_cg_solve_host(plans[pk], h["y"], h["S"], h["lines"], MAXIT, TOL, h["x"], h["it"], h["res"])
+            s_lat.append((time.perf_counter() - t0 - a) * 1e3)
+            s_ok = s_ok and converged(h["it"].numpy(), h["res"].numpy())
+        s_wall = time.perf_counter() - t0
+        frames = int(sum(pool[pk]["frames"] for pk in picks))
+        results[str(int(rate)) if len(wave_list) == 1 else "%d@%g" % (int(rate), waves)] = {
+            "p50_ms": pct(q_lat, 50), "p99_ms": pct(q_lat, 99), "mean_ms": float(np.mean(q_lat)),
             "solves_per_s": count / wall, "ticks": st["ticks"],
-            "serial_plain": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                             "solves_per_s": count / finish,
-                             "kind": "one request at a time in arrival order; per-request time measured on the "
-                                     "GPU with host copies, plain per-iteration launches"},
+            "latency_from_submit_p50_p99_ms": [st["p50_ms"], st["p99_ms"]],
+            "submit_lag_max_ms": 1e3 * late,
+            "every_request_converged_or_at_100_iterations": q_ok,
+            "serial_plain": {"p50_ms": pct(s_lat, 50), "p99_ms": pct(s_lat, 99),
+                             "mean_ms": float(np.mean(s_lat)) if s_lat else None,
+                             "solves_per_s": count / s_wall if s_lat else None,
+                             "every_request_converged_or_at_100_iterations": s_ok,
+                             "kind": "live: one request at a time in arrival order through sense_cg_solve_host "
+                                     "(host buffers in and out), plain per-iteration launches, a prepared plan per "
+                                     "instance"},
             "requests": count, "frames": frames,
         }
     line = {
-        "metric": "served recon latency p50/p99 (ms) and solves/s", "value": results[max(results, key=float)]["solves_per_s"],
+        "metric": "served recon latency p50/p99 (ms) and solves/s", "value": list(results.values())[-1]["solves_per_s"],
         "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "serving: Poisson arrivals, sizes from the uneven-batch distribution, "
-                               "CG to a relative residual of 1e-4 or 100 iterations",
-                   "pool_shapes": len(pool),
+        "config": {"workload": "serving: Poisson arrivals, %d requests per rate, each a draw from a pool of %d "
+                               "instances sampled from the uneven-batch distribution (n in {128,192,256,384}, "
+                               "coils 8..32, frames 1..30, R in {2,3,4,6}); CG to a relative residual of 1e-4 or "
+                               "100 iterations" % (args.serve_requests, len(pool)),
+                   "latency": "from each request's Poisson arrival time to its result being ready in host memory",
                    "queue_variants": {str(n): v for n, v in sorted(class_variant.items())},
+                   "admit_waves": args.serve_admit_waves if args.serve_admit_waves != "0" else "default (6)",
                    "max_live_work": args.serve_live_work or "no limit",
-                   "staging": "%d GiB of page-locked host staging reserved at queue creation, before the "
-                              "stream starts" % (SERVE_STAGING_BYTES >> 30)},
+                   "staging": "page-locked host staging for every input of the stream (at most %d GiB) reserved "
+                              "at queue creation, before the stream starts" % (SERVE_STAGING_CAP >> 30),
+                   "setup_s": setup_s},
         "rates": results,
     }
     print(json.dumps(line))
+    for pl in plans:
+        pl.close()
     return 0
 
 

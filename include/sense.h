@@ -149,13 +149,22 @@ sense_status sense_adjoint(sense_plan* plan, const void* y, const void* S, const
 sense_status sense_adjoint_noalloc(const sense_shape* shape, const void* y, const void* S, const int32_t* lines,
                                    sense_c32* x, void* stream);
 
-/* Normal operator out = E^H E x, per frame.  Computed column-wise: because the
+/* Normal operator out = E^H E x, per frame: the composition of the encoding
+ * operator whose adjoint, with every line sampled, is Eq. 1 (Sec. IV-A) with
+ * that adjoint.  The paper applies Eq. 1 once and has no normal operator; it
+ * is the product every CG iteration needs.  Computed column-wise: because the
  * mask acts on rows only and F_x is unitary, E^H E = sum_c S_c^H F_y^H M_f F_y S_c,
  * so no x-direction transform is needed.  `out` must not alias `x`. */
 sense_status sense_normal(sense_plan* plan, const sense_c32* x, const void* S, const int32_t* lines,
                           sense_c32* out, void* stream);
 
-/* CG-SENSE: Hestenes-Stiefel conjugate gradients on (E^H E) x = E^H y, run
+/* CG-SENSE.  The paper reconstructs by Eq. 1 alone (Sec. IV-A), which is the
+ * least-squares solution only when every line is sampled and sum_c |S_c|^2 = 1;
+ * with undersampled k-space the same encoding model is inverted iteratively
+ * by conjugate gradients on its normal equations.  The paper fixes no
+ * iteration; the library's choices (per-frame scalars, FP64 inner products,
+ * the stopping rules below, breakdown handling) are stated here in full.
+ * Hestenes-Stiefel conjugate gradients on (E^H E) x = E^H y, run
  * independently per frame from x0 = 0 with FP64 inner products:
  *   r0 = p0 = E^H y;  per iteration  q = E^H E p,  alpha = <r,r>/Re<p,q>,
  *   x += alpha p,  r -= alpha q,  beta = <r',r'>/<r,r>,  p = r' + beta p.
@@ -188,6 +197,9 @@ sense_status sense_cg_solve_host(sense_plan* plan, const void* y_host, const voi
                                  double* rel_resid_host, int32_t* outcome_host, void* stream);
 
 /* ---- Uneven batching ----
+ * (No counterpart in the paper: a deployment layer that runs many
+ * independent sense_cg_solve problems together; each instance's result is
+ * its own solve's.) 
  * A batch holds many independent CG-SENSE problems ("instances") of
  * different ny x nx, coil count, frame count and line count.  Instances are
  * grouped by (ny, nx, storage) into size classes; every CG iteration of every
@@ -236,6 +248,8 @@ sense_status sense_batch_cg_solve(sense_batch* batch, const sense_batch_io* io, 
 sense_status sense_batch_check(sense_batch* batch, void* stream);
 
 /* ---- Serving: request queue with continuous batching ----
+ * (No counterpart in the paper: a serving layer over the same CG-SENSE solve;
+ * a request's result equals the problem solved alone, see below.) 
  * A scheduler thread admits submitted reconstructions in arrival order while
  * the HBM budget and the live-request limit allow, keeps their k-space, maps
  * and CG state on the device, and advances every live request by one CG
@@ -253,27 +267,26 @@ typedef struct sense_queue sense_queue;
 typedef struct {
   size_t hbm_budget_bytes; /* device bytes requests may hold; 0 = free memory at creation minus 1 GiB */
   int max_live;            /* most requests admitted at once; 0 = no limit */
-  int fake_device;         /* 1: no GPU work at all -- each tick sleeps fake_tick_us and every frame
-                              "converges" after min(max_iter, fake_iters) ticks (scheduler tests) */
-  int fake_tick_us;
-  int fake_iters;
   int autotune;            /* 1: autotune each size class on its first request; 0: variant 0 */
   int iters_per_tick;      /* CG iterations per tick; each frame still stops at its own max_iter /
                               tolerance inside the tick, new requests join between ticks.  0: adaptive --
                               while requests wait for admission, as many as fit in about 4 ms at the
                               last tick's time per iteration (1 to 10); otherwise 10, stretched up to 80
                               (the largest remaining budget of the live requests) */
-  int fail_admit_every;    /* test hook, 0 = off: every k-th admission fails as if a device allocation
-                              had failed (after the others succeeded); the request ends FAILED and
-                              sense_queue_wait returns SENSE_ENOMEM */
   size_t staging_reserve_bytes; /* page-locked host staging allocated at creation (0: none); the
                                    staging arena grows on demand beyond it */
   size_t max_live_work;    /* 0 = no limit.  Otherwise admit while the live requests' work, the sum of
                               frames x coils x ny x nx, stays at or below this (a request is admitted
-                              alone whatever its size): under overload, requests beyond it wait in
-                              arrival order instead of sharing every tick, so early ones finish early.
-                              Too low a value leaves the GPU part idle; waiting requests keep their
-                              host staging */
+                              alone whatever its size) */
+  double admit_waves;      /* saturation-aware admission: requests are admitted in arrival order while
+                              the live requests' normal-operator work per CG iteration -- for each live
+                              request, frames x column tiles of its size class's kernel variant, divided
+                              by the blocks that variant keeps resident on the device -- is below this
+                              many waves (the request that crosses it is admitted; a lone request always
+                              is).  Under overload the oldest requests then have the GPU to themselves
+                              while later ones wait, instead of every admitted request sharing each tick
+                              and all finishing near the end of the backlog.  0: the default, 6 waves;
+                              negative: no such limit (admission by budget and max_live only) */
 } sense_queue_cfg;
 
 typedef enum {
@@ -291,7 +304,9 @@ typedef struct {
   size_t staging_in_use;   /* of which held by requests: inputs until uploaded, outputs until waited for */
 } sense_queue_stats;
 
-/* cfg may be NULL (all fields 0).  When the environment variable
+/* cfg may be NULL (all fields 0).  (Scheduler tests create queues with
+ * host-only test hooks through sense_queue_create_with_hooks, declared in
+ * sense_testing.h.)  When the environment variable
  * SENSE_QUEUE_LOG names a file, the queue appends one JSON line per request
  * that leaves it (completed, failed or cancelled): id, shape, state, status,
  * submit_ms / admit_ms / first_tick_ms / done_ms (milliseconds since the

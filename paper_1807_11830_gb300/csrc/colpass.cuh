@@ -47,7 +47,7 @@ struct ColTma {
   static constexpr int W = 8;
   using C = Col<Base::T, W, typename Base::Radix>;
   static constexpr bool ok = (Base::T * W) % 32 == 0;
-  static constexpr int MINB = C::THREADS <= 256 ? 2 : 1;  // register cap 128 at two 256-thread blocks
+  static constexpr int MINB = C::THREADS <= 384 ? 2 : 1;  // two blocks per SM: register cap 128 (256 threads) to 85 (384)
   static constexpr int NB = N <= 256 ? N : N / 2;         // rows per S box
   static_assert(N <= 256 || N % 2 == 0, "two S boxes need an even length");
 };

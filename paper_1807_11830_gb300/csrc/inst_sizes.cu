@@ -89,3 +89,14 @@ cudaError_t launch_transpose_maps(bool bf16, const void* S, void* ST, int ny, in
 }
 
 }  // namespace sense
+
+namespace sense {
+
+int cg_persistent_resident_stc64(int n, int variant);
+int cg_persistent_resident_stbf16(int n, int variant);
+
+int cg_persistent_resident(int n, int variant, bool bf16) {
+  return bf16 ? cg_persistent_resident_stbf16(n, variant) : cg_persistent_resident_stc64(n, variant);
+}
+
+}  // namespace sense

@@ -34,6 +34,9 @@ cudaError_t launch_transpose_maps(bool bf16, const void* S, void* ST, int ny, in
 // `sms` x resident blocks per SM)
 template <class St>
 cudaError_t launch_cg_persistent(int n, int variant, const PArgs& a, int sms, cudaStream_t s);
+// blocks per SM the persistent CG kernel of (n, variant, storage) keeps
+// resident (0 if the variant does not exist)
+int cg_persistent_resident(int n, int variant, bool bf16);
 // forward row pass: FP32 in, storage St out
 template <class St>
 cudaError_t launch_rows_fwd(int n, const RowArgs<float2, typename St::T>& a, cudaStream_t s);

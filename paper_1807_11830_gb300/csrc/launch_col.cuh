@@ -75,6 +75,34 @@ cudaError_t persistent_nv(const PArgs& a, int sms, cudaStream_t s) {
   }
 }
 
+template <int N, int V, class St>
+int persistent_resident_nv() {
+  if constexpr (!NormCfg<N, V>::exists) {
+    return 0;
+  } else {
+    using C = typename NormCfg<N, V>::C;
+    static unsigned long long done = 0;
+    constexpr size_t sm = persistent_smem_bytes<C, St>();
+    if (ensure_smem(k_cg_persistent<N, V, St>, sm, &done) != cudaSuccess) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persistent<N, V, St>, C::THREADS, sm) !=
+        cudaSuccess)
+      return 0;
+    return per_sm;
+  }
+}
+
+template <int N, class St>
+int persistent_resident_n(int variant) {
+  switch (variant) {
+    case 0: return persistent_resident_nv<N, 0, St>();
+    case 1: return persistent_resident_nv<N, 1, St>();
+    case 2: return persistent_resident_nv<N, 2, St>();
+    case 3: return persistent_resident_nv<N, 3, St>();
+    default: return 0;
+  }
+}
+
 template <int N, class St>
 cudaError_t persistent_n(int variant, const PArgs& a, int sms, cudaStream_t s) {
   switch (variant) {

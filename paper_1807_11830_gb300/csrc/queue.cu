@@ -43,6 +43,7 @@
 #include "plan.h"
 #include "trace.h"
 #include "sense.h"
+#include "sense_testing.h"
 
 using namespace sense;
 using Clock = std::chrono::steady_clock;
@@ -83,6 +84,7 @@ struct Request {
   int state = SENSE_REQ_PENDING;
   bool cancel = false;
   int status_off = 0;  // position of its frames in the tick's status array
+  double waves = -1.0;  // normal-operator work per CG iteration in waves of resident blocks (at admission)
   int cls = -1;
   Clock::time_point t_submit, t_admit, t_first, t_done;
   bool admitted = false, ticked = false;
@@ -112,6 +114,7 @@ size_t elem_bytes(int storage) { return storage == SENSE_STORE_BF16 ? 4 : 8; }
 struct sense_queue {
   int device = 0;
   sense_queue_cfg cfg{};
+  sense_queue_test_hooks hooks{};
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Request*> pending;
@@ -232,6 +235,32 @@ void log_request(sense_queue* q, const Request* r) {
 
 // Work of a request per CG iteration, in coil-pixels: frames x coils x ny x nx.
 double request_work(const sense_shape& sh) { return (double)sh.frames * sh.coils * sh.ny * sh.nx; }
+
+// Normal-operator work of a request per CG iteration in waves of the device:
+// frames x column tiles of its size class's kernel variant, over the blocks
+// that variant's persistent kernel keeps resident (SMs x blocks per SM).
+// Called by the worker thread with q->mu held (reads the class variants).
+double request_waves(sense_queue* q, const sense_shape& sh) {
+  static std::map<std::tuple<int, int, int>, int> resident;  // (ny, variant, storage) -> blocks per SM
+  int variant = 0;
+  auto it = q->variants.find(std::make_tuple(sh.ny, sh.nx, sh.storage));
+  if (it != q->variants.end() && it->second >= 0) variant = it->second;
+  int W = normal_variant_width(sh.ny, variant);
+  if (W <= 0) W = 8;
+  int per_sm = 2;
+  if (!q->hooks.fake_device) {
+    const auto key = std::make_tuple(sh.ny, variant, sh.storage);
+    auto rt = resident.find(key);
+    if (rt == resident.end()) {
+      int occ = cg_persistent_resident(sh.ny, variant, sh.storage == SENSE_STORE_BF16);
+      rt = resident.emplace(key, occ > 0 ? occ : 1).first;
+    }
+    per_sm = rt->second;
+  }
+  const int sms = q->sms > 0 ? q->sms : 152;
+  const double tiles = (double)((sh.nx + W - 1) / W);
+  return (double)sh.frames * tiles / ((double)sms * per_sm);
+}
 
 void record_done(sense_queue* q, Request* r, int state) {
   std::lock_guard<std::mutex> lock(q->mu);
@@ -526,7 +555,7 @@ bool tick_device(sense_queue* q) {
 }
 
 void tick_fake(sense_queue* q) {
-  if (q->cfg.fake_tick_us > 0) std::this_thread::sleep_for(std::chrono::microseconds(q->cfg.fake_tick_us));
+  if (q->hooks.fake_tick_us > 0) std::this_thread::sleep_for(std::chrono::microseconds(q->hooks.fake_tick_us));
   std::vector<Request*> still;
   const Clock::time_point now = Clock::now();
   for (Request* r : q->live) {
@@ -540,7 +569,7 @@ void tick_fake(sense_queue* q) {
       std::lock_guard<std::mutex> lock(q->mu);
       cancel = r->cancel;
     }
-    const int stop_at = std::min(r->max_iter, q->cfg.fake_iters > 0 ? q->cfg.fake_iters : r->max_iter);
+    const int stop_at = std::min(r->max_iter, q->hooks.fake_iters > 0 ? q->hooks.fake_iters : r->max_iter);
     if (cancel) {
       record_done(q, r, SENSE_REQ_CANCELLED);
     } else if (r->ticks >= stop_at) {
@@ -560,13 +589,20 @@ void tick_fake(sense_queue* q) {
   q->live.swap(still);
 }
 
+constexpr double kDefaultAdmitWaves = 6.0;
+
 void worker_main(sense_queue* q) {
-  if (!q->cfg.fake_device) cudaSetDevice(q->device);
+  if (!q->hooks.fake_device) cudaSetDevice(q->device);
   for (;;) {
     std::vector<Request*> admit;
     const double work_cap = q->cfg.max_live_work > 0 ? (double)q->cfg.max_live_work : 1e300;
-    double live_work = 0.0;
-    for (const Request* r : q->live) live_work += request_work(r->sh);
+    const double waves_cap =
+        q->cfg.admit_waves < 0.0 ? 1e300 : (q->cfg.admit_waves == 0.0 ? kDefaultAdmitWaves : q->cfg.admit_waves);
+    double live_work = 0.0, live_waves = 0.0;
+    for (const Request* r : q->live) {
+      live_work += request_work(r->sh);
+      live_waves += r->waves;
+    }
     {
       std::unique_lock<std::mutex> lock(q->mu);
       q->cv_work.wait(lock, [&] { return q->stop || !q->pending.empty() || !q->live.empty(); });
@@ -588,6 +624,11 @@ void worker_main(sense_queue* q) {
         // enough work live to fill the GPU: later requests wait, in arrival order, rather
         // than share every tick and all finish late (a lone request over the cap is admitted)
         if (live_work > 0 && live_work + request_work(r->sh) > work_cap) break;
+        // saturation: enough normal-operator work is live to fill the device; the
+        // head waits (arrival order) so the oldest requests finish first
+        if (live_waves >= waves_cap) break;
+        if (r->waves < 0.0) r->waves = request_waves(q, r->sh);
+        live_waves += r->waves;
         live_work += request_work(r->sh);
         q->pending.pop_front();
         q->in_use += r->need;
@@ -600,9 +641,9 @@ void worker_main(sense_queue* q) {
     }
     for (Request* r : admit) {
       std::string err;
-      const bool inject = q->cfg.fail_admit_every > 0 && ++q->admissions % (uint64_t)q->cfg.fail_admit_every == 0;
+      const bool inject = q->hooks.fail_admit_every > 0 && ++q->admissions % (uint64_t)q->hooks.fail_admit_every == 0;
       bool ok;
-      if (q->cfg.fake_device) {
+      if (q->hooks.fake_device) {
         ok = !inject;
         if (inject) err = "device allocation failed (injected by the fail_admit_every test hook)";
       } else {
@@ -611,14 +652,14 @@ void worker_main(sense_queue* q) {
       if (ok) {
         q->live.push_back(r);
       } else {
-        if (!q->cfg.fake_device) free_device(r, q->stream);
+        if (!q->hooks.fake_device) free_device(r, q->stream);
         r->fail_status = err.rfind("device allocation failed", 0) == 0 ? SENSE_ENOMEM : SENSE_ECUDA;
         r->fail_msg = "admission failed: " + err;
         record_done(q, r, SENSE_REQ_FAILED);
       }
     }
     if (q->live.empty()) continue;
-    if (q->cfg.fake_device) {
+    if (q->hooks.fake_device) {
       tick_fake(q);
     } else if (!tick_device(q)) {
       // launches already issued on the class streams may still read the requests' memory
@@ -635,7 +676,7 @@ void worker_main(sense_queue* q) {
   }
   // shutdown: cancel what is left
   for (Request* r : q->live) {
-    if (!q->cfg.fake_device) free_device(r, q->stream);
+    if (!q->hooks.fake_device) free_device(r, q->stream);
     record_done(q, r, SENSE_REQ_CANCELLED);
   }
   q->live.clear();
@@ -660,19 +701,26 @@ sense_status qfail(sense_status s, const std::string& m) {
 extern "C" {
 
 sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_queue** out) {
+  return sense_queue_create_with_hooks(device, cfg, nullptr, out);
+}
+
+sense_status sense_queue_create_with_hooks(int device, const sense_queue_cfg* cfg, const sense_queue_test_hooks* hooks,
+                                           sense_queue** out) {
   if (!out) return qfail(SENSE_EINVAL, "out is NULL");
   *out = nullptr;
-  if (cfg && cfg->fail_admit_every < 0) return qfail(SENSE_EINVAL, "fail_admit_every must be >= 0");
+  if (hooks && hooks->fail_admit_every < 0) return qfail(SENSE_EINVAL, "fail_admit_every must be >= 0");
+  if (cfg && !(cfg->admit_waves == cfg->admit_waves)) return qfail(SENSE_EINVAL, "admit_waves is NaN");
   sense_queue* q = new sense_queue();
   if (cfg) q->cfg = *cfg;
+  if (hooks) q->hooks = *hooks;
   q->device = device;
   q->t0 = Clock::now();
-  q->arena.reset(new PinnedArena(!q->cfg.fake_device));
+  q->arena.reset(new PinnedArena(!q->hooks.fake_device));
   if (!q->arena->reserve(q->cfg.staging_reserve_bytes)) {
     delete q;
     return qfail(SENSE_ENOMEM, "staging reservation of page-locked host memory failed");
   }
-  if (!q->cfg.fake_device) {
+  if (!q->hooks.fake_device) {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
       delete q;
@@ -707,7 +755,7 @@ sense_status sense_queue_create(int device, const sense_queue_cfg* cfg, sense_qu
     if (*path) {
       q->log = std::fopen(path, "a");
       if (!q->log) {
-        if (!q->cfg.fake_device) {
+        if (!q->hooks.fake_device) {
           cudaEventDestroy(q->admitted);
           cudaStreamDestroy(q->stream);
         }
@@ -920,12 +968,12 @@ sense_status sense_queue_destroy(sense_queue* q) {
   if (q->worker.joinable()) q->worker.join();
   for (auto& kv : q->reqs) {
     Request* r = kv.second;
-    if (!q->cfg.fake_device) free_device(r, q->stream);
+    if (!q->hooks.fake_device) free_device(r, q->stream);
     free_outputs(q, r);
     free_host(q, r);
     delete r;
   }
-  if (!q->cfg.fake_device) {
+  if (!q->hooks.fake_device) {
     for (auto& kv : q->classes) {
       SizeClass& c = kv.second;
       for (void* p : {(void*)c.ints, (void*)c.part_nrm, (void*)c.part_upd, (void*)c.table_d, (void*)c.status_d})

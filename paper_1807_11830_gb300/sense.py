@@ -39,7 +39,7 @@ EXPORTED = (
     "sense_plan_set_temporal", "sense_batch_set_temporal",
     "sense_batch_create", "sense_batch_destroy", "sense_batch_workspace_bytes", "sense_batch_classes",
     "sense_batch_autotune", "sense_batch_set_variant", "sense_batch_cg_solve", "sense_batch_check",
-    "sense_queue_create", "sense_queue_submit", "sense_queue_poll", "sense_queue_wait", "sense_queue_cancel",
+    "sense_queue_create", "sense_queue_create_with_hooks", "sense_queue_submit", "sense_queue_poll", "sense_queue_wait", "sense_queue_cancel",
     "sense_queue_stats_get", "sense_queue_variant", "sense_queue_set_variant", "sense_queue_destroy",
 )
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_CANCELLED, REQ_FAILED = 0, 1, 2, 3, 4
@@ -78,10 +78,15 @@ class _BatchIO(ctypes.Structure):
 
 
 class _QueueCfg(ctypes.Structure):
-    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_live", ctypes.c_int), ("fake_device", ctypes.c_int),
-                ("fake_tick_us", ctypes.c_int), ("fake_iters", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("iters_per_tick", ctypes.c_int), ("fail_admit_every", ctypes.c_int),
-                ("staging_reserve_bytes", ctypes.c_size_t), ("max_live_work", ctypes.c_size_t)]
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_live", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("iters_per_tick", ctypes.c_int), ("staging_reserve_bytes", ctypes.c_size_t),
+                ("max_live_work", ctypes.c_size_t), ("admit_waves", ctypes.c_double)]
+
+
+class _QueueHooks(ctypes.Structure):
+    """sense_queue_test_hooks (sense_testing.h): host-only scheduler tests."""
+    _fields_ = [("fake_device", ctypes.c_int), ("fake_tick_us", ctypes.c_int), ("fake_iters", ctypes.c_int),
+                ("fail_admit_every", ctypes.c_int)]
 
 
 class _QueueStats(ctypes.Structure):
@@ -173,6 +178,9 @@ def load_library(path=LIB_PATH):
     lib.sense_batch_check.restype = st
     lib.sense_queue_create.argtypes = [i, ctypes.POINTER(_QueueCfg), ctypes.POINTER(vp)]
     lib.sense_queue_create.restype = st
+    lib.sense_queue_create_with_hooks.argtypes = [i, ctypes.POINTER(_QueueCfg), ctypes.POINTER(_QueueHooks),
+                                                  ctypes.POINTER(vp)]
+    lib.sense_queue_create_with_hooks.restype = st
     lib.sense_queue_submit.argtypes = [vp, ctypes.POINTER(_Shape), vp, vp, vp, i, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_uint64)]
     lib.sense_queue_submit.restype = st
@@ -485,12 +493,16 @@ class Queue:
 
     def __init__(self, device=0, hbm_budget_bytes=0, max_live=0, fake_device=False, fake_tick_us=0,
                  fake_iters=0, autotune=False, iters_per_tick=0, fail_admit_every=0, staging_reserve_bytes=0,
-                 max_live_work=0):
-        cfg = _QueueCfg(hbm_budget_bytes, max_live, 1 if fake_device else 0, fake_tick_us, fake_iters,
-                        1 if autotune else 0, iters_per_tick, fail_admit_every, staging_reserve_bytes,
-                        max_live_work)
+                 max_live_work=0, admit_waves=0.0):
+        cfg = _QueueCfg(hbm_budget_bytes, max_live, 1 if autotune else 0, iters_per_tick, staging_reserve_bytes,
+                        max_live_work, float(admit_waves))
         h = ctypes.c_void_p()
-        _check(load_library().sense_queue_create(device, ctypes.byref(cfg), ctypes.byref(h)))
+        lib = load_library()
+        if fake_device or fake_tick_us or fake_iters or fail_admit_every:  # test hooks (sense_testing.h)
+            hooks = _QueueHooks(1 if fake_device else 0, fake_tick_us, fake_iters, fail_admit_every)
+            _check(lib.sense_queue_create_with_hooks(device, ctypes.byref(cfg), ctypes.byref(hooks), ctypes.byref(h)))
+        else:
+            _check(lib.sense_queue_create(device, ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h
 
     def submit(self, shape, y, S, lines, max_iter, rel_tol=0.0):

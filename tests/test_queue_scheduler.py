@@ -300,3 +300,52 @@ def test_live_work_cap_admits_in_arrival_order():
     q.wait(b)
     assert q.stats()["completed"] == 2
     q.close()
+
+
+def test_saturation_admission_keeps_the_oldest_requests_live():
+    """With admit_waves set, requests are admitted in arrival order only while
+    the live normal-operator work is below that many device waves (the request
+    that crosses it is admitted).  Here each request is 0.026 waves (4 frames x
+    2 column tiles over 152 SMs x 2 resident blocks), so a cap of 0.03 keeps at
+    most two requests live, and they complete in arrival order."""
+    q = sense.Queue(fake_device=True, fake_tick_us=1000, fake_iters=4, admit_waves=0.03)
+    ids = [q.submit(*_req(frames=4), max_iter=10) for _ in range(6)]
+    peak, done_order, pending = 0, [], set(ids)
+    while pending:
+        peak = max(peak, q.stats()["live"])
+        for rid in list(pending):
+            if q.poll(rid)[0] == sense.REQ_DONE:
+                done_order.append(rid)
+                pending.discard(rid)
+        time.sleep(0.0005)
+    assert peak == 2
+    assert done_order == ids
+    for rid in ids:
+        q.wait(rid)
+    q.close()
+
+
+def test_saturation_admission_off_admits_everything():
+    q = sense.Queue(fake_device=True, fake_tick_us=3000, fake_iters=20, admit_waves=-1.0)
+    ids = [q.submit(*_req(frames=4), max_iter=20) for _ in range(6)]
+    peak = 0
+    for _ in range(40):
+        peak = max(peak, q.stats()["live"])
+        time.sleep(0.001)
+    assert peak == 6
+    for rid in ids:
+        q.wait(rid)
+    q.close()
+
+
+def test_test_hooks_are_not_part_of_the_public_config():
+    """The scheduler's test hooks live in sense_testing.h, not in sense_queue_cfg."""
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    public = open(os.path.join(root, "include", "sense.h")).read()
+    i = public.index("typedef struct {\n  size_t hbm_budget_bytes;")
+    cfg = public[i:public.index("} sense_queue_cfg;")]
+    for hook in ("fake_device", "fake_tick_us", "fake_iters", "fail_admit_every"):
+        assert hook not in cfg
+    testing = open(os.path.join(root, "include", "sense_testing.h")).read()
+    assert "sense_queue_create_with_hooks" in testing and "fail_admit_every" in testing
