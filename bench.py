@@ -72,8 +72,9 @@ UNIT = "applications/s"
 FLUSH_BYTES = 512 << 20
 # ncu DRAM traffic of k_cg_persistent on this workload, bytes per CG iteration,
 # keyed by (kernel variant, CG mode): the lane-major 256-point variant in the
-# persistent kernel (40.4 MB read + 173.2 MB written over 30 iterations)
-CINE_TRAFFIC_PER_ITER = {(1, "persistent"): (40.359936e6 + 173.227776e6) / 30}
+# persistent kernel with compensated coil sums (51.3 MB read + 146.6 MB
+# written over 30 iterations, one launch)
+CINE_TRAFFIC_PER_ITER = {(1, "persistent"): (51.302400e6 + 146.589440e6) / 30}
 # ncu DRAM traffic (read + write) of one k_cg_persistent launch of a mix size class, bytes per CG
 # iteration (empty until captured)
 MIX_TRAFFIC_PER_ITER = {}
@@ -83,8 +84,9 @@ PAPER_METRIC, PAPER_UNIT = "reconstructions/s", "reconstructions/s"
 # OpenCLIPER's own time for this workload on a GTX 970 (Table II: clFFT 1.361 ms + RSS 0.252 ms): context
 PAPER_GTX970_MS = 1.361 + 0.252
 # ncu DRAM traffic per launch of the paper workload's kernels (read + write), from one launch
-# list of `bench.py --workload paper` (k_rows_bulk<160,+1>, k_adj_col<160,c64,rss>)
-PAPER_TRAFFIC = {"rows_inv": 26.232576e6 + 0.0, "adj_col": 26.254848e6 + 0.0}
+# list of `bench.py --workload paper` (k_rows_bulk<160,+1>, k_adj_col_tma<160,c64,rss>); empty until
+# the current kernels are captured
+PAPER_TRAFFIC = {}
 
 
 def parse_args():
@@ -1022,7 +1024,7 @@ def run_serve(args):
                                "100 iterations" % (args.serve_requests, len(pool)),
                    "latency": "from each request's Poisson arrival time to its result being ready in host memory",
                    "queue_variants": {str(n): v for n, v in sorted(class_variant.items())},
-                   "admit_waves": args.serve_admit_waves if args.serve_admit_waves != "0" else "default (6)",
+                   "admit_waves": args.serve_admit_waves if args.serve_admit_waves != "0" else "default (12)",
                    "max_live_work": args.serve_live_work or "no limit",
                    "staging": "page-locked host staging for every input of the stream (at most %d GiB) reserved "
                               "at queue creation, before the stream starts" % (SERVE_STAGING_CAP >> 30),
@@ -1208,8 +1210,9 @@ def run_paper(args):
         dur_s = phase[dom] / 1e3
         achieved = kernel_bytes[dom] / dur_s / 1e9
         roofline = {
-            "kernel": {"rows_inv": "k_rows<160,+1> (inverse x-transforms of every k-space row)",
-                       "adj_col": "k_adj_col<160,c64,rss> (inverse y-transforms, |.|^2 summed over coils, sqrt)"}[dom],
+            "kernel": {"rows_inv": "k_rows_bulk<160,+1> (inverse x-transforms of every k-space row)",
+                       "adj_col": "k_adj_col_tma<160,c64,rss> (inverse y-transforms, |.|^2 summed over coils, "
+                                  "sqrt)"}[dom],
             "bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
             "traffic": PAPER_TRAFFIC.get(dom), "peak_source": "%s hbm_gbs (copy)" % peak_src,
             "algorithmic_mb_per_launch": kernel_bytes[dom] / 1e6, "duration_us": dur_s * 1e6,
