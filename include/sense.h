@@ -285,7 +285,7 @@ typedef struct {
                               many waves (the request that crosses it is admitted; a lone request always
                               is).  Under overload the oldest requests then have the GPU to themselves
                               while later ones wait, instead of every admitted request sharing each tick
-                              and all finishing near the end of the backlog.  0: the default, 6 waves;
+                              and all finishing near the end of the backlog.  0: the default, 12 waves;
                               negative: no such limit (admission by budget and max_live only) */
 } sense_queue_cfg;
 

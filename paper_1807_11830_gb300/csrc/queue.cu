@@ -589,7 +589,7 @@ void tick_fake(sense_queue* q) {
   q->live.swap(still);
 }
 
-constexpr double kDefaultAdmitWaves = 6.0;
+constexpr double kDefaultAdmitWaves = 12.0;
 
 void worker_main(sense_queue* q) {
   if (!q->hooks.fake_device) cudaSetDevice(q->device);
