@@ -84,9 +84,9 @@ PAPER_METRIC, PAPER_UNIT = "reconstructions/s", "reconstructions/s"
 # OpenCLIPER's own time for this workload on a GTX 970 (Table II: clFFT 1.361 ms + RSS 0.252 ms): context
 PAPER_GTX970_MS = 1.361 + 0.252
 # ncu DRAM traffic per launch of the paper workload's kernels (read + write), from one launch
-# list of `bench.py --workload paper` (k_rows_bulk<160,+1>, k_adj_col_tma<160,c64,rss>); empty until
-# the current kernels are captured
-PAPER_TRAFFIC = {}
+# list of `bench.py --workload paper` (k_rows_bulk<160,+1>: 26.23 MB read; k_adj_col_tma<160,c64,rss>:
+# 26.25 MB read; their writes leave L2 after the launch)
+PAPER_TRAFFIC = {"rows_inv": 26.232576e6, "adj_col": 26.254848e6}
 
 
 def parse_args():
@@ -589,11 +589,12 @@ def run_ours(args):
 
     # ---- the operators on their own (steps A, B, C outside CG), same plan and inputs ----
     operators = time_operators(plan, x_true, y, S, lines, flush, stream, dev, sbytes) if rank == 0 else None
-    if operators is not None:  # the same calls with the per-tile column kernels, for comparison
-        sense.sense_plan_set_column_pass(plan, 0)
-        reg = time_operators(plan, x_true, y, S, lines, flush, stream, dev, sbytes, only=("forward", "adjoint"))
+    if operators is not None:  # the same calls with the two-launch forms, for comparison
+        for mode, key in ((2, "fused_single_launch"), (0, "per_tile_column_kernels")):
+            sense.sense_plan_set_column_pass(plan, mode)
+            reg = time_operators(plan, x_true, y, S, lines, flush, stream, dev, sbytes, only=("forward", "adjoint"))
+            operators[key] = {k: {"ms": v["ms"], "hbm_frac": v["hbm_frac"]} for k, v in reg.items()}
         sense.sense_plan_set_column_pass(plan, 1)
-        operators["per_tile_column_kernels"] = {k: {"ms": v["ms"], "hbm_frac": v["hbm_frac"]} for k, v in reg.items()}
 
     # max over ranks
     total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], world, dev)
@@ -1205,14 +1206,17 @@ def run_paper(args):
     if rank == 0:
         hbm_gbs, _, peak_src = peaks()
         cimg = 8.0 * F * C * n * n  # one pass over the complex k-space (or its row-transformed copy)
-        kernel_bytes = {"rows_inv": 2 * cimg, "adj_col": cimg + 4.0 * F * n * n}
+        kernel_bytes = {"rows_inv": 2 * cimg, "adj_col": cimg + 4.0 * F * n * n,
+                        "adj_fused": cimg + 4.0 * F * n * n}  # one launch: read y, write the image
         dom = max(kernel_bytes, key=lambda k: phase.get(k, 0.0))
         dur_s = phase[dom] / 1e3
         achieved = kernel_bytes[dom] / dur_s / 1e9
         roofline = {
             "kernel": {"rows_inv": "k_rows_bulk<160,+1> (inverse x-transforms of every k-space row)",
                        "adj_col": "k_adj_col_tma<160,c64,rss> (inverse y-transforms, |.|^2 summed over coils, "
-                                  "sqrt)"}[dom],
+                                  "sqrt)",
+                       "adj_fused": "k_adjoint_fused<160,c64,rss> (both passes in one launch: inverse x- and "
+                                    "y-transforms, |.|^2 summed over coils, sqrt)"}[dom],
             "bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
             "traffic": PAPER_TRAFFIC.get(dom), "peak_source": "%s hbm_gbs (copy)" % peak_src,
             "algorithmic_mb_per_launch": kernel_bytes[dom] / 1e6, "duration_us": dur_s * 1e6,

@@ -373,14 +373,26 @@ sense_status sense_c32_to_bf16(const sense_c32* in, void* out, size_t count, voi
  * sums (the per-tile and per-chunk partitions differ). */
 sense_status sense_plan_set_cg_mode(sense_plan* plan, int mode);
 
-/* Column passes of E, E^H and root-sum-of-squares (the y-direction transforms
- * with the maps, line mask and coil sum).  1 (default): persistent kernels
- * that loop over (frame, 8-column tile) items and stage each coil's map tile
- * and k-space tile in shared memory by TMA one coil ahead, for every length
- * from 64 up whose 8-column tile fills whole warps (the other lengths use
- * the per-tile kernels whatever the setting).  0: per-tile kernels, one
- * block per (frame, column tile), tiles loaded through registers.  Both give
- * the same results up to the rounding order of the coil sums. */
+/* How E, E^H, the CG start and root-sum-of-squares run their two passes (the
+ * x-direction transforms of the sampled rows, and the y-direction transforms
+ * with the maps, line mask and coil sum):
+ *   2: both passes in ONE persistent launch for square images whose
+ *     length has a TMA column pass (below): row tiles and column tiles of
+ *     the frames are handed out in a frame-staggered order, a column tile
+ *     waits (bounded) for its frame's row tiles, and the row-transformed
+ *     intermediate of only a couple of frames is live at a time, so it stays
+ *     in L2 and one frame's row work overlaps another frame's column work.
+ *     Measured slower than mode 1 at every shape tried (the column work is
+ *     bound by its instruction stream, not by the intermediate's traffic, and
+ *     the dynamic schedule adds waits), so it is not the default;
+ *   1 (default): two launches, the column pass a persistent kernel that loops over
+ *     (frame, 8-column tile) items and stages each coil's map tile and
+ *     k-space tile in shared memory by TMA one coil ahead, for every length
+ *     from 64 up whose 8-column tile fills whole warps;
+ *   0: two launches, the column pass per-tile kernels (one block per
+ *     frame and column tile, tiles loaded through registers).
+ * Shapes a mode does not cover fall back to the next lower one.  All give the
+ * same results up to the rounding order of the coil sums. */
 sense_status sense_plan_set_column_pass(sense_plan* plan, int staged);
 
 /* Kernel variants.  Each transform length has one or more compiled variants
@@ -446,7 +458,9 @@ typedef enum {
   SENSE_PHASE_CG_PERSISTENT = 7, /* all CG iterations in one persistent launch */
   SENSE_PHASE_MAPS_TRANSPOSE = 8, /* S -> S^T for kernel variants with lane-major tiles */
   SENSE_PHASE_CG_FINISH = 9,      /* per-frame CG outputs (iterations, residual, outcome) */
-  SENSE_PHASE_COUNT = 10
+  SENSE_PHASE_FWD_FUSED = 10,     /* E, both passes in one launch */
+  SENSE_PHASE_ADJ_FUSED = 11,     /* E^H (also CG start, RSS), both passes in one launch */
+  SENSE_PHASE_COUNT = 12
 } sense_phase;
 
 /* Turn the plan's kernel timers on (1) or off (0); either way the totals

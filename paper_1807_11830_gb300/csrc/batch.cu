@@ -16,6 +16,7 @@
 #include <string>
 #include <vector>
 
+#include "fused.cuh"
 #include "launch.h"
 #include "plan.h"
 #include "trace.h"
@@ -358,18 +359,21 @@ sense_status sense_batch_cg_solve(sense_batch* b, const sense_batch_io* io, int 
     for (auto& c : b->classes) {
       PArgs none{};
       CUtensorMap none_map{};  // no work below: the launchers only set kernel attributes
+      const FusedSched none_sched{nullptr, nullptr, 0, 0, 0, 1};
       if (c.storage == SENSE_STORE_BF16) {
         RowArgs<__nv_bfloat162, float2> ra{};
         AdjColArgs<StBF16> aa{};
         launch_rows_inv<StBF16>(c.nx, ra, st);
         launch_adj_col<StBF16>(c.ny, 1, aa, 0, 0, st);
         launch_adj_col_tma<StBF16>(c.ny, 1, none_map, none_map, aa, 0, b->sms, st);
+        launch_adjoint_fused<StBF16>(c.ny, 1, true, none_map, none_map, aa, nullptr, nullptr, none_sched, 1.f, b->sms, st);
       } else {
         RowArgs<float2, float2> ra{};
         AdjColArgs<StC64> aa{};
         launch_rows_inv<StC64>(c.nx, ra, st);
         launch_adj_col<StC64>(c.ny, 1, aa, 0, 0, st);
         launch_adj_col_tma<StC64>(c.ny, 1, none_map, none_map, aa, 0, b->sms, st);
+        launch_adjoint_fused<StC64>(c.ny, 1, false, none_map, none_map, aa, nullptr, nullptr, none_sched, 1.f, b->sms, st);
       }
       cudaError_t e = c.storage == SENSE_STORE_BF16 ? launch_cg_persistent<StBF16>(c.ny, c.variant, none, b->sms, st)
                                                     : launch_cg_persistent<StC64>(c.ny, c.variant, none, b->sms, st);

@@ -58,6 +58,19 @@ template <class St>
 cudaError_t launch_fwd_col_tma(int n, const CUtensorMap& tmS, const FwdColArgs<St>& a, int tiles, int frames,
                                int sms, cudaStream_t s);
 
+// Single-launch fused operators (square images with a TMA column pass; else
+// cudaErrorNotSupported): E^H / CG start / RSS (`mode` 0 / 1 / 2; for RSS, St
+// is complex64 and y_bf16 gives y's storage) and E.  `sc` holds the ticket and
+// per-frame counters, zeroed by the caller on the same stream.
+struct FusedSched;
+template <class St>
+cudaError_t launch_adjoint_fused(int n, int mode, bool y_bf16, const CUtensorMap& tmK, const CUtensorMap& tmS,
+                                 const AdjColArgs<St>& a, const void* y, float2* tmp_out, const FusedSched& sc,
+                                 float cs, int sms, cudaStream_t s);
+template <class St>
+cudaError_t launch_forward_fused(int n, const CUtensorMap& tmS, const FwdColArgs<St>& a, void* y, const FusedSched& sc,
+                                 float cs, int sms, cudaStream_t s);
+
 // Set the dynamic shared memory limit of `kern` once per device.
 template <class K>
 inline cudaError_t ensure_smem(K kern, size_t bytes, unsigned long long* done_mask) {

@@ -15,6 +15,7 @@
 
 #include "cg_kernels.cuh"
 #include "colpass.cuh"
+#include "fused.cuh"
 #include "launch.h"
 #include "plan.h"
 #include "trace.h"
@@ -285,6 +286,18 @@ sense_status run_forward(sense_plan* pl, const float2* x, const void* S, const i
   a.centred = sh.centred;
   a.err = pl->err();
   sense_status rc;
+  if (pl->col_tma == 2 && sh.ny == sh.nx && coltma_supported(sh.ny)) {  // both passes in one launch
+    CUtensorMap tmS;
+    if (encode_maps_col(&tmS, sh, S)) {
+      const int row_items = ((sh.coils * sh.lines + 7) / 8 + kFusedRowTiles - 1) / kFusedRowTiles;
+      FusedSched sc{reinterpret_cast<unsigned*>(pl->fused_ints + sh.frames), pl->fused_ints, sh.frames, pl->tiles8,
+                    row_items, kFusedLag};
+      SENSE_CUDA_TRY(cudaMemsetAsync(pl->fused_ints, 0, sizeof(int) * ((size_t)sh.frames + 1), st));
+      PhaseScope ps(pl, SENSE_PHASE_FWD_FUSED, st);
+      const cudaError_t e = launch_forward_fused<St>(sh.ny, tmS, a, y, sc, centred_sign(sh), pl->sms, st);
+      if (e != cudaErrorNotSupported) return launch_status(e, "fused forward operator");
+    }
+  }
   {
     PhaseScope ps(pl, SENSE_PHASE_FWD_COL, st);
     cudaError_t e = cudaErrorNotSupported;
@@ -326,6 +339,54 @@ template <class St>
 sense_status run_adjoint(sense_plan* pl, int mode, const void* y, const void* S, const int* lines, float2* x,
                          float* rss, double tol, cudaStream_t st) {
   const sense_shape& sh = pl->sh;
+  if (pl->col_tma == 2 && sh.ny == sh.nx && coltma_supported(sh.ny)) {  // both passes in one launch
+    CUtensorMap tmK, tmS;
+    const bool maps_ok =
+        encode_rows_2d(&tmK, pl->tmp, 8, (size_t)sh.nx, (size_t)sh.frames * sh.coils * sh.lines, 8,
+                       kbox_rows(sh.lines)) &&
+        (mode == 2 ? encode_rows_2d(&tmS, pl->tmp, 8, (size_t)sh.nx, 1, 8, 1) : encode_maps_col(&tmS, sh, S));
+    if (maps_ok) {
+      const int row_items = ((sh.coils * sh.lines + 7) / 8 + kFusedRowTiles - 1) / kFusedRowTiles;
+      FusedSched sc{reinterpret_cast<unsigned*>(pl->fused_ints + sh.frames), pl->fused_ints, sh.frames, row_items,
+                    pl->tiles8, kFusedLag};
+      SENSE_CUDA_TRY(cudaMemsetAsync(pl->fused_ints, 0, sizeof(int) * ((size_t)sh.frames + 1), st));
+      const bool ybf16 = sh.storage == SENSE_STORE_BF16;
+      cudaError_t e;
+      PhaseScope ps(pl, SENSE_PHASE_ADJ_FUSED, st);
+      if (mode == 2) {
+        AdjColArgs<StC64> a{};
+        a.tmp = pl->tmp;
+        a.lines = lines;
+        a.tw = pl->tw_y;
+        a.rss = rss;
+        a.nx = sh.nx;
+        a.coils = sh.coils;
+        a.L = sh.lines;
+        a.tiles = pl->tiles8;
+        a.centred = sh.centred;
+        a.err = pl->err();
+        e = launch_adjoint_fused<StC64>(sh.ny, 2, ybf16, tmK, tmS, a, y, pl->tmp, sc, centred_sign(sh), pl->sms, st);
+      } else {
+        AdjColArgs<St> a{};
+        a.tmp = pl->tmp;
+        a.S = static_cast<const typename St::T*>(S);
+        a.lines = lines;
+        a.tw = pl->tw_y;
+        a.x = x;
+        a.r = pl->r;
+        a.p = pl->pp[0];
+        a.nx = sh.nx;
+        a.coils = sh.coils;
+        a.L = sh.lines;
+        a.tiles = pl->tiles8;
+        a.centred = sh.centred;
+        a.err = pl->err();
+        a.cg = pl->cg(tol);
+        e = launch_adjoint_fused<St>(sh.ny, mode, ybf16, tmK, tmS, a, y, pl->tmp, sc, centred_sign(sh), pl->sms, st);
+      }
+      if (e != cudaErrorNotSupported) return launch_status(e, "fused adjoint operator");
+    }
+  }
   sense_status rc = run_rows_inv<St>(pl, y, st);
   if (rc != SENSE_OK) return rc;
   // TMA column passes: the intermediate [F*C*L][nx] as a tensor map (box 8 x rows per box)
@@ -681,7 +742,7 @@ sense_status plan_allocate(sense_plan* pl) {
       (rc = dalloc(pl, &pl->ptable, F)) != SENSE_OK || (rc = dalloc(pl, &pl->pints, 4 * F + 1)) != SENSE_OK ||
       (rc = dalloc(pl, &pl->part_nrm, F * (size_t)max_tiles)) != SENSE_OK ||
       (rc = dalloc(pl, &pl->part_upd, F * (size_t)pl->max_chunks)) != SENSE_OK ||
-      (rc = dalloc(pl, &pl->tmap_d, 1)) != SENSE_OK)
+      (rc = dalloc(pl, &pl->tmap_d, 1)) != SENSE_OK || (rc = dalloc(pl, &pl->fused_ints, F + 1)) != SENSE_OK)
     return rc;
   return SENSE_OK;
 }
@@ -983,7 +1044,7 @@ sense_status sense_cg_solve_host(sense_plan* pl, const void* y_host, const void*
 
 sense_status sense_plan_set_column_pass(sense_plan* pl, int staged) {
   if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
-  if (staged != 0 && staged != 1) return fail(SENSE_EINVAL, "staged must be 0 or 1");
+  if (staged < 0 || staged > 2) return fail(SENSE_EINVAL, "staged must be 0, 1 or 2");
   pl->col_tma = staged;
   return SENSE_OK;
 }

@@ -48,7 +48,7 @@ NORM_VARIANTS = 4
 SIZES = (8, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192, 240, 256, 288, 320, 384)
 
 PHASES = ("rows_fwd", "rows_inv", "fwd_col", "adj_col", "normal", "cg_normal", "cg_update", "cg_persistent",
-          "maps_transpose", "cg_finish")
+          "maps_transpose", "cg_finish", "fwd_fused", "adj_fused")
 CG_MODE_GRAPH, CG_MODE_PERSISTENT, CG_MODE_DIRECT = 0, 1, 2
 
 

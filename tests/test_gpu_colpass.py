@@ -1,7 +1,8 @@
-"""The two column-pass implementations of E, E^H and root-sum-of-squares
-against the FP64 oracle: the persistent kernels that stage each coil's map
-and k-space tiles by TMA (the default for lengths from 64 up) and the
-per-tile kernels (sense_plan_set_column_pass(plan, 0)).
+"""The three ways E, E^H and root-sum-of-squares can run against the FP64
+oracle (sense_plan_set_column_pass): 1 (the default), two launches with the
+persistent TMA-staged column pass; 2, both passes in one persistent launch
+with a frame-staggered schedule (square images of a length with a TMA column
+pass); 0, two launches with the per-tile column kernels.
 
 Shapes cover every length with a TMA column pass, ragged column tails (nx not
 a multiple of 8), more (frame, tile) items than resident blocks (so blocks
@@ -65,7 +66,7 @@ SHAPES = [
 IDS = ["%dx%d_c%d_l%d_f%d" % s for s in SHAPES]
 
 
-@pytest.mark.parametrize("staged", [1, 0])
+@pytest.mark.parametrize("staged", [2, 1, 0])
 @pytest.mark.parametrize("shape", SHAPES, ids=IDS)
 def test_forward_and_adjoint_both_column_passes(shape, staged):
     x, S, lines, y = _problem(*shape, seed=7000 + sum(shape))
@@ -104,6 +105,15 @@ def test_centred_and_bf16(shape):
     sense.sense_plan_check(bplan)
     assert rel(xb.cpu().numpy(), oracle.adjoint(q(y), q(S), lines)) <= OP_TOL
     assert rel(bf16_pairs_to_complex(yb), oracle.forward(_as32(x), q(S), lines)) <= 2.0 ** -8
+    # the single-launch form on the same centred and BF16 problems
+    fplan = _plan(S, cl, 2, centred=True)
+    sense.sense_adjoint(fplan, c64(y), c64(S), i32(cl), xa)
+    sense.sense_plan_check(fplan)
+    assert rel(xa.cpu().numpy(), oracle.adjoint(_as32(y), _as32(S), cl, centred=True)) <= OP_TOL
+    fb = _plan(S, lines, 2, storage=sense.STORE_BF16)
+    sense.sense_forward(fb, c64(x), storage_tensor(S, sense.STORE_BF16), i32(lines), yb)
+    sense.sense_plan_check(fb)
+    assert rel(bf16_pairs_to_complex(yb), oracle.forward(_as32(x), q(S), lines)) <= 2.0 ** -8
 
 
 @pytest.mark.parametrize("shape", [(160, 160, 8, 160, 16), (256, 192, 4, 64, 3), (384, 384, 2, 300, 1)],
@@ -112,7 +122,7 @@ def test_rss_both_column_passes(shape):
     _, _, lines, y = _problem(*shape, seed=7200 + sum(shape))
     ny, nx, C, L, F = shape
     ref = oracle.rss(_as32(y), lines, ny)
-    for staged in (1, 0):
+    for staged in (2, 1, 0):
         plan = sense.Plan(ny, nx, C, F, L)
         sense.sense_plan_set_column_pass(plan, staged)
         out = torch.empty((F, ny, nx), dtype=torch.float32, device=DEV)
@@ -130,7 +140,7 @@ def test_cg_start_both_column_passes(shape):
     _, S, lines, y = _problem(*shape, seed=7300 + sum(shape))
     ny, nx, C, L, F = shape
     xo, io, _, _ = oracle.cg(_as32(y), _as32(S), lines, 6)
-    for staged in (1, 0):
+    for staged in (2, 1, 0):
         plan = _plan(S, lines, staged)
         x = torch.empty((F, ny, nx), dtype=torch.complex64, device=DEV)
         it = torch.zeros(F, dtype=torch.int32, device=DEV)
@@ -138,3 +148,27 @@ def test_cg_start_both_column_passes(shape):
         sense.sense_plan_check(plan)
         assert rel(x.cpu().numpy(), xo) <= CG_TOL
         np.testing.assert_array_equal(it.cpu().numpy(), io)
+
+
+@pytest.mark.parametrize("shape", [(256, 256, 12, 64, 20), (160, 160, 8, 160, 16), (128, 128, 3, 33, 1)],
+                         ids=lambda s: "%dx%d_f%d" % (s[0], s[1], s[4]))
+def test_fused_equals_two_launch_results(shape):
+    """The single-launch schedule gives the two-launch TMA results to the bit
+    for E (no sums differ) and within rounding for E^H, RSS and the CG start,
+    with many frames (so tiles of several frames are in flight at once)."""
+    x, S, lines, y = _problem(*shape, seed=7400 + sum(shape))
+    ny, nx, C, L, F = shape
+    res = {}
+    for staged in (2, 1):
+        plan = _plan(S, lines, staged)
+        yo = torch.empty((F, C, L, nx), dtype=torch.complex64, device=DEV)
+        xa = torch.empty((F, ny, nx), dtype=torch.complex64, device=DEV)
+        ro = torch.empty((F, ny, nx), dtype=torch.float32, device=DEV)
+        sense.sense_forward(plan, c64(x), c64(S), i32(lines), yo)
+        sense.sense_adjoint(plan, c64(y), c64(S), i32(lines), xa)
+        sense.sense_rss(plan, c64(y), i32(lines), ro)
+        sense.sense_plan_check(plan)
+        res[staged] = (yo.cpu().numpy(), xa.cpu().numpy(), ro.cpu().numpy())
+    np.testing.assert_array_equal(res[2][0], res[1][0])
+    assert rel(res[2][1], res[1][1]) <= 1e-6
+    assert rel(res[2][2], res[1][2]) <= 1e-6
