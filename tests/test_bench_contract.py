@@ -27,9 +27,10 @@ def _run(args, env_extra=None, timeout=300):
     return [l for l in res.stdout.splitlines() if l.strip()]
 
 
-@pytest.mark.parametrize("workload", ["cine", "paper"])
-def test_reference_line(workload):
-    out = _run(["--impl", "reference", "--workload", workload, "--steps", "1", "--warmup", "3"])
+@pytest.mark.parametrize("workload,extra", [("cine", []), ("paper", []), ("cine", ["--storage", "bf16"])],
+                         ids=["cine", "paper", "cine-bf16"])
+def test_reference_line(workload, extra):
+    out = _run(["--impl", "reference", "--workload", workload, "--steps", "1", "--warmup", "3"] + extra)
     assert len(out) == 1
     line = json.loads(out[0])
     assert KEYS <= set(line)
@@ -41,6 +42,8 @@ def test_reference_line(workload):
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    if extra:  # the reference arm describes the configuration of the arm it is compared with
+        assert "BF16" in line["config"]["workload"] and "bfloat16" in line["config"]["storage"]
 
 
 def test_reference_other_ranks_do_nothing():
