@@ -69,8 +69,29 @@ __host__ __device__ constexpr CosSin turn(long num, long den) {
 // ---------------------------------------------------------------------------
 // complex helpers on float2
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add and subtract as one paired FP32 operation (add.rn.f32x2 /
+// sub.rn.f32x2 on the (re, im) register pair): the same round-to-nearest
+// results as two scalar operations, in one instruction.
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
+  unsigned long long u;
+  memcpy(&u, &a, sizeof(u));
+  return u;
+}
+__device__ __forceinline__ float2 bits_f2(unsigned long long u) {
+  float2 a;
+  memcpy(&a, &u, sizeof(a));
+  return a;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(r);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(r);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
