@@ -92,6 +92,20 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
   return bits_f2(r);
 }
+// Element-wise paired multiply and fused multiply-add on (re, im) pairs
+// (mul.rn.f32x2 / fma.rn.f32x2): the same rounding as the two scalar
+// operations.  splat(s) is the pair (s, s).
+__device__ __forceinline__ float2 splat(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(r);
+}
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+  return bits_f2(r);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -103,7 +117,7 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 __device__ __forceinline__ float2 cfma_conj(float2 acc, float2 b, float2 a) {
   return make_float2(fmaf(b.x, a.x, fmaf(b.y, a.y, acc.x)), fmaf(b.x, a.y, fmaf(-b.y, a.x, acc.y)));
 }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return pmul(a, splat(s)); }
 
 // Compensated (Kahan) accumulation of a coil sum, hi + lo ~ sum_c conj(b_c) a_c.
 // A plain FP32 running sum rounds every step relative to the partial sum, so
@@ -112,19 +126,16 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 // explicit round-to-nearest operations so that nothing is contracted or
 // reassociated.
 // y = (the new term) - lo is formed by the fused multiply-adds that make the
-// term, so each component costs two FMAs and three adds.
-__device__ __forceinline__ void kahan_step(float& hi, float& lo, float y) {
-  const float t = __fadd_rn(hi, y);
-  lo = __fsub_rn(__fsub_rn(t, hi), y);
+// term; the Kahan step then runs on (re, im) together as three paired adds,
+// so a complex term costs four FMAs and three paired instructions.
+__device__ __forceinline__ void csum_fma_conj(float2& hi, float2& lo, float2 b, float2 a) {
+  const float2 y = make_float2(__fmaf_rn(b.x, a.x, __fmaf_rn(b.y, a.y, -lo.x)),
+                               __fmaf_rn(b.x, a.y, __fmaf_rn(-b.y, a.x, -lo.y)));
+  const float2 t = cadd(hi, y);
+  lo = csub(csub(t, hi), y);
   hi = t;
 }
-__device__ __forceinline__ void csum_fma_conj(float2& hi, float2& lo, float2 b, float2 a) {
-  kahan_step(hi.x, lo.x, __fmaf_rn(b.x, a.x, __fmaf_rn(b.y, a.y, -lo.x)));
-  kahan_step(hi.y, lo.y, __fmaf_rn(b.x, a.y, __fmaf_rn(-b.y, a.x, -lo.y)));
-}
-__device__ __forceinline__ float2 csum_value(float2 hi, float2 lo) {
-  return make_float2(__fsub_rn(hi.x, lo.x), __fsub_rn(hi.y, lo.y));
-}
+__device__ __forceinline__ float2 csum_value(float2 hi, float2 lo) { return csub(hi, lo); }
 // multiply by DIR * i
 template <int DIR>
 __device__ __forceinline__ float2 mul_i(float2 a) {
@@ -151,7 +162,7 @@ __device__ __forceinline__ void twiddle_const(float2& v) {
     constexpr float s = (cs.s > 0 ? 1.0f : -1.0f) * (float)DIR;
     float re = c * v.x - s * v.y;
     float im = s * v.x + c * v.y;
-    v = make_float2(re * h, im * h);
+    v = pmul(make_float2(re, im), splat(h));
   } else {
     constexpr CosSin cs = turn(r, M);
     constexpr float c = (float)cs.c;
@@ -187,7 +198,7 @@ struct Dft<3, DIR> {
     constexpr float h = 0.86602540378443864676f;  // sin(2 pi / 3)
     float2 s = cadd(v[1], v[2]);
     float2 d = csub(v[1], v[2]);
-    float2 m = make_float2(fmaf(-0.5f, s.x, v[0].x), fmaf(-0.5f, s.y, v[0].y));
+    float2 m = pfma(splat(-0.5f), s, v[0]);
     float2 t = mul_i<DIR>(cscale(d, h));
     v[0] = cadd(v[0], s);
     v[1] = cadd(m, t);
@@ -217,10 +228,10 @@ struct Dft<5, DIR> {
     constexpr float c1 = (float)w1.c, s1 = (float)w1.s, c2 = (float)w2.c, s2 = (float)w2.s;
     float2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
     float2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
-    float2 a1 = make_float2(fmaf(c1, t1.x, fmaf(c2, t2.x, v[0].x)), fmaf(c1, t1.y, fmaf(c2, t2.y, v[0].y)));
-    float2 a2 = make_float2(fmaf(c2, t1.x, fmaf(c1, t2.x, v[0].x)), fmaf(c2, t1.y, fmaf(c1, t2.y, v[0].y)));
-    float2 b1 = make_float2(fmaf(s1, t3.x, s2 * t4.x), fmaf(s1, t3.y, s2 * t4.y));
-    float2 b2 = make_float2(fmaf(s2, t3.x, -s1 * t4.x), fmaf(s2, t3.y, -s1 * t4.y));
+    float2 a1 = pfma(splat(c1), t1, pfma(splat(c2), t2, v[0]));
+    float2 a2 = pfma(splat(c2), t1, pfma(splat(c1), t2, v[0]));
+    float2 b1 = pfma(splat(s1), t3, pmul(splat(s2), t4));
+    float2 b2 = pfma(splat(s2), t3, pmul(splat(-s1), t4));
     b1 = mul_i<DIR>(b1);
     b2 = mul_i<DIR>(b2);
     v[0] = cadd(v[0], cadd(t1, t2));
