@@ -393,7 +393,10 @@ def time_operators(plan, x_img, y, S, lines, flush, stream, dev, sbytes=8, reps=
     frames.  Algorithmic bytes per call: the operator's inputs and outputs once
     (S once for all frames; `sbytes` per stored complex value of S and y); the
     two-pass intermediate is not counted.  `hbm_frac_s_per_frame` counts S
-    once per frame instead (the per-frame minimum of the forward operator)."""
+    once per frame instead (the per-frame minimum of the forward operator);
+    `hbm_frac_two_pass` adds, for E and E^H, the write and re-read of the
+    compacted [F][C][L][nx] complex64 intermediate (16·F·C·L·nx bytes) that
+    the two-launch form moves between its row and column passes."""
     import torch
 
     from paper_1807_11830_gb300 import sense
@@ -405,15 +408,15 @@ def time_operators(plan, x_img, y, S, lines, flush, stream, dev, sbytes=8, reps=
     x_out = torch.empty_like(x_img)
     calls = {
         "forward": (lambda: sense.sense_forward(plan, x_img, S, lines, y_out, stream=stream),
-                    8 * F * img + sbytes * (C * img + F * C * L * nx), sbytes * (F - 1) * C * img),
+                    8 * F * img + sbytes * (C * img + F * C * L * nx), sbytes * (F - 1) * C * img, 16 * F * C * L * nx),
         "adjoint": (lambda: sense.sense_adjoint(plan, y, S, lines, x_out, stream=stream),
-                    sbytes * (F * C * L * nx + C * img) + 8 * F * img, sbytes * (F - 1) * C * img),
+                    sbytes * (F * C * L * nx + C * img) + 8 * F * img, sbytes * (F - 1) * C * img, 16 * F * C * L * nx),
         "normal": (lambda: sense.sense_normal(plan, x_img, S, lines, x_out, stream=stream),
-                   sbytes * C * img + 16 * F * img, sbytes * (F - 1) * C * img),
+                   sbytes * C * img + 16 * F * img, sbytes * (F - 1) * C * img, 0),
     }
     hbm_gbs, _, _ = peaks()
     out = {}
-    for name, (call, nbytes, s_extra) in calls.items():
+    for name, (call, nbytes, s_extra, inter) in calls.items():
         if only and name not in only:
             continue
         for _ in range(3):
@@ -431,6 +434,8 @@ def time_operators(plan, x_img, y, S, lines, flush, stream, dev, sbytes=8, reps=
         out[name] = {"applications_per_s": F / (ms / 1e3), "ms": ms, "algorithmic_mb": nbytes / 1e6,
                      "achieved_gbs": gbs, "hbm_frac": gbs / hbm_gbs,
                      "hbm_frac_s_per_frame": (nbytes + s_extra) / (ms / 1e3) / 1e9 / hbm_gbs}
+        if inter:
+            out[name]["hbm_frac_two_pass"] = (nbytes + s_extra + inter) / (ms / 1e3) / 1e9 / hbm_gbs
     return out
 
 

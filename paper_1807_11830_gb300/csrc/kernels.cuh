@@ -992,24 +992,46 @@ __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSm
   };
   if (lane == 0) issue(fill, 0);
 
-  // p (CG: p = r + beta p_prev, written back) staged as [column][row]
-  for (int i = threadIdx.x; i < N * W; i += C::THREADS) {
-    const int row = i / W, cc = i - row * W, xx = x0 + cc;
-    float2 v = make_float2(0.f, 0.f);
-    if (xx < a.nx) {
-      const size_t idx = (size_t)row * a.nx + xx;
-      if (CG) {
-        v = __ldcg(a.p_src + idx);
-        if (a.p_update) {
-          const float2 rv = __ldcg(a.r + idx);
-          v = make_float2(fmaf(a.beta, v.x, rv.x), fmaf(a.beta, v.y, rv.y));
-          __stcg(a.p_dst + idx, v);
+  // p (CG: p = r + beta p_prev, written back) staged as [column][row].  A
+  // thread's loads are all issued before the first is used, so their L2
+  // latencies overlap instead of adding up.
+  constexpr int PER = N * W / C::THREADS;
+  static_assert(PER * C::THREADS == N * W, "whole staging rounds");
+  {
+    float2 pv[PER], rv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int i = (int)threadIdx.x + u * C::THREADS;
+      const int row = i / W, xx = x0 + (i - row * W);
+      pv[u] = make_float2(0.f, 0.f);
+      rv[u] = make_float2(0.f, 0.f);
+      if (xx < a.nx) {
+        const size_t idx = (size_t)row * a.nx + xx;
+        if (CG) {
+          pv[u] = __ldcg(a.p_src + idx);
+          if (a.p_update) rv[u] = __ldcg(a.r + idx);
+        } else {
+          pv[u] = __ldg(a.x + idx);
         }
-      } else {
-        v = negate_if(__ldg(a.x + idx), a.centred && ((row + xx) & 1));
       }
     }
-    s.buf0[cc * CP + row] = v;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int i = (int)threadIdx.x + u * C::THREADS;
+      const int row = i / W, cc = i - row * W, xx = x0 + cc;
+      float2 v = pv[u];
+      if (xx < a.nx) {
+        if (CG) {
+          if (a.p_update) {
+            v = pfma(splat(a.beta), v, rv[u]);
+            __stcg(a.p_dst + (size_t)row * a.nx + xx, v);
+          }
+        } else {
+          v = negate_if(v, a.centred && ((row + xx) & 1));
+        }
+      }
+      s.buf0[cc * CP + row] = v;
+    }
   }
   __syncthreads();
   float2 p[C::J0][C::R0], q[C::J0][C::R0], ql[C::J0][C::R0];  // q: compensated coil sum
