@@ -944,13 +944,22 @@ __device__ __forceinline__ void wcol_setup(const WSmem<C, St>& s, const float2* 
 }
 
 // line map of a frame: map[row] = index in the frame's line list, or -1
+// (The first round of line loads is issued before the map is cleared, so
+// its latency overlaps the clearing and the barrier.)
 template <int N, int THREADS>
 __device__ __forceinline__ void build_linemap(short* map, const int* ln, int L, int* err) {
+  const int l0 = (int)threadIdx.x;
+  int v0 = 0, u0 = -1;
+  if (l0 < L) {
+    v0 = __ldg(ln + l0);
+    if (l0 > 0) u0 = __ldg(ln + l0 - 1);
+  }
   for (int i = threadIdx.x; i < N; i += THREADS) map[i] = -1;
   __syncthreads();
-  for (int l = threadIdx.x; l < L; l += THREADS) {
-    const int v = __ldg(ln + l);
-    const bool good = v >= 0 && v < N && (l == 0 || __ldg(ln + l - 1) < v);
+  for (int l = l0; l < L; l += THREADS) {
+    const int v = l == l0 ? v0 : __ldg(ln + l);
+    const int u = l == l0 ? u0 : __ldg(ln + l - 1);  // l > 0 unless l == l0 == 0
+    const bool good = v >= 0 && v < N && (l == 0 || u < v);
     if (good)
       map[v] = (short)l;
     else

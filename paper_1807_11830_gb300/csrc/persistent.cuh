@@ -161,6 +161,11 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
   PTile<C, St> tile(smem_raw, a.tw);
   __shared__ int s_ticket, s_ok, s_active;
   unsigned nfill = 0;  // map copies requested so far by this block (same in every thread)
+  // The thread that takes the block's tickets: the next item's ticket is
+  // taken at the end of the current item, while thread 0 publishes the
+  // item's arrival, so the two atomic round trips overlap.
+  constexpr int TK = T > 32 ? 32 : 0;
+  if (threadIdx.x == TK) s_ticket = (int)atomicAdd(a.ticket, 1u);
 
   const int per_iter = a.nframes * (a.tiles + a.chunks);
   const long total = (long)per_iter * a.iters;
@@ -168,9 +173,7 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
   const PState& g = a.st;
 
   for (;;) {
-    __syncthreads();  // previous item fully done with shared memory and s_*
-    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(a.ticket, 1u);
-    __syncthreads();
+    __syncthreads();  // previous item fully done with shared memory and s_*; s_ticket is this item's
     const long t = s_ticket;
     if (t >= total) break;
     const int k = (int)(t / per_iter);
@@ -233,6 +236,7 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
         if (threadIdx.x == 0) __stcg(g.part_nrm + (size_t)f * a.tiles + piece, tot);
       }
       __threadfence();
+      if (threadIdx.x == TK) s_ticket = (int)atomicAdd(a.ticket, 1u);  // every thread has read this item's
       __syncthreads();
       if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(g.nrm_arrive + gi, 1u);
@@ -292,6 +296,7 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
         if (threadIdx.x == 0) __stcg(g.part_upd + (size_t)f * a.chunks + piece, tot);
       }
       __threadfence();
+      if (threadIdx.x == TK) s_ticket = (int)atomicAdd(a.ticket, 1u);
       __syncthreads();
       if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(g.upd_arrive + gi, 1u);
