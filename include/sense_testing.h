@@ -28,6 +28,17 @@ typedef struct {
 sense_status sense_queue_create_with_hooks(int device, const sense_queue_cfg* cfg, const sense_queue_test_hooks* hooks,
                                            sense_queue** out);
 
+/* The frame-staggered item order that the persistent CG kernel (units =
+   frame-iterations k*frames + f; first phase = normal-product tiles, second =
+   update chunks) and the single-launch operators (units = frames) hand out:
+   ticket t -> out[0] = 1 for a second-phase item, out[1] = unit, out[2] =
+   piece.  Stage s holds the first-phase items of unit s, then the
+   second-phase items of unit s - lag.  Host only; needs no GPU. */
+void sense_testing_staggered_item(long long t, int units, int first_items, int second_items, int lag, int out[3]);
+/* The stagger the persistent CG kernel uses for a table of independent
+   frames: frames, tiles per frame, grid blocks -> lag (0 .. frames - 1). */
+int sense_testing_persistent_lag(int frames, int tiles, int grid);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,7 @@ struct sense_batch {
     std::vector<int> members;  // instance indices
     int frames = 0;
     int variant = 0, tiles = 0, chunks = 0;
+    int order = kOrderIterationMajor;  // item order its frame table allows (persistent_order)
     int* ints = nullptr;        // nrm_arrive, upd_arrive, nrm_ready, upd_ready ([4][frames]), ticket
     double* part_nrm = nullptr; // [frames][tiles]
     double* part_upd = nullptr; // [frames][chunks]
@@ -101,8 +102,7 @@ void class_partition(sense_batch::Class& c) {
   const int W = normal_variant_width(c.ny, c.variant);
   const int th = normal_variant_threads(c.ny, c.variant);
   c.tiles = (c.nx + W - 1) / W;
-  const size_t img2 = (size_t)c.ny * c.nx / 2;
-  c.chunks = (int)((img2 + (size_t)th * 4 - 1) / ((size_t)th * 4));
+  c.chunks = update_chunks((size_t)c.ny * c.nx, th);
 }
 
 sense_status run_batch(sense_batch* b, const sense_batch_io* io, const std::vector<PFrame*>& tables, int max_iter,
@@ -124,6 +124,7 @@ sense_status run_batch(sense_batch* b, const sense_batch_io* io, const std::vect
       a.nx = c.nx;
       a.tiles = c.tiles;
       a.chunks = c.chunks;
+      a.lag = c.order;
       a.iters = max_iter;
       a.ticket = reinterpret_cast<unsigned*>(c.ints + 4 * c.frames);
       a.tw = b->plans[c.members[0]]->tw_y;
@@ -197,8 +198,7 @@ sense_status sense_batch_create(const sense_shape* shapes, int count, int device
         const int th = normal_variant_threads(c.ny, v);
         if (th > 0) min_threads = std::min(min_threads, th);
       }
-      const size_t img2 = (size_t)c.ny * c.nx / 2;
-      c.part_upd_cap = (img2 + (size_t)min_threads * 4 - 1) / ((size_t)min_threads * 4);
+      c.part_upd_cap = (size_t)update_chunks((size_t)c.ny * c.nx, min_threads);
       if ((rc = balloc(b, &c.ints, 4 * (size_t)c.frames + 1)) != SENSE_OK) break;
       if ((rc = balloc(b, &c.part_nrm, (size_t)c.frames * ((c.nx + 3) / 4))) != SENSE_OK) break;
       if ((rc = balloc(b, &c.part_upd, (size_t)c.frames * c.part_upd_cap)) != SENSE_OK) break;
@@ -354,6 +354,7 @@ sense_status sense_batch_cg_solve(sense_batch* b, const sense_batch_io* io, int 
         return bfail(SENSE_ECUDA, std::string("batch frame table: ") + cudaGetErrorString(e));
       }
       g.tables.push_back(dev);
+      c.order = persistent_order(host.data(), c.frames);
     }
     // kernel attributes are set outside the capture (empty grids launch nothing)
     for (auto& c : b->classes) {

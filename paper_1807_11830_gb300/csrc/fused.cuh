@@ -50,44 +50,6 @@ constexpr int kFusedRowTiles = 4;
 // Second-pass items of frame f come after the first-pass items of frame f + kFusedLag.
 constexpr int kFusedLag = 3;
 
-struct FusedItem {
-  int second;  // 0: first pass, 1: second pass
-  int f;
-  int piece;
-};
-
-// Ticket t of the frame-staggered order with lag D: stage s holds the
-// first-pass items of frame s (s < F), then the second-pass items of frame
-// s - D (s >= D).  So the first min(D, F) stages hold first-pass items only,
-// stages D .. F - 1 both kinds, and the last min(D, F) stages second-pass
-// items only.
-__host__ __device__ __forceinline__ FusedItem fused_item(long t, int F, int P1, int P2, int D) {
-  FusedItem it;
-  const long A = D < F ? D : F;
-  if (t < A * P1) {
-    it.second = 0;
-    it.f = (int)(t / P1);
-    it.piece = (int)(t - (long)it.f * P1);
-    return it;
-  }
-  t -= A * P1;
-  const long M = F > D ? F - D : 0;
-  const long per = (long)P1 + P2;
-  if (t < M * per) {
-    const long s = D + t / per;
-    const int r = (int)(t - (s - D) * per);
-    it.second = r >= P1;
-    it.f = it.second ? (int)(s - D) : (int)s;
-    it.piece = it.second ? r - P1 : r;
-    return it;
-  }
-  t -= M * per;
-  it.second = 1;
-  it.f = (int)((F - A) + t / P2);
-  it.piece = (int)(t - (long)(it.f - (F - A)) * P2);
-  return it;
-}
-
 // Shared memory of the fused kernels: twiddles, one exchange region used by
 // either pass (column engine: two N x 8 buffers; row engine: the 8-row tile
 // of pitch N + 2 and one N x 8 buffer), FP64 scratch, line map, two map
@@ -293,21 +255,21 @@ __global__ void __launch_bounds__(TH, ColTma<N>::MINB)
     __syncthreads();
     const long t = s_ticket;
     if (t >= total) break;
-    const FusedItem it = fused_item(t, sc.frames, sc.first_tiles, sc.second_tiles, sc.lag);
-    if (!it.second) {  // ---- rows of frame it.f: kFusedRowTiles tiles of 8 ----
+    const StaggeredItem it = staggered_item(t, sc.frames, sc.first_tiles, sc.second_tiles, sc.lag);
+    if (!it.second) {  // ---- rows of frame it.unit: kFusedRowTiles tiles of 8 ----
       for (int k = 0; k < kFusedRowTiles; ++k) {
         const int first = (it.piece * kFusedRowTiles + k) * 8;
         if (first >= rows_per_frame) break;
         const int left = rows_per_frame - first;
         if (k > 0) __syncthreads();  // the previous tile's stores have read the shared tile
-        fused_row_tile<N, +1, YSt, StC64, C>(y, tmp_out, (long)it.f * rows_per_frame + first, left < 8 ? left : 8,
+        fused_row_tile<N, +1, YSt, StC64, C>(y, tmp_out, (long)it.unit * rows_per_frame + first, left < 8 ? left : 8,
                                              s.tw, fs.tile, fs.rbuf, a.centred, cs);
       }
-      fused_count(sc.done, it.f);
+      fused_count(sc.done, it.unit);
       continue;
     }
-    // ---- column tile it.piece of frame it.f ----
-    const int f = it.f, tile = it.piece;
+    // ---- column tile it.piece of frame it.unit ----
+    const int f = it.unit, tile = it.piece;
     if (threadIdx.x == 0) {
       s_ok = fused_wait(sc, f, a.err) ? 1 : 0;
       coltma_issue<N, St, WITH_S, true>(m, &tmS, &tmK, fill, f, tile, 0, a.coils, a.L);
@@ -456,9 +418,9 @@ __global__ void __launch_bounds__(TH, ColTma<N>::MINB)
     __syncthreads();
     const long t = s_ticket;
     if (t >= total) break;
-    const FusedItem it = fused_item(t, sc.frames, sc.first_tiles, sc.second_tiles, sc.lag);
-    if (it.second) {  // ---- rows of frame it.f: y = F_x(intermediate rows), kFusedRowTiles tiles of 8 ----
-      if (threadIdx.x == 0) s_ok = wait_at_least(sc.done + it.f, sc.first_tiles) ? 1 : 0;
+    const StaggeredItem it = staggered_item(t, sc.frames, sc.first_tiles, sc.second_tiles, sc.lag);
+    if (it.second) {  // ---- rows of frame it.unit: y = F_x(intermediate rows), kFusedRowTiles tiles of 8 ----
+      if (threadIdx.x == 0) s_ok = wait_at_least(sc.done + it.unit, sc.first_tiles) ? 1 : 0;
       __syncthreads();
       if (!s_ok) {
         if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
@@ -469,13 +431,13 @@ __global__ void __launch_bounds__(TH, ColTma<N>::MINB)
         if (first >= rows_per_frame) break;
         const int left = rows_per_frame - first;
         if (k > 0) __syncthreads();
-        fused_row_tile<N, -1, StC64, St, C>(a.tmp, y, (long)it.f * rows_per_frame + first, left < 8 ? left : 8, s.tw,
+        fused_row_tile<N, -1, StC64, St, C>(a.tmp, y, (long)it.unit * rows_per_frame + first, left < 8 ? left : 8, s.tw,
                                             fs.tile, fs.rbuf, a.centred, cs);
       }
       continue;
     }
-    // ---- column tile it.piece of frame it.f ----
-    const int f = it.f, tile = it.piece;
+    // ---- column tile it.piece of frame it.unit ----
+    const int f = it.unit, tile = it.piece;
     if (threadIdx.x == 0) coltma_issue<N, St, true, false>(m, &tmS, nullptr, fill, f, tile, 0, a.coils, a.L);
     if (f != mapped_f) {
       fused_linemap<N, C::THREADS>(s, a.lines, a.L, f, a.err);

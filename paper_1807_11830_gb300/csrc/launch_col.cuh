@@ -70,7 +70,10 @@ cudaError_t persistent_nv(const PArgs& a, int sms, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (a.nframes == 0 || a.iters == 0) return cudaSuccess;  // attribute set-up only
-    k_cg_persistent<N, V, St><<<sms * per_sm, C::THREADS, sm, s>>>(a);
+    PArgs b = a;
+    if (b.lag == kOrderAuto) b.lag = persistent_lag(b.nframes, b.tiles, sms * per_sm);
+    if (b.lag < kOrderIterationMajor || (b.lag > 0 && b.lag >= b.nframes)) return cudaErrorInvalidValue;  // D < frames
+    k_cg_persistent<N, V, St><<<sms * per_sm, C::THREADS, sm, s>>>(b);
     return cudaGetLastError();
   }
 }

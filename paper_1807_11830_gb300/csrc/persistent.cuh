@@ -10,8 +10,11 @@
 //   phase 1 (update): piece = chunk of the image: x += alpha p_k,
 //                     r -= alpha q, <r, r> partial; the last chunk computes
 //                     beta and the stopping test.
-// Tickets are ordered by iteration, then phase, then frame, then piece.  An
-// item waits (thread 0, bounded spin) only for the previous phase of its own
+// Tickets follow one of two orders (PArgs::lag, below): iteration-major
+// (iteration, then phase, then frame, then piece), or frame-staggered, where
+// a frame's update chunks come a few frames' worth of tiles after its own
+// tiles, so they rarely find those tiles still running.  In both, an item
+// waits (thread 0, bounded spin) only for the previous phase of its own
 // frame, i.e. for items with smaller tickets, which blocks already running
 // have taken.  So the wait always ends; frames pipeline freely: one frame's
 // memory-bound update runs while another frame's transform-bound normal
@@ -25,6 +28,71 @@
 #include "kernels.cuh"
 
 namespace sense {
+
+// A two-phase item of a frame-staggered order: units 0 .. U-1 (frames, or
+// frame-iterations) each have P1 first-phase items and P2 second-phase ones.
+struct StaggeredItem {
+  int second;  // 0: first phase, 1: second phase
+  int unit;
+  int piece;
+};
+
+// Ticket t of the frame-staggered order with lag D: stage s holds the
+// first-phase items of unit s (s < U), then the second-phase items of unit
+// s - D (s >= D).  So the first min(D, U) stages hold first-phase items only,
+// stages D .. U - 1 both kinds, and the last min(D, U) stages second-phase
+// items only.  A unit's second phase comes D stages after its first.
+__host__ __device__ __forceinline__ StaggeredItem staggered_item(long t, int U, int P1, int P2, int D) {
+  StaggeredItem it;
+  const long A = D < U ? D : U;
+  if (t < A * P1) {
+    it.second = 0;
+    it.unit = (int)(t / P1);
+    it.piece = (int)(t - (long)it.unit * P1);
+    return it;
+  }
+  t -= A * P1;
+  const long M = U > D ? U - D : 0;
+  const long per = (long)P1 + P2;
+  if (t < M * per) {
+    const long s = D + t / per;
+    const int r = (int)(t - (s - D) * per);
+    it.second = r >= P1;
+    it.unit = it.second ? (int)(s - D) : (int)s;
+    it.piece = it.second ? r - P1 : r;
+    return it;
+  }
+  t -= M * per;
+  it.second = 1;
+  it.unit = (int)((U - A) + t / P2);
+  it.piece = (int)(t - (long)(it.unit - (U - A)) * P2);
+  return it;
+}
+
+// Update items: each thread updates kUpdateRounds rounds of kUpdateVec float4
+// (two complex values each) of one frame's image.
+constexpr int kUpdateVec = 4, kUpdateRounds = 4;
+__host__ __device__ constexpr int update_chunks(size_t img, int threads) {
+  return (int)((img / 2 + (size_t)threads * kUpdateVec * kUpdateRounds - 1) /
+               ((size_t)threads * kUpdateVec * kUpdateRounds));
+}
+
+// Item orders of the persistent CG kernel (PArgs::lag).
+//   kOrderIterationMajor: per CG iteration, every frame's normal-product
+//     tiles, then every frame's update chunks.
+//   D >= 0: frame-staggered over frame-iterations u = k F + f
+//     (staggered_item with P1 = tiles, P2 = chunks): u's update chunks follow
+//     the tiles of u + D.  Valid when every frame is its own CG (no temporal
+//     coupling) and D < F: u's update waits for u's tiles, D stages earlier,
+//     and the tiles of u + F (the frame's next iteration) wait for u's
+//     update, F - D stages earlier.  So every wait is for smaller tickets.
+//   kOrderAuto: the launcher picks D from the grid: enough stages that about
+//     one wave of tiles separates a frame's tiles from its update.
+constexpr int kOrderIterationMajor = -1, kOrderAuto = -2;
+__host__ __device__ constexpr int persistent_lag(int frames, int tiles, int grid) {
+  const int d = (grid + tiles - 1) / (tiles > 0 ? tiles : 1) + 1;
+  return frames <= 1 ? 0 : (d < frames - 1 ? d : frames - 1);
+}
 
 // One frame of the table: its instance's maps, its own vectors and its own
 // CG scalars (wherever its owner keeps them), so frames of different
@@ -63,9 +131,18 @@ struct PState {
   double *part_nrm, *part_upd;                // [frames][tiles] / [frames][chunks]
 };
 
+// The order a frame table allows: the staggered one (picked by the launcher)
+// unless some frames are coupled in time.
+inline int persistent_order(const PFrame* host_table, int frames) {
+  for (int f = 0; f < frames; ++f)
+    if (host_table[f].gsize != 1) return kOrderIterationMajor;
+  return kOrderAuto;
+}
+
 struct PArgs {
   const PFrame* frames;
   int nframes, nx, tiles, chunks, iters;
+  int lag;  // item order: kOrderIterationMajor, kOrderAuto or a stagger D >= 0 (see above)
   unsigned* ticket;
   const float2* tw;  // twiddles of the column transform
   int* err;
@@ -176,13 +253,23 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
     __syncthreads();  // previous item fully done with shared memory and s_*; s_ticket is this item's
     const long t = s_ticket;
     if (t >= total) break;
-    const int k = (int)(t / per_iter);
-    int w = (int)(t - (long)k * per_iter);
-    const bool normal = w < a.nframes * a.tiles;
-    if (!normal) w -= a.nframes * a.tiles;
-    const int per = normal ? a.tiles : a.chunks;
-    const int f = w / per;
-    const int piece = w - f * per;
+    int k, f, piece;
+    bool normal;
+    if (a.lag >= 0) {
+      const StaggeredItem it = staggered_item(t, a.nframes * a.iters, a.tiles, a.chunks, a.lag);
+      normal = !it.second;
+      k = it.unit / a.nframes;
+      f = it.unit - k * a.nframes;
+      piece = it.piece;
+    } else {
+      k = (int)(t / per_iter);
+      int w = (int)(t - (long)k * per_iter);
+      normal = w < a.nframes * a.tiles;
+      if (!normal) w -= a.nframes * a.tiles;
+      const int per = normal ? a.tiles : a.chunks;
+      f = w / per;
+      piece = w - f * per;
+    }
     const PFrame fr = a.frames[f];
     const int gi = fr.g0;  // this frame's group: state index and first table entry
 
@@ -266,30 +353,34 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
         float4* xp = reinterpret_cast<float4*>(fr.x);
         float4* rp = reinterpret_cast<float4*>(fr.r);
         const long img4 = (long)(img / 2);
-        constexpr int VEC = 4;
-        float4 xv[VEC], pv[VEC], qv[VEC], rv[VEC];
+        constexpr int VEC = kUpdateVec;
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+        for (int rd = 0; rd < kUpdateRounds; ++rd) {
+          const long base = ((long)piece * kUpdateRounds + rd) * (T * VEC) + threadIdx.x;
+          float4 xv[VEC], pv[VEC], qv[VEC], rv[VEC];
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-          const long i = (long)piece * (T * VEC) + j * T + threadIdx.x;
-          const bool ok = i < img4;
-          xv[j] = ok ? __ldcg(xp + i) : z;
-          pv[j] = ok ? __ldcg(pp + i) : z;
-          qv[j] = ok ? __ldcg(qp + i) : z;
-          rv[j] = ok ? __ldcg(rp + i) : z;
-        }
+          for (int j = 0; j < VEC; ++j) {
+            const long i = base + j * T;
+            const bool ok = i < img4;
+            xv[j] = ok ? __ldcg(xp + i) : z;
+            pv[j] = ok ? __ldcg(pp + i) : z;
+            qv[j] = ok ? __ldcg(qp + i) : z;
+            rv[j] = ok ? __ldcg(rp + i) : z;
+          }
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-          const long i = (long)piece * (T * VEC) + j * T + threadIdx.x;
-          float4 xn = xv[j], rn = rv[j];
-          xn.x = fmaf(al, pv[j].x, xn.x); xn.y = fmaf(al, pv[j].y, xn.y);
-          xn.z = fmaf(al, pv[j].z, xn.z); xn.w = fmaf(al, pv[j].w, xn.w);
-          rn.x = fmaf(-al, qv[j].x, rn.x); rn.y = fmaf(-al, qv[j].y, rn.y);
-          rn.z = fmaf(-al, qv[j].z, rn.z); rn.w = fmaf(-al, qv[j].w, rn.w);
-          if (i < img4) {
-            __stcg(xp + i, xn);
-            __stcg(rp + i, rn);
-            acc = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, acc))));
+          for (int j = 0; j < VEC; ++j) {
+            const long i = base + j * T;
+            float4 xn = xv[j], rn = rv[j];
+            xn.x = fmaf(al, pv[j].x, xn.x); xn.y = fmaf(al, pv[j].y, xn.y);
+            xn.z = fmaf(al, pv[j].z, xn.z); xn.w = fmaf(al, pv[j].w, xn.w);
+            rn.x = fmaf(-al, qv[j].x, rn.x); rn.y = fmaf(-al, qv[j].y, rn.y);
+            rn.z = fmaf(-al, qv[j].z, rn.z); rn.w = fmaf(-al, qv[j].w, rn.w);
+            if (i < img4) {
+              __stcg(xp + i, xn);
+              __stcg(rp + i, rn);
+              acc = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, acc))));
+            }
           }
         }
         const double tot = block_sum<T>((double)acc, tile.red());

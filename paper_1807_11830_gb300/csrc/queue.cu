@@ -296,7 +296,7 @@ bool ensure_class_capacity(sense_queue* q, SizeClass& c, int frames) {
     const int th = normal_variant_threads(c.ny, v);
     if (th > 0) min_threads = std::min(min_threads, th);
   }
-  c.upd_cap = (int)(((size_t)c.ny * c.nx / 2 + (size_t)min_threads * 4 - 1) / ((size_t)min_threads * 4));
+  c.upd_cap = update_chunks((size_t)c.ny * c.nx, min_threads);
   bool ok = cudaMalloc(&c.ints, sizeof(int) * (4 * (size_t)cap + 1)) == cudaSuccess &&
             cudaMalloc(&c.part_nrm, sizeof(double) * (size_t)cap * ((c.nx + 3) / 4)) == cudaSuccess &&
             cudaMalloc(&c.part_upd, sizeof(double) * (size_t)cap * c.upd_cap) == cudaSuccess &&
@@ -481,7 +481,8 @@ bool tick_device(sense_queue* q) {
     a.nframes = frames;
     a.nx = c.nx;
     a.tiles = (c.nx + W - 1) / W;
-    a.chunks = (int)(((size_t)c.ny * c.nx / 2 + (size_t)th * 4 - 1) / ((size_t)th * 4));
+    a.chunks = update_chunks((size_t)c.ny * c.nx, th);
+    a.lag = persistent_order(c.table_h, frames);
     a.iters = m;
     a.ticket = reinterpret_cast<unsigned*>(c.ints + 4 * frames);
     a.tw = kv.second[0]->plan->tw_y;

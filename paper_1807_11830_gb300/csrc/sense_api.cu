@@ -20,6 +20,7 @@
 #include "plan.h"
 #include "trace.h"
 #include "sense.h"
+#include "sense_testing.h"
 
 using namespace sense;
 
@@ -632,7 +633,8 @@ sense_status run_cg_persistent(sense_plan* pl, const void* S, const int* lines, 
   a.nframes = F;
   a.nx = sh.nx;
   a.tiles = pl->norm_tiles;
-  a.chunks = (int)((pl->img / 2 + (size_t)threads * 4 - 1) / ((size_t)threads * 4));
+  a.chunks = update_chunks(pl->img, threads);
+  a.lag = persistent_order(pl->ptable_host, F);
   a.iters = max_iter;
   a.ticket = reinterpret_cast<unsigned*>(pl->pints + 4 * F);
   a.tw = pl->tw_y;
@@ -726,7 +728,7 @@ sense_status plan_allocate(sense_plan* pl) {
       const int th = normal_variant_threads(sh.ny, v);
       if (th > 0 && th < min_threads) min_threads = th;
     }
-    pl->max_chunks = (int)((pl->img / 2 + (size_t)min_threads * 4 - 1) / ((size_t)min_threads * 4));
+    pl->max_chunks = update_chunks(pl->img, min_threads);
   }
   const size_t F = (size_t)sh.frames;
   sense_status rc = SENSE_OK;
@@ -1262,3 +1264,15 @@ sense_status sense_plan_check(sense_plan* pl, void* stream) {
 }
 
 }  // extern "C"
+
+extern "C" void sense_testing_staggered_item(long long t, int units, int first_items, int second_items, int lag,
+                                             int out[3]) {
+  const sense::StaggeredItem it = sense::staggered_item((long)t, units, first_items, second_items, lag);
+  out[0] = it.second;
+  out[1] = it.unit;
+  out[2] = it.piece;
+}
+
+extern "C" int sense_testing_persistent_lag(int frames, int tiles, int grid) {
+  return sense::persistent_lag(frames, tiles, grid);
+}

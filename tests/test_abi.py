@@ -43,7 +43,8 @@ def test_library_exports_every_declared_symbol(lib):
 def test_binding_covers_every_declared_symbol():
     assert set(sense.EXPORTED) <= declared_entry_points() | {"sense_plan_workspace_bytes"}
     for name in declared_entry_points():
-        assert name in sense.EXPORTED or name.startswith("sense_queue") or name.startswith("sense_sched"), name
+        assert (name in sense.EXPORTED or name.startswith("sense_queue") or name.startswith("sense_sched")
+                or name.startswith("sense_testing")), name
 
 
 def test_size_table_is_host_only(lib):
