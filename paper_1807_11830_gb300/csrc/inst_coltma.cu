@@ -3,6 +3,7 @@
 // have them; the others keep the register-staged column kernels.
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 #include <utility>
 
@@ -20,14 +21,15 @@ constexpr int kMaxDynSmem = 227 * 1024;
 template <class K>
 cudaError_t coltma_grid(K kern, int threads, size_t smem, long items, int sms, int* grid) {
   static std::mutex mu;
-  static std::map<std::pair<int, size_t>, int> occ_cache;
+  static std::map<std::tuple<const void*, int, size_t>, int> occ_cache;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  const auto key = std::make_tuple(reinterpret_cast<const void*>(kern), dev, smem);
   int occ = 0;
   {
     std::lock_guard<std::mutex> lk(mu);
-    auto it = occ_cache.find({dev, smem});
+    auto it = occ_cache.find(key);
     if (it != occ_cache.end()) occ = it->second;
   }
   if (occ == 0) {
@@ -35,7 +37,7 @@ cudaError_t coltma_grid(K kern, int threads, size_t smem, long items, int sms, i
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorNotSupported;
     std::lock_guard<std::mutex> lk(mu);
-    occ_cache[{dev, smem}] = occ;
+    occ_cache[key] = occ;
   }
   const long cap = (long)sms * occ;
   *grid = (int)(items < cap ? items : cap);

@@ -71,7 +71,7 @@ __host__ __device__ __forceinline__ StaggeredItem staggered_item(long t, int U, 
 
 // Update items: each thread updates kUpdateRounds rounds of kUpdateVec float4
 // (two complex values each) of one frame's image.
-constexpr int kUpdateVec = 4, kUpdateRounds = 4;
+constexpr int kUpdateVec = 4, kUpdateRounds = 8;
 __host__ __device__ constexpr int update_chunks(size_t img, int threads) {
   return (int)((img / 2 + (size_t)threads * kUpdateVec * kUpdateRounds - 1) /
                ((size_t)threads * kUpdateVec * kUpdateRounds));
