@@ -943,6 +943,20 @@ __device__ __forceinline__ void wcol_setup(const WSmem<C, St>& s, const float2* 
   }
 }
 
+// One bit per frequency row this thread holds: set if the row is sampled.
+template <class C>
+__device__ __forceinline__ unsigned sampled_bits(const short* map) {
+  static_assert(C::JL * C::RL <= 32, "mask bits");
+  const C col;
+  unsigned keep = 0u;
+#pragma unroll
+  for (int j = 0; j < C::JL; ++j)
+#pragma unroll
+    for (int m = 0; m < C::RL; ++m)
+      if (col.okL(j) && map[col.krow(j, m)] >= 0) keep |= 1u << (j * C::RL + m);
+  return keep;
+}
+
 // line map of a frame: map[row] = index in the frame's line list, or -1
 // (The first round of line loads is issued before the map is cleared, so
 // its latency overlaps the clearing and the barrier.)
@@ -973,7 +987,7 @@ __device__ __forceinline__ void build_linemap(short* map, const int* ln, int L, 
 // thread's share of Re<p, q> (CG) as normal_tile does.
 template <class C, class St, bool CG>
 __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSmem<C, St>& s, unsigned keep,
-                                                  unsigned fill, int* err) {
+                                                  unsigned fill, int* err, const int* lines = nullptr, int L = 0) {
   constexpr int N = C::N, W = C::W, T = C::T, CW = 32 / T, CP = C::CP;
   using E = typename St::T;
   const C col;
@@ -1023,6 +1037,10 @@ __device__ __forceinline__ float normal_tile_warp(const NormalTile& a, const WSm
           pv[u] = __ldg(a.x + idx);
         }
       }
+    }
+    if (lines) {  // the frame's line map (and this lane's mask), built while the loads are in flight
+      build_linemap<N, C::THREADS>(s.map, lines, L, err);
+      keep = sampled_bits<C>(s.map);
     }
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
@@ -1138,19 +1156,6 @@ __global__ void __launch_bounds__(256) k_transpose_maps(const E* __restrict__ S,
   }
 }
 
-// One bit per frequency row this thread holds: set if the row is sampled.
-template <class C>
-__device__ __forceinline__ unsigned sampled_bits(const short* map) {
-  static_assert(C::JL * C::RL <= 32, "mask bits");
-  const C col;
-  unsigned keep = 0u;
-#pragma unroll
-  for (int j = 0; j < C::JL; ++j)
-#pragma unroll
-    for (int m = 0; m < C::RL; ++m)
-      if (col.okL(j) && map[col.krow(j, m)] >= 0) keep |= 1u << (j * C::RL + m);
-  return keep;
-}
 template <class C>
 __device__ __forceinline__ unsigned sampled_bits(const ColSmem& s) {
   return sampled_bits<C>(s.map);

@@ -71,7 +71,7 @@ __host__ __device__ __forceinline__ StaggeredItem staggered_item(long t, int U, 
 
 // Update items: each thread updates kUpdateRounds rounds of kUpdateVec float4
 // (two complex values each) of one frame's image.
-constexpr int kUpdateVec = 4, kUpdateRounds = 8;
+constexpr int kUpdateVec = 4, kUpdateRounds = 16;
 __host__ __device__ constexpr int update_chunks(size_t img, int threads) {
   return (int)((img / 2 + (size_t)threads * kUpdateVec * kUpdateRounds - 1) /
                ((size_t)threads * kUpdateVec * kUpdateRounds));
@@ -211,8 +211,10 @@ struct PTile<C, St, false> {  // block tiles, maps staged by TMA as [N][W] tiles
     sg.tmap = fr.tmap;
     if (threadIdx.x == 0) sg.issue(nfill, piece, 0);
   }
-  __device__ __forceinline__ float run(const NormalTile& nt, unsigned keep, unsigned nfill, int* err) const {
-    return normal_tile_tma<C, St>(nt, s, keep, sg, nfill, err);
+  // builds the frame's line map, then runs the tile
+  __device__ __forceinline__ float run(const NormalTile& nt, const int* lines, int L, unsigned nfill, int* err) const {
+    build_linemap<C::N, C::THREADS>(s.map, lines, L, err);
+    return normal_tile_tma<C, St>(nt, s, sampled_bits<C>(s.map), sg, nfill, err);
   }
 };
 
@@ -225,8 +227,9 @@ struct PTile<C, St, true> {  // lane-major tiles, maps by per-warp bulk copies o
   __device__ __forceinline__ double* red() const { return s.red; }
   __device__ __forceinline__ short* map() const { return s.map; }
   __device__ __forceinline__ void prefetch(const PFrame&, int, unsigned) {}
-  __device__ __forceinline__ float run(const NormalTile& nt, unsigned keep, unsigned nfill, int* err) const {
-    return normal_tile_warp<C, St, true>(nt, s, keep, nfill, err);
+  // the tile builds the line map while its p staging loads are in flight
+  __device__ __forceinline__ float run(const NormalTile& nt, const int* lines, int L, unsigned nfill, int* err) const {
+    return normal_tile_warp<C, St, true>(nt, s, 0u, nfill, err, lines, L);
   }
 };
 
@@ -291,8 +294,6 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
     if (normal) {
       if (work) {
         tile.prefetch(fr, piece, nfill);  // first coil's maps, overlapping the set-up below
-        build_linemap<N, T>(tile.map(), fr.lines, fr.L, a.err);
-        const unsigned keep = sampled_bits<C>(tile.map());
         const int kg = k + fr.k0;  // global iteration index of this frame
         NormalTile nt;
         nt.p_src = (kg > 0 && ((kg - 1) & 1) ? fr.p[1] : fr.p[0]);
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
           nt.ps_next = ip ? fn->p[1] : fn->p[0];
         }
         nt.beta = kg > 0 ? (float)__ldcg(fr.beta) : 0.f;
-        const float part = tile.run(nt, keep, nfill, a.err);
+        const float part = tile.run(nt, fr.lines, fr.L, nfill, a.err);
         nfill += (unsigned)fr.coils;
         const double tot = block_sum<T>((double)part, tile.red());
         if (threadIdx.x == 0) __stcg(g.part_nrm + (size_t)f * a.tiles + piece, tot);
