@@ -71,10 +71,8 @@ METRIC = "E^H·E applications/s"
 UNIT = "applications/s"
 FLUSH_BYTES = 512 << 20
 # ncu DRAM traffic of k_cg_persistent on this workload, bytes per CG iteration,
-# keyed by (kernel variant, CG mode): the lane-major 256-point variant in the
-# persistent kernel with compensated coil sums (51.3 MB read + 146.6 MB
-# written over 30 iterations, one launch)
-CINE_TRAFFIC_PER_ITER = {(1, "persistent"): (51.302400e6 + 146.589440e6) / 30}
+# keyed by (kernel variant, CG mode); empty until captured for the current kernel
+CINE_TRAFFIC_PER_ITER = {}
 # ncu DRAM traffic (read + write) of one k_cg_persistent launch of a mix size class, bytes per CG
 # iteration (empty until captured)
 MIX_TRAFFIC_PER_ITER = {}
