@@ -83,10 +83,10 @@ PAPER_WORKLOAD = ("paper reconstruction: 16 frames x 160x160, 8 coils, fully sam
 PAPER_METRIC, PAPER_UNIT = "reconstructions/s", "reconstructions/s"
 # OpenCLIPER's own time for this workload on a GTX 970 (Table II: clFFT 1.361 ms + RSS 0.252 ms): context
 PAPER_GTX970_MS = 1.361 + 0.252
-# ncu DRAM traffic per launch of the paper workload's kernels (read + write), from one launch
-# list of `bench.py --workload paper` (k_rows_bulk<160,+1>: 26.23 MB read; k_adj_col_tma<160,c64,rss>:
-# 26.25 MB read; their writes leave L2 after the launch)
-PAPER_TRAFFIC = {"rows_inv": 26.232576e6, "adj_col": 26.254848e6}
+# ncu DRAM traffic per launch of the paper workload's kernels (read + write, mean over the launches of one
+# launch list of `bench.py --workload paper --steps 20 --warmup 3 --no-cpu-baseline`: k_rows_bulk<160,+1>
+# 26.23 MB read; k_adj_col_tma<160,c64,rss> 26.25 MB read; their writes leave L2 after the launch)
+PAPER_TRAFFIC = {"rows_inv": 26.234243e6, "adj_col": 26.246184e6}
 
 
 def parse_args():
