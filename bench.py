@@ -71,10 +71,11 @@ METRIC = "E^H·E applications/s"
 UNIT = "applications/s"
 FLUSH_BYTES = 512 << 20
 # ncu DRAM traffic of k_cg_persistent on this workload, bytes per CG iteration,
-# keyed by (kernel variant, CG mode): the lane-major 256-point variant in the
-# persistent kernel (53.0 MB read + 120.0 MB written over 30 iterations, one
-# launch)
-CINE_TRAFFIC_PER_ITER = {(1, "persistent"): (52.997888e6 + 119.976192e6) / 30}
+# keyed by (kernel variant, CG mode), one launch of 30 iterations each: the
+# lane-major 8·4·8 variant (53.0 MB read + 120.0 MB written) and the
+# lane-major 16·16 variant (49.5 MB read + 93.6 MB written)
+CINE_TRAFFIC_PER_ITER = {(1, "persistent"): (52.997888e6 + 119.976192e6) / 30,
+                         (2, "persistent"): (49.472512e6 + 93.554176e6) / 30}
 # ncu DRAM traffic (read + write) of one k_cg_persistent launch of a mix size class, bytes per CG
 # iteration (empty until captured)
 MIX_TRAFFIC_PER_ITER = {}

@@ -753,6 +753,45 @@ __device__ __forceinline__ float normal_tile(const NormalTile& a, const ColSmem&
   return part;
 }
 
+// One bit per frequency row this thread holds: set if the row is sampled.
+template <class C>
+__device__ __forceinline__ unsigned sampled_bits(const short* map) {
+  static_assert(C::JL * C::RL <= 32, "mask bits");
+  const C col;
+  unsigned keep = 0u;
+#pragma unroll
+  for (int j = 0; j < C::JL; ++j)
+#pragma unroll
+    for (int m = 0; m < C::RL; ++m)
+      if (col.okL(j) && map[col.krow(j, m)] >= 0) keep |= 1u << (j * C::RL + m);
+  return keep;
+}
+
+// line map of a frame: map[row] = index in the frame's line list, or -1
+// (The first round of line loads is issued before the map is cleared, so
+// its latency overlaps the clearing and the barrier.)
+template <int N, int THREADS>
+__device__ __forceinline__ void build_linemap(short* map, const int* ln, int L, int* err) {
+  const int l0 = (int)threadIdx.x;
+  int v0 = 0, u0 = -1;
+  if (l0 < L) {
+    v0 = __ldg(ln + l0);
+    if (l0 > 0) u0 = __ldg(ln + l0 - 1);
+  }
+  for (int i = threadIdx.x; i < N; i += THREADS) map[i] = -1;
+  __syncthreads();
+  for (int l = l0; l < L; l += THREADS) {
+    const int v = l == l0 ? v0 : __ldg(ln + l);
+    const int u = l == l0 ? u0 : __ldg(ln + l - 1);  // l > 0 unless l == l0 == 0
+    const bool good = v >= 0 && v < N && (l == 0 || u < v);
+    if (good)
+      map[v] = (short)l;
+    else
+      atomicOr(err, ERR_LINES);
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // TMA-staged variant of normal_tile (CG mode): the maps of each coil arrive
 // as one [N][W] tile in shared memory by a 2D bulk tensor copy, double
@@ -786,30 +825,45 @@ struct SStage {
 
 template <class C, class St>
 __device__ __forceinline__ float normal_tile_tma(const NormalTile& a, const ColSmem& s, unsigned keep,
-                                                 const SStage<C, St>& sg, unsigned nfill, int* err) {
+                                                 const SStage<C, St>& sg, unsigned nfill, int* err,
+                                                 const int* lines = nullptr, int L = 0) {
   constexpr int N = C::N;
   const C col;
   const int x = a.tile * C::W + col.c;
   const bool xin = x < a.nx;
   float2 p[C::J0][C::R0], q[C::J0][C::R0], ql[C::J0][C::R0];  // q: compensated coil sum
+  {
+    // every load first, so their latencies overlap (and, given `lines`, the
+    // frame's line map is built while they are in flight)
+    float2 rv[C::J0][C::R0];
 #pragma unroll
-  for (int j = 0; j < C::J0; ++j)
+    for (int j = 0; j < C::J0; ++j)
 #pragma unroll
-    for (int n = 0; n < C::R0; ++n) {
-      float2 v = make_float2(0.f, 0.f);
-      if (col.ok0(j) && xin) {
-        const size_t idx = (size_t)col.xrow(j, n) * a.nx + x;
-        v = __ldcg(a.p_src + idx);
-        if (a.p_update) {
-          const float2 rv = __ldcg(a.r + idx);
-          v = make_float2(fmaf(a.beta, v.x, rv.x), fmaf(a.beta, v.y, rv.y));
-          __stcg(a.p_dst + idx, v);
+      for (int n = 0; n < C::R0; ++n) {
+        p[j][n] = make_float2(0.f, 0.f);
+        rv[j][n] = make_float2(0.f, 0.f);
+        if (col.ok0(j) && xin) {
+          const size_t idx = (size_t)col.xrow(j, n) * a.nx + x;
+          p[j][n] = __ldcg(a.p_src + idx);
+          if (a.p_update) rv[j][n] = __ldcg(a.r + idx);
         }
       }
-      p[j][n] = v;
-      q[j][n] = make_float2(0.f, 0.f);
-      ql[j][n] = make_float2(0.f, 0.f);
+    if (lines) {
+      build_linemap<N, C::THREADS>(s.map, lines, L, err);
+      keep = sampled_bits<C>(s.map);
     }
+#pragma unroll
+    for (int j = 0; j < C::J0; ++j)
+#pragma unroll
+      for (int n = 0; n < C::R0; ++n) {
+        if (col.ok0(j) && xin && a.p_update) {
+          p[j][n] = make_float2(fmaf(a.beta, p[j][n].x, rv[j][n].x), fmaf(a.beta, p[j][n].y, rv[j][n].y));
+          __stcg(a.p_dst + (size_t)col.xrow(j, n) * a.nx + x, p[j][n]);
+        }
+        q[j][n] = make_float2(0.f, 0.f);
+        ql[j][n] = make_float2(0.f, 0.f);
+      }
+  }
 
   float2* bufs[2] = {s.buf0, s.buf1};
 #pragma unroll 1
@@ -941,45 +995,6 @@ __device__ __forceinline__ void wcol_setup(const WSmem<C, St>& s, const float2* 
     for (int i = 0; i < 2 * (C::THREADS / 32); ++i) mbar_init(s.bar + i, 1);
     mbar_fence_init();
   }
-}
-
-// One bit per frequency row this thread holds: set if the row is sampled.
-template <class C>
-__device__ __forceinline__ unsigned sampled_bits(const short* map) {
-  static_assert(C::JL * C::RL <= 32, "mask bits");
-  const C col;
-  unsigned keep = 0u;
-#pragma unroll
-  for (int j = 0; j < C::JL; ++j)
-#pragma unroll
-    for (int m = 0; m < C::RL; ++m)
-      if (col.okL(j) && map[col.krow(j, m)] >= 0) keep |= 1u << (j * C::RL + m);
-  return keep;
-}
-
-// line map of a frame: map[row] = index in the frame's line list, or -1
-// (The first round of line loads is issued before the map is cleared, so
-// its latency overlaps the clearing and the barrier.)
-template <int N, int THREADS>
-__device__ __forceinline__ void build_linemap(short* map, const int* ln, int L, int* err) {
-  const int l0 = (int)threadIdx.x;
-  int v0 = 0, u0 = -1;
-  if (l0 < L) {
-    v0 = __ldg(ln + l0);
-    if (l0 > 0) u0 = __ldg(ln + l0 - 1);
-  }
-  for (int i = threadIdx.x; i < N; i += THREADS) map[i] = -1;
-  __syncthreads();
-  for (int l = l0; l < L; l += THREADS) {
-    const int v = l == l0 ? v0 : __ldg(ln + l);
-    const int u = l == l0 ? u0 : __ldg(ln + l - 1);  // l > 0 unless l == l0 == 0
-    const bool good = v >= 0 && v < N && (l == 0 || u < v);
-    if (good)
-      map[v] = (short)l;
-    else
-      atomicOr(err, ERR_LINES);
-  }
-  __syncthreads();
 }
 
 // One tile: `fill` counts the map copies this block has issued before (the

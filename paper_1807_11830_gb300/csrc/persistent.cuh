@@ -211,10 +211,9 @@ struct PTile<C, St, false> {  // block tiles, maps staged by TMA as [N][W] tiles
     sg.tmap = fr.tmap;
     if (threadIdx.x == 0) sg.issue(nfill, piece, 0);
   }
-  // builds the frame's line map, then runs the tile
+  // the tile builds the line map while its p loads are in flight
   __device__ __forceinline__ float run(const NormalTile& nt, const int* lines, int L, unsigned nfill, int* err) const {
-    build_linemap<C::N, C::THREADS>(s.map, lines, L, err);
-    return normal_tile_tma<C, St>(nt, s, sampled_bits<C>(s.map), sg, nfill, err);
+    return normal_tile_tma<C, St>(nt, s, 0u, sg, nfill, err, lines, L);
   }
 };
 
