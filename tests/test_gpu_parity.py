@@ -279,7 +279,8 @@ def test_cg_every_variant_and_autotune():
     assert rel(xg, xo) <= CG_TOL
 
 
-@pytest.mark.parametrize("shape", [(256, 20, 3, 64, 2), (128, 12, 4, 40, 3), (192, 20, 5, 48, 2)],
+@pytest.mark.parametrize("shape", [(256, 20, 3, 64, 2), (128, 12, 4, 40, 3), (192, 20, 5, 48, 2),
+                                   (320, 20, 3, 107, 2)],
                          ids=lambda s: "%dx%d" % s[:2])
 def test_cg_every_variant_ragged_tiles(shape):
     """Image widths that leave the last column tile (and, for lane-major
