@@ -205,7 +205,6 @@ struct PTile<C, St, false> {  // block tiles, maps staged by TMA as [N][W] tiles
     }
   }
   __device__ __forceinline__ double* red() const { return s.red; }
-  __device__ __forceinline__ short* map() const { return s.map; }
   // called before the line map is built, so the first coil's copy overlaps it
   __device__ __forceinline__ void prefetch(const PFrame& fr, int piece, unsigned nfill) {
     sg.tmap = fr.tmap;
@@ -224,7 +223,6 @@ struct PTile<C, St, true> {  // lane-major tiles, maps by per-warp bulk copies o
     wcol_setup<C, St>(s, tw);
   }
   __device__ __forceinline__ double* red() const { return s.red; }
-  __device__ __forceinline__ short* map() const { return s.map; }
   __device__ __forceinline__ void prefetch(const PFrame&, int, unsigned) {}
   // the tile builds the line map while its p staging loads are in flight
   __device__ __forceinline__ float run(const NormalTile& nt, const int* lines, int L, unsigned nfill, int* err) const {
@@ -241,8 +239,9 @@ __global__ void __launch_bounds__(TH, MINB) k_cg_persistent(PArgs a) {
   __shared__ int s_ticket, s_ok, s_active;
   unsigned nfill = 0;  // map copies requested so far by this block (same in every thread)
   // The thread that takes the block's tickets: the next item's ticket is
-  // taken at the end of the current item, while thread 0 publishes the
-  // item's arrival, so the two atomic round trips overlap.
+  // taken at the end of the current item, while the block's threads wait at
+  // their fence for their stores to become visible, so its round trip
+  // overlaps that wait.
   constexpr int TK = T > 32 ? 32 : 0;
   if (threadIdx.x == TK) s_ticket = (int)atomicAdd(a.ticket, 1u);
 
