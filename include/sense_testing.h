@@ -38,6 +38,12 @@ void sense_testing_staggered_item(long long t, int units, int first_items, int s
 /* The stagger the persistent CG kernel uses for a table of independent
    frames: frames, tiles per frame, grid blocks -> lag (0 .. frames - 1). */
 int sense_testing_persistent_lag(int frames, int tiles, int grid);
+/* Pins the item order of a plan's persistent CG launches: -1 iteration-major,
+   -2 automatic (the default), D >= 0 the frame-staggered order with lag D
+   (D < frames, else the solve fails with SENSE_ECUDA).  Frames coupled in
+   time always run iteration-major.  The order changes no arithmetic, so
+   every order gives the same bits; tests use this to check that. */
+sense_status sense_testing_plan_set_order(sense_plan* plan, int order);
 
 #ifdef __cplusplus
 }

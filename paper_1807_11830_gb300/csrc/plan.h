@@ -24,6 +24,7 @@ struct sense_plan {
   int norm_tiles = 0;    // column tiles per frame of that variant
   int cg_mode = 1;       // 0: per-phase kernels replayed as CUDA graphs; 1: one persistent launch
   int col_tma = 1;       // 1: TMA column passes; 2: single-launch fused E / E^H (square, TMA lengths); 0: per-tile
+  int cg_order = -2;     // persistent CG item order (kOrderAuto; a test hook can pin another, see sense_testing.h)
   int* fused_ints = nullptr;  // ticket and per-frame counters of the fused operators ([F + 1])
   int tiles8 = 0;        // 8-column tiles per frame (TMA column passes)
   double lambda = 0.0;   // Tikhonov weight of CG: (E^H E + lambda I) x = E^H y

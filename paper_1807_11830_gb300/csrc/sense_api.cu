@@ -635,6 +635,7 @@ sense_status run_cg_persistent(sense_plan* pl, const void* S, const int* lines, 
   a.tiles = pl->norm_tiles;
   a.chunks = update_chunks(pl->img, threads);
   a.lag = persistent_order(pl->ptable_host, F);
+  if (a.lag != kOrderIterationMajor) a.lag = pl->cg_order;  // frames coupled in time keep the iteration-major order
   a.iters = max_iter;
   a.ticket = reinterpret_cast<unsigned*>(pl->pints + 4 * F);
   a.tw = pl->tw_y;
@@ -1275,4 +1276,11 @@ extern "C" void sense_testing_staggered_item(long long t, int units, int first_i
 
 extern "C" int sense_testing_persistent_lag(int frames, int tiles, int grid) {
   return sense::persistent_lag(frames, tiles, grid);
+}
+
+extern "C" sense_status sense_testing_plan_set_order(sense_plan* pl, int order) {
+  if (!pl) return fail(SENSE_EINVAL, "plan is NULL");
+  if (order < sense::kOrderAuto) return fail(SENSE_EINVAL, "order must be -1, -2 or a lag >= 0");
+  pl->cg_order = order;
+  return SENSE_OK;
 }
